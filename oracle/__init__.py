@@ -1,0 +1,425 @@
+"""FP64 CPU oracle for batched finite-element cell kernels and global assembly.
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA library (``paper_2410_12614_gb300``) and never calls it.
+
+Contents and the passages they follow (Croci & Wells, "Mixed-precision finite
+element kernels and assembly"):
+
+* ``gauss_jacobi`` / ``collapsed_rule`` -- quadrature exact to degree 2m-1 on
+  the reference simplex by the collapsed (Duffy) conical product of
+  Gauss-Jacobi rules; the paper only requires exact rules (Sec. 3.1 footnote)
+  and states 2p-exact rules for the workloads.  Nodes and weights come from
+  the Golub-Welsch eigenproblem of the Jacobi matrix (numpy ``eigh``).
+* ``strang_fix_3`` -- the 3-point degree-2 triangle rule with interior points.
+* ``lattice_nodes`` / ``tabulate`` -- degree-p Lagrange basis on equispaced
+  lattice nodes, evaluated in the product form of Appendix A (Nicolaides'
+  representation phi_a = prod_i prod_{j<a_i} (p lambda_i - j)/(j+1)) and
+  differentiated by the product rule (Appendix A, derivative formula).
+* C routines in ``fe_oracle.c``: geometry by LU (Sec. 4.2), element matrices
+  by the literal quadrature sum (Sec. 3.1), canonical dof map, CSR pattern,
+  assembly A^g = L D L^T (Sec. 3.3), kappa_q^A (Corollary 4.10), adjoint.
+* ``error_bound`` -- the per-cell bound of Theorem 4.8 / Corollary 4.10 in
+  the form used by the tests (see its docstring).
+
+Everything is FP64; nothing is tuned.
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "libfe_oracle.so")
+_SRC = os.path.join(_HERE, "fe_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+# Unit roundoffs (Table 1 of the paper; e4m3 and tf32 added).
+UNIT_ROUNDOFF = {
+    "fp64": 2.0 ** -53,
+    "fp32": 2.0 ** -24,
+    "tf32": 2.0 ** -11,
+    "fp16": 2.0 ** -11,
+    "bf16": 2.0 ** -8,
+    "e4m3": 2.0 ** -4,
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile fe_oracle.c with gcc (no fast-math)."""
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+            i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+            f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+            c_int, c_i64 = ctypes.c_int, ctypes.c_int64
+            lib.fo_geometry.argtypes = [c_int, f64p, f64p, f64p, f64p]
+            lib.fo_mesh_geometry.argtypes = [c_int, c_i64, i32p, f64p, f64p, ctypes.c_void_p]
+            lib.fo_element_matrices.argtypes = [c_int, c_i64, c_i64, i32p, f64p, c_int, c_int, f64p, f64p,
+                                                f64p, f64p, c_int, f64p]
+            lib.fo_kappa_q.argtypes = [c_int, c_i64, c_i64, i32p, f64p, c_int, c_int, f64p, f64p, f64p,
+                                       f64p, c_int, f64p, f64p]
+            lib.fo_dofmap.argtypes = [c_int, c_int, i32p, c_i64, c_i64, i32p, i32p, ctypes.POINTER(c_i64)]
+            lib.fo_csr_pattern.argtypes = [c_i64, c_i64, c_int, i32p, i64p, ctypes.c_void_p]
+            lib.fo_assemble.argtypes = [c_i64, c_int, i32p, f64p, i64p, i32p, c_i64, c_int, f64p]
+            lib.fo_adjoint_stiffness.argtypes = [c_int, c_i64, i32p, f64p, c_i64, c_int, c_int, f64p, f64p,
+                                                 f64p, i32p, f64p, f64p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 ctypes.POINTER(ctypes.c_double)]
+            for f in ("fo_geometry", "fo_mesh_geometry", "fo_element_matrices", "fo_kappa_q", "fo_dofmap",
+                      "fo_csr_pattern", "fo_assemble", "fo_adjoint_stiffness"):
+                getattr(lib, f).restype = c_int
+            _lib = lib
+    return _lib
+
+
+def _check(status, what):
+    if status != 0:
+        raise RuntimeError(f"oracle {what} failed with status {status}")
+
+
+def _dim(cell_type):
+    if cell_type in ("triangle", "tri", 2):
+        return 2
+    if cell_type in ("tetrahedron", "tet", 3):
+        return 3
+    raise ValueError(cell_type)
+
+
+# --------------------------------------------------------------------------
+# Quadrature
+# --------------------------------------------------------------------------
+def gauss_jacobi(m: int, alpha: int):
+    """m-point Gauss rule on [0, 1] for the weight (1 - t)^alpha.
+
+    Golub-Welsch: the nodes are the eigenvalues of the symmetric Jacobi matrix
+    of the monic Jacobi polynomials P^(alpha, 0) on [-1, 1]; the weights are
+    mu_0 times the squared first components of the normalised eigenvectors,
+    mu_0 = int_{-1}^{1} (1 - x)^alpha dx = 2^(alpha+1)/(alpha+1).  The map
+    t = (1 + x)/2 turns (1-x)^alpha dx into 2^(alpha+1) (1-t)^alpha dt.
+    Returns (nodes ascending, weights).
+    """
+    a, b = float(alpha), 0.0
+    diag = np.empty(m)
+    off = np.empty(max(m - 1, 0))
+    for n in range(m):
+        s = 2 * n + a + b
+        diag[n] = (b - a) / (a + b + 2) if s == 0 else (b * b - a * a) / (s * (s + 2))
+    for n in range(1, m):
+        s = 2 * n + a + b
+        off[n - 1] = math.sqrt(4 * n * (n + a) * (n + b) * (n + a + b) / (s * s * (s + 1) * (s - 1)))
+    T = np.diag(diag) + np.diag(off, 1) + np.diag(off, -1)
+    x, V = np.linalg.eigh(T)
+    mu0 = 2.0 ** (a + 1) / (a + 1)
+    wx = mu0 * V[0, :] ** 2
+    t = (1.0 + x) / 2.0
+    wt = wx / 2.0 ** (a + 1)
+    return t, wt
+
+
+def collapsed_rule(cell_type, m: int):
+    """Collapsed conical product rule, exact to degree 2m-1, n_q = m^d.
+
+    Triangle: x = a (1 - b), y = b; Jacobian (1 - b).
+    Tetrahedron: x = a (1-b)(1-c), y = b (1-c), z = c; Jacobian (1-b)(1-c)^2.
+    Point order: q = ia + m (ib + m ic) (the first collapsed coordinate runs
+    fastest), 1-D nodes ascending.  Returns (points [n_q, d], weights [n_q]).
+    """
+    d = _dim(cell_type)
+    ta, wa = gauss_jacobi(m, 0)
+    tb, wb = gauss_jacobi(m, 1)
+    pts, wts = [], []
+    if d == 2:
+        for ib in range(m):
+            for ia in range(m):
+                a, b = ta[ia], tb[ib]
+                pts.append((a * (1 - b), b))
+                wts.append(wa[ia] * wb[ib])
+    else:
+        tc, wc = gauss_jacobi(m, 2)
+        for ic in range(m):
+            for ib in range(m):
+                for ia in range(m):
+                    a, b, c = ta[ia], tb[ib], tc[ic]
+                    pts.append((a * (1 - b) * (1 - c), b * (1 - c), c))
+                    wts.append(wa[ia] * wb[ib] * wc[ic])
+    return np.array(pts, dtype=np.float64), np.array(wts, dtype=np.float64)
+
+
+def strang_fix_3():
+    """3-point, degree-2 triangle rule with interior points (1/6,1/6),
+    (2/3,1/6), (1/6,2/3), each of weight 1/6 (reference area 1/2)."""
+    pts = np.array([[1 / 6, 1 / 6], [2 / 3, 1 / 6], [1 / 6, 2 / 3]], dtype=np.float64)
+    wts = np.full(3, 1 / 6, dtype=np.float64)
+    return pts, wts
+
+
+def rule_for_degree(cell_type, p: int):
+    """2p-exact collapsed rule (m = p + 1)."""
+    return collapsed_rule(cell_type, p + 1)
+
+
+# --------------------------------------------------------------------------
+# Lagrange basis on equispaced lattice nodes (Appendix A, product form)
+# --------------------------------------------------------------------------
+def lattice_nodes(d: int, p: int) -> np.ndarray:
+    """Barycentric multi-indices a in N^(d+1), |a| = p, in local order.
+
+    Order: support size, then the support's vertex tuple (lexicographic),
+    then a in descending lexicographic order.  Vertices come first in cell
+    vertex order, then edges 01,02,(03),12,(13),(23), faces, interior.
+    """
+    idx = [a for a in itertools.product(range(p + 1), repeat=d + 1) if sum(a) == p]
+
+    def key(a):
+        sup = tuple(i for i in range(d + 1) if a[i] > 0)
+        return (len(sup), sup, tuple(-x for x in a))
+
+    idx.sort(key=key)
+    return np.array(idx, dtype=np.int32)
+
+
+def node_points(d: int, p: int) -> np.ndarray:
+    """Reference coordinates X_a = (a_1, ..., a_d) / p of the lattice nodes."""
+    a = lattice_nodes(d, p)
+    return a[:, 1:].astype(np.float64) / p
+
+
+def _barycentric(points):
+    X = np.asarray(points, dtype=np.float64)
+    lam = np.empty((X.shape[0], X.shape[1] + 1))
+    lam[:, 0] = 1.0 - X.sum(axis=1)
+    lam[:, 1:] = X
+    return lam
+
+
+def tabulate(d: int, p: int, points):
+    """phi [n_phi, n_q] and dphi [d, n_phi, n_q] at the given reference points.
+
+    phi_a(lambda) = prod_i prod_{j=0}^{a_i - 1} (p lambda_i - j) / (j + 1).
+    d phi_a / d lambda_i by the product rule over the factors of index i;
+    d lambda_0 / d X_s = -1 and d lambda_i / d X_s = delta_is.
+    """
+    nodes = lattice_nodes(d, p)
+    lam = _barycentric(points)
+    n_q = lam.shape[0]
+    n_phi = nodes.shape[0]
+    phi = np.zeros((n_phi, n_q))
+    dphi = np.zeros((d, n_phi, n_q))
+    for k, a in enumerate(nodes):
+        for q in range(n_q):
+            # factors f[i][j] = (p lam_i - j)/(j+1), j < a_i
+            fac = []
+            for i in range(d + 1):
+                for j in range(a[i]):
+                    fac.append((i, (p * lam[q, i] - j) / (j + 1), p / (j + 1)))
+            val = 1.0
+            for _, f, _ in fac:
+                val *= f
+            phi[k, q] = val
+            dlam = np.zeros(d + 1)
+            for r, (i, _, df) in enumerate(fac):
+                prod = df
+                for r2, (_, f2, _) in enumerate(fac):
+                    if r2 != r:
+                        prod *= f2
+                dlam[i] += prod
+            for s in range(d):
+                dphi[s, k, q] = dlam[s + 1] - dlam[0]
+    return phi, dphi
+
+
+def n_phi(d: int, p: int) -> int:
+    return math.comb(p + d, d)
+
+
+# --------------------------------------------------------------------------
+# Mesh-level routines (C)
+# --------------------------------------------------------------------------
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def geometry(xv):
+    """J, det J, J^{-1} of one simplex from its (d+1) x d vertex array."""
+    xv = _c(xv, np.float64)
+    d = xv.shape[1]
+    J = np.zeros(d * d)
+    det = np.zeros(1)
+    Jinv = np.zeros(d * d)
+    _check(_load().fo_geometry(d, xv.ravel(), J, det, Jinv), "geometry")
+    return J.reshape(d, d), float(det[0]), Jinv.reshape(d, d)
+
+
+def mesh_geometry(vertices, cells, with_G: bool = True):
+    vertices, cells = _c(vertices, np.float64), _c(cells, np.int32)
+    d = vertices.shape[1]
+    nc = cells.shape[0]
+    det = np.zeros(nc)
+    G = np.zeros((nc, d, d)) if with_G else None
+    _check(_load().fo_mesh_geometry(d, nc, cells, vertices, det,
+                                    G.ctypes.data if with_G else None), "mesh_geometry")
+    return det, G
+
+
+class Problem:
+    """A mesh + degree + quadrature rule with the reference tabulation."""
+
+    def __init__(self, vertices, cells, p: int, points, weights):
+        self.vertices = _c(vertices, np.float64)
+        self.cells = _c(cells, np.int32)
+        self.d = self.vertices.shape[1]
+        self.p = int(p)
+        self.points = _c(points, np.float64)
+        self.weights = _c(weights, np.float64)
+        self.n_q = self.weights.shape[0]
+        self.n_cells = self.cells.shape[0]
+        self.n_phi = n_phi(self.d, self.p)
+        self.phi, self.dphi = tabulate(self.d, self.p, self.points)
+        self.phi = _c(self.phi, np.float64)
+        self.dphi = _c(self.dphi, np.float64)
+        self._dofs = None
+        self._pattern = None
+
+    # element matrices --------------------------------------------------
+    def element_matrices(self, kappa, form: str, c0: int = 0, c1: int | None = None):
+        """A [n_cells, n_phi, n_phi] (rows outside [c0, c1) are left zero)."""
+        c1 = self.n_cells if c1 is None else c1
+        kappa = _c(kappa, np.float64).reshape(self.n_cells, self.n_q)
+        A = np.zeros((self.n_cells, self.n_phi, self.n_phi))
+        f = {"mass": 1, "stiffness": 2}[form]
+        _check(_load().fo_element_matrices(self.d, c0, c1, self.cells, self.vertices, self.n_phi, self.n_q,
+                                           self.weights, self.phi, self.dphi, kappa.ravel(), f, A.reshape(-1)),
+               "element_matrices")
+        return A
+
+    def element_matrices_subset(self, kappa, form: str, cell_ids):
+        """Element matrices of the listed cells only, [len(cell_ids), n_phi, n_phi]."""
+        cell_ids = np.asarray(cell_ids, dtype=np.int64)
+        sub = Problem.__new__(Problem)
+        sub.__dict__.update(self.__dict__)
+        sub.cells = _c(self.cells[cell_ids], np.int32)
+        sub.n_cells = len(cell_ids)
+        kap = _c(np.asarray(kappa).reshape(self.n_cells, self.n_q)[cell_ids], np.float64)
+        return Problem.element_matrices(sub, kap, form)
+
+    def kappa_q(self, kappa, form: str, A, cell_ids=None):
+        """Per-cell kappa_q^A (Corollary 4.10) for the given exact matrices."""
+        kappa = _c(kappa, np.float64).reshape(-1, self.n_q)
+        cells = self.cells if cell_ids is None else _c(self.cells[np.asarray(cell_ids)], np.int32)
+        if cell_ids is not None:
+            kappa = _c(kappa[np.asarray(cell_ids)], np.float64)
+        nc = cells.shape[0]
+        kq = np.zeros(nc)
+        f = {"mass": 1, "stiffness": 2}[form]
+        _check(_load().fo_kappa_q(self.d, 0, nc, cells, self.vertices, self.n_phi, self.n_q, self.weights,
+                                  self.phi, self.dphi, kappa.ravel(), f, _c(A, np.float64).reshape(-1), kq),
+               "kappa_q")
+        return kq
+
+    # dof map / pattern ----------------------------------------------------
+    def cell_dofs(self):
+        if self._dofs is None:
+            nodes = _c(lattice_nodes(self.d, self.p), np.int32)
+            dofs = np.zeros((self.n_cells, self.n_phi), dtype=np.int32)
+            nd = ctypes.c_int64(0)
+            _check(_load().fo_dofmap(self.d, self.n_phi, nodes.ravel(), self.vertices.shape[0], self.n_cells,
+                                     self.cells, dofs.reshape(-1), ctypes.byref(nd)), "dofmap")
+            self._dofs = (dofs, int(nd.value))
+        return self._dofs
+
+    @property
+    def n_dofs(self):
+        return self.cell_dofs()[1]
+
+    def csr_pattern(self):
+        if self._pattern is None:
+            dofs, nd = self.cell_dofs()
+            row_ptr = np.zeros(nd + 1, dtype=np.int64)
+            lib = _load()
+            _check(lib.fo_csr_pattern(nd, self.n_cells, self.n_phi, dofs.reshape(-1), row_ptr, None), "pattern")
+            col = np.zeros(int(row_ptr[-1]), dtype=np.int32)
+            _check(lib.fo_csr_pattern(nd, self.n_cells, self.n_phi, dofs.reshape(-1), row_ptr, col.ctypes.data),
+                   "pattern")
+            self._pattern = (row_ptr, col)
+        return self._pattern
+
+    def assemble(self, A, absval: bool = False):
+        dofs, nd = self.cell_dofs()
+        row_ptr, col = self.csr_pattern()
+        vals = np.zeros(col.shape[0])
+        _check(_load().fo_assemble(self.n_cells, self.n_phi, dofs.reshape(-1), _c(A, np.float64).reshape(-1),
+                                   row_ptr, col, col.shape[0], int(absval), vals), "assemble")
+        return vals
+
+    def dof_points(self):
+        """Physical coordinates of every global dof (from the cell that first lists it)."""
+        dofs, nd = self.cell_dofs()
+        lam = _barycentric(node_points(self.d, self.p))
+        pts = np.full((nd, self.d), np.nan)
+        xv = self.vertices[self.cells]  # [nc, d+1, d]
+        phys = np.einsum("kv,cvi->cki", lam, xv)
+        pts[dofs.reshape(-1)] = phys.reshape(-1, self.d)
+        return pts
+
+    # adjoint --------------------------------------------------------------
+    def adjoint_stiffness(self, kappa, u, v, vertices=None, want_kappa=True, want_x=True):
+        dofs, nd = self.cell_dofs()
+        verts = self.vertices if vertices is None else _c(vertices, np.float64)
+        kappa = _c(kappa, np.float64).reshape(self.n_cells, self.n_q)
+        gk = np.zeros((self.n_cells, self.n_q)) if want_kappa else None
+        gx = np.zeros_like(verts) if want_x else None
+        L = ctypes.c_double(0.0)
+        _check(_load().fo_adjoint_stiffness(self.d, self.n_cells, self.cells, verts, verts.shape[0], self.n_phi,
+                                            self.n_q, self.weights, self.dphi, kappa.ravel(), dofs.reshape(-1),
+                                            _c(u, np.float64), _c(v, np.float64),
+                                            gk.ctypes.data if want_kappa else None,
+                                            gx.ctypes.data if want_x else None, ctypes.byref(L)), "adjoint")
+        return float(L.value), gk, gx
+
+    def with_vertices(self, vertices):
+        other = Problem.__new__(Problem)
+        other.__dict__.update(self.__dict__)
+        other.vertices = _c(vertices, np.float64)
+        return other
+
+
+# --------------------------------------------------------------------------
+# Error bounds (Theorem 4.8 / Corollary 4.10, Corollary 4.11)
+# --------------------------------------------------------------------------
+def error_bound(kq, u_s: float, K: int, u_acc: float = 2.0 ** -23, u_out: float = 2.0 ** -24,
+                storage_roundings: int = 2):
+    """Per-cell relative max-norm bound for a reduced-precision contraction.
+
+        err_c <= (r u_s + gamma_K(2 u_acc)) kappa_q^A(c) + u_out
+
+    with r the number of operand roundings to storage (C and the tabulated
+    operand: r = 2), gamma_K(x) = K x / (1 - K x) the accumulation constant
+    over the contraction length K (Lemma 2.2 / matrix-product bound, Sec. 2),
+    the accumulation roundoff doubled to allow truncating (round-toward-zero)
+    accumulation, and u_out the rounding of the FP32 output.  This is the
+    bound of Corollary 4.10 with u_g = u_p ~ 0 (FP64 geometry and tabulation).
+    """
+    x = K * 2.0 * u_acc
+    gamma = x / (1.0 - x)
+    return (storage_roundings * u_s + gamma) * np.asarray(kq) + u_out

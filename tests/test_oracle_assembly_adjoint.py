@@ -1,0 +1,205 @@
+"""Pins for the oracle's dof map, CSR pattern, assembly and adjoint.
+
+Dof map: n_dofs = (pN+1)^d on the structured meshes (equispaced nodes of a
+degree-p simplex mesh coincide with the fine lattice), every dof has one
+physical point on all cells that list it and distinct dofs have distinct
+points (continuity of the Lagrange space), vertex dofs take the vertex id and
+the remaining keys are strictly increasing (the canonical numbering).
+Pattern: brute force from a dense boolean matrix; P1 closed form
+nnz = n_v + 2 n_edges.  Assembly (Sec. 3.3, A^g = L D L^T): dense
+brute-force scatter with numpy, K^g 1 = 0, 1^T M^g 1 = sum of weighted
+volumes, and the global energy identity.  Adjoint: central differences
+(exact in kappa, which enters linearly), translation invariance and the
+homogeneity identity sum_v x_v . dL/dx_v = (d-2) L.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_12614_gb300 import inputs
+
+
+def _problem(cell, n, p, alpha=0.15, seed=3):
+    v, c = inputs.structured_mesh(cell, n, alpha, seed)
+    return oracle.Problem(v, c, p, *oracle.rule_for_degree(cell, p))
+
+
+@pytest.mark.parametrize("cell,n,p", [("triangle", 3, 1), ("triangle", 4, 3), ("triangle", 2, 6),
+                                      ("tetrahedron", 2, 1), ("tetrahedron", 2, 3), ("tetrahedron", 3, 2),
+                                      ("tetrahedron", 1, 5)])
+def test_dofmap_counts_and_continuity(cell, n, p):
+    d = 2 if cell == "triangle" else 3
+    pr = _problem(cell, n, p)
+    dofs, nd = pr.cell_dofs()
+    assert nd == (p * n + 1) ** d
+    assert set(np.unique(dofs)) == set(range(nd))
+    # vertex dofs are the vertex ids
+    assert np.array_equal(dofs[:, : d + 1], pr.cells)
+    # one physical point per dof, agreed on by every cell
+    lam = np.hstack([1 - oracle.node_points(d, p).sum(1, keepdims=True), oracle.node_points(d, p)])
+    phys = np.einsum("kv,cvi->cki", lam, pr.vertices[pr.cells]).reshape(-1, d)
+    ref = pr.dof_points()
+    np.testing.assert_allclose(phys, ref[dofs.reshape(-1)], rtol=0, atol=1e-14)
+    # distinct dofs -> distinct points
+    r = np.round(ref, 10)
+    assert len(np.unique(r, axis=0)) == nd
+    # no dof appears twice in one cell
+    assert all(len(set(row)) == pr.n_phi for row in dofs)
+
+
+def test_canonical_key_order():
+    pr = _problem("tetrahedron", 2, 4)
+    d = 3
+    dofs, nd = pr.cell_dofs()
+    nodes = oracle.lattice_nodes(d, 4)
+    keys = {}
+    for ci, cell in enumerate(pr.cells):
+        for k, a in enumerate(nodes):
+            sup = sorted((int(cell[i]), int(a[i])) for i in range(d + 1) if a[i] > 0)
+            if len(sup) == 1:
+                continue
+            key = (len(sup), tuple(g for g, _ in sup), tuple(m for _, m in sup))
+            keys.setdefault(int(dofs[ci, k]), set()).add(key)
+    assert all(len(s) == 1 for s in keys.values())
+    ordered = [next(iter(keys[i])) for i in range(pr.vertices.shape[0], nd)]
+    assert all(ordered[i] < ordered[i + 1] for i in range(len(ordered) - 1))
+
+
+def _dense_pattern(dofs, nd):
+    P = np.zeros((nd, nd), dtype=bool)
+    for row in dofs:
+        P[np.ix_(row, row)] = True
+    return P
+
+
+@pytest.mark.parametrize("cell,n,p", [("triangle", 3, 2), ("tetrahedron", 2, 2), ("tetrahedron", 1, 4)])
+def test_pattern_brute_force(cell, n, p):
+    pr = _problem(cell, n, p)
+    dofs, nd = pr.cell_dofs()
+    rp, ci = pr.csr_pattern()
+    P = _dense_pattern(dofs, nd)
+    for i in range(nd):
+        assert np.array_equal(ci[rp[i]:rp[i + 1]], np.nonzero(P[i])[0])
+    assert rp[-1] == P.sum()
+
+
+def test_p1_triangle_pattern_closed_form():
+    n = 32
+    pr = _problem("triangle", n, 1, alpha=0.2)
+    edges = 2 * n * (n + 1) + n * n  # horizontal + vertical + one diagonal per box
+    assert pr.csr_pattern()[0][-1] == (n + 1) ** 2 + 2 * edges == 7361
+
+
+def test_p1_tet_pattern_closed_form():
+    n = 6
+    pr = _problem("tetrahedron", n, 1)
+    edges = 3 * n * (n + 1) ** 2 + 3 * n * n * (n + 1) + n ** 3  # axis, face-diagonal, body-diagonal
+    assert pr.csr_pattern()[0][-1] == (n + 1) ** 3 + 2 * edges
+
+
+@pytest.mark.parametrize("cell,n,p", [("triangle", 3, 3), ("tetrahedron", 2, 2), ("tetrahedron", 2, 3)])
+def test_assembly_brute_force_and_invariants(cell, n, p):
+    d = 2 if cell == "triangle" else 3
+    pr = _problem(cell, n, p)
+    kap = inputs.lognormal_kappa(pr.n_cells, pr.n_q, 12)
+    dofs, nd = pr.cell_dofs()
+    rp, ci = pr.csr_pattern()
+    for form in ("stiffness", "mass"):
+        A = pr.element_matrices(kap, form)
+        vals = pr.assemble(A)
+        D = np.zeros((nd, nd))
+        for c in range(pr.n_cells):
+            np.add.at(D, (dofs[c][:, None], dofs[c][None, :]), A[c])
+        S = np.zeros((nd, nd))
+        for i in range(nd):
+            S[i, ci[rp[i]:rp[i + 1]]] = vals[rp[i]:rp[i + 1]]
+        np.testing.assert_allclose(S, D, rtol=0, atol=1e-14 * np.abs(D).max())
+        np.testing.assert_allclose(S, S.T, rtol=0, atol=1e-14 * np.abs(D).max())
+        if form == "stiffness":
+            np.testing.assert_allclose(S.sum(axis=1), 0.0, atol=1e-12 * np.abs(S).max())
+        else:
+            det, _ = oracle.mesh_geometry(pr.vertices, pr.cells, with_G=False)
+            total = float(np.sum((kap @ pr.weights) * np.abs(det)))
+            assert abs(S.sum() - total) <= 1e-13 * total
+
+
+def test_global_energy_identity():
+    cell, p = "tetrahedron", 3
+    pr = _problem(cell, 2, p)
+    d = 3
+    kap = inputs.lognormal_kappa(pr.n_cells, pr.n_q, 13)
+    vals = pr.assemble(pr.element_matrices(kap, "stiffness"))
+    rp, ci = pr.csr_pattern()
+    pts = pr.dof_points()
+    rng = np.random.default_rng(14)
+    expo = [e for e in itertools.product(range(p + 1), repeat=d) if sum(e) <= p]
+    cf, cg = rng.standard_normal(len(expo)), rng.standard_normal(len(expo))
+    f = lambda x: sum(a * np.prod(x ** np.array(e), axis=-1) for a, e in zip(cf, expo))
+    g = lambda x: sum(a * np.prod(x ** np.array(e), axis=-1) for a, e in zip(cg, expo))
+
+    def grad(cfs, x):
+        out = np.zeros(x.shape)
+        for a, e in zip(cfs, expo):
+            for s in range(d):
+                if e[s]:
+                    e2 = list(e)
+                    e2[s] -= 1
+                    out[..., s] += a * e[s] * np.prod(x ** np.array(e2), axis=-1)
+        return out
+
+    uf, ug = f(pts), g(pts)
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    lhs = np.sum(uf[rows] * vals * ug[ci])
+    lam_q = np.hstack([1 - pr.points.sum(1, keepdims=True), pr.points])
+    rhs = 0.0
+    for c in range(pr.n_cells):
+        xv = pr.vertices[pr.cells[c]]
+        vol = abs(np.linalg.det((xv[1:] - xv[0]).T))
+        xq = lam_q @ xv
+        rhs += np.sum(pr.weights * kap[c] * vol * np.sum(grad(cf, xq) * grad(cg, xq), axis=1))
+    assert abs(lhs - rhs) <= 1e-11 * abs(rhs)
+
+
+# ---------------------------------------------------------------------------
+# adjoint of L = v^T A^g u (Poisson)
+# ---------------------------------------------------------------------------
+def _L(pr, kap, u, v):
+    vals = pr.assemble(pr.element_matrices(kap, "stiffness"))
+    rp, ci = pr.csr_pattern()
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    return float(np.sum(v[rows] * vals * u[ci]))
+
+
+@pytest.mark.parametrize("cell,p", [("triangle", 2), ("tetrahedron", 2)])
+def test_adjoint_matches_finite_differences(cell, p):
+    d = 2 if cell == "triangle" else 3
+    pr = _problem(cell, 2, p)
+    kap = inputs.lognormal_kappa(pr.n_cells, pr.n_q, 21)
+    u = inputs.gaussian_vector(pr.n_dofs, 22).astype(np.float64)
+    v = inputs.gaussian_vector(pr.n_dofs, 23).astype(np.float64)
+    L, gk, gx = pr.adjoint_stiffness(kap, u, v)
+    assert abs(L - _L(pr, kap, u, v)) <= 1e-12 * abs(L)
+    rng = np.random.default_rng(5)
+    # kappa enters linearly: central differences are exact up to rounding
+    for _ in range(6):
+        c, q = rng.integers(pr.n_cells), rng.integers(pr.n_q)
+        h = 1e-3
+        kp, km = kap.copy(), kap.copy()
+        kp[c, q] += h
+        km[c, q] -= h
+        fd = (_L(pr, kp, u, v) - _L(pr, km, u, v)) / (2 * h)
+        assert abs(fd - gk[c, q]) <= 1e-9 * (abs(gk).max())
+    # vertex coordinates: central differences with step 1e-6 (kappa held fixed)
+    for _ in range(6):
+        vi, i = rng.integers(pr.vertices.shape[0]), rng.integers(d)
+        h = 1e-6
+        xp, xm = pr.vertices.copy(), pr.vertices.copy()
+        xp[vi, i] += h
+        xm[vi, i] -= h
+        fd = (_L(pr.with_vertices(xp), kap, u, v) - _L(pr.with_vertices(xm), kap, u, v)) / (2 * h)
+        assert abs(fd - gx[vi, i]) <= 1e-6 * np.abs(gx).max()
+    # translation invariance and homogeneity of degree d-2
+    np.testing.assert_allclose(gx.sum(axis=0), 0.0, atol=1e-12 * np.abs(gx).max())
+    assert abs(np.sum(pr.vertices * gx) - (d - 2) * L) <= 1e-11 * max(abs(L), np.abs(gx).max())
