@@ -1,0 +1,347 @@
+"""Benchmark: element matrices/s and assembled nnz/s of the P3 stiffness +
+mass workload on tetrahedra (unit cube, 24^3 boxes x 6 Kuhn tetrahedra =
+82,944 cells, vertices jittered +-0.15h, kappa lognormal(0,1) at the 64
+points of the 6-exact collapsed Gauss-Jacobi rule), mixed precision (BF16
+operands, FP32 accumulation) against the FP64 GPU path.
+
+One step = element matrices of both forms (written to HBM) + their CSR
+assembly, through the C ABI (fe_assemble).  Inputs are resident in HBM; the
+L2 is flushed between timed steps (a 512 MB write outside the timed events).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun): every rank runs an independent copy of the workload (weak
+scaling, no collective); rank 0 prints the JSON line with the max-over-ranks
+time.  --impl reference times the FP64 CPU oracle on a bounded sample of the
+same workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("P3 stiffness + mass, unit cube 24^3 boxes x 6 Kuhn tetrahedra (82,944 cells, 389,017 dofs, "
+            "18,388,729 nnz per matrix), jitter +-0.15h, kappa lognormal(0,1) at 64 collapsed Gauss-Jacobi points")
+METRIC = "element matrices/s (stiffness + mass, with CSR assembly), mixed BF16 tensor-core path"
+N_BOX, DEGREE, ALPHA, SEED_MESH, SEED_KAPPA = 24, 3, 0.15, 2, 3
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.samples = []
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except Exception:
+            self.proc.kill()
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for n, v in zip(names, s[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def make_inputs():
+    from paper_2410_12614_gb300 import inputs
+    v, c = inputs.cube_mesh(N_BOX, ALPHA, SEED_MESH)
+    return v, c
+
+
+def algorithmic_bytes(plan, prec):
+    eb = 8 if prec == "fp64" else 4
+    nc, nph, nq = plan.n_cells, plan.n_phi, plan.n_q
+    elem = nc * nq * 8 + nc * 4 * 4 + plan.n_vertices * 3 * 8 + 2 * nc * nph * nph * eb
+    asm = (2 * nc * nph * nph * eb + 2 * plan.nnz * eb + (plan.n_dofs + 1) * 16 + nc * nph * 4
+           + nc * nph * nph * 2)
+    return elem, asm
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2410_12614_gb300 import api, inputs
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    v, c = make_inputs()
+    pts, w = api.quadrature_rule("tetrahedron", DEGREE + 1)
+    with torch.cuda.stream(stream):
+        plan = api.Plan("tetrahedron", v, c, DEGREE, pts, w, precisions=("bf16", "fp16"), stream=stream)
+        kap_h = inputs.lognormal_kappa(plan.n_cells, plan.n_q, SEED_KAPPA)
+        kap = torch.from_numpy(kap_h).cuda()
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+        def buffers(prec):
+            els = {f: plan.empty_elements(prec) for f in ("stiffness", "mass")}
+            vals = {f: plan.empty_values(prec) for f in ("stiffness", "mass")}
+            return els, vals
+
+        def timed(prec, steps, warmup):
+            els, vals = buffers(prec)
+            plan.enable_timing(True)
+            for _ in range(warmup):
+                plan.assemble(kap, prec=prec, elements=els, out=vals)
+            plan.sync()
+            step_ms, el_ms, as_ms = [], [], []
+            launches = 0
+            for _ in range(steps):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                plan.assemble(kap, prec=prec, elements=els, out=vals)
+                e1.record(stream)
+                launches += plan.last_launches()
+                stream.synchronize()
+                step_ms.append(e0.elapsed_time(e1))
+                st = plan.stage_times()
+                el_ms.append(st[0])
+                as_ms.append(st[1])
+            plan.sync()
+            plan.enable_timing(False)
+            return step_ms, el_ms, as_ms, launches, els, vals
+
+        # headline: BF16
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(dev)
+        sampler.start()
+        step_ms, el_ms, as_ms, launches, els, vals = timed("bf16", args.steps, args.warmup)
+        clocks = sampler.stop()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        total_ms = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([total_ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+        ms_step = total_ms / args.steps
+        elems_per_step = 2 * plan.n_cells
+        value = world * elems_per_step / (ms_step / 1e3)
+        nnz_per_s = world * 2 * plan.nnz / (ms_step / 1e3)
+
+        # end to end through the public API with host buffers
+        kap_pinned = torch.from_numpy(kap_h).pin_memory()
+        host_out = {f: torch.empty(plan.nnz, dtype=torch.float32, pin_memory=True) for f in ("stiffness", "mass")}
+        for _ in range(2):
+            plan.assemble_host(kap_pinned, prec="bf16", out=host_out)
+        e2e_ms = []
+        for _ in range(max(3, args.steps // 2)):
+            t0 = time.perf_counter()
+            plan.assemble_host(kap_pinned, prec="bf16", out=host_out)
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e_step = statistics.median(e2e_ms)
+
+        # other precisions (context lines)
+        extra = {}
+        for prec, k in (("fp16", max(3, args.steps // 2)), ("fp64", 3)):
+            s2, e2, a2, _, _, _ = timed(prec, k, 1)
+            extra[prec] = {"ms_per_step": statistics.mean(s2), "element_kernel_ms": statistics.mean(e2),
+                           "assembly_kernel_ms": statistics.mean(a2),
+                           "element_matrices_per_s": elems_per_step / (statistics.mean(s2) / 1e3)}
+        extra["bf16_speedup_vs_fp64"] = extra["fp64"]["ms_per_step"] / ms_step
+
+    hbm, how = _peaks()
+    eb, ab = algorithmic_bytes(plan, "bf16")
+    el_avg, as_avg = statistics.mean(el_ms), statistics.mean(as_ms)
+    if as_avg >= el_avg:
+        dom, dom_ms, dom_bytes = "assembly (segmented row reduction)", as_avg, ab
+    else:
+        dom, dom_ms, dom_bytes = "element matrices (tcgen05 BF16)", el_avg, eb
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    result = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "element matrices/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16",
+        "data": "synthetic (seeded structured mesh + lognormal kappa)",
+        "config": {"workload": WORKLOAD, "precision": "BF16 operands, FP32 accumulation, FP64 geometry",
+                   "step": "fe_assemble: element matrices of both forms to HBM + CSR assembly of both",
+                   "l2": "flushed between steps (512 MB write outside the timed events)",
+                   "parallelism": f"independent replica per GPU x{world}"},
+        "nnz_per_s": nnz_per_s,
+        "stage_ms": {"element_kernel": el_avg, "assembly_kernel": as_avg},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "peak_source": f"{how} (MEASURED_PEAKS.json hbm_gbs)",
+                     "algorithmic_bytes_per_launch": dom_bytes},
+        "e2e": {"value": elems_per_step / (e2e_step / 1e3) * world, "unit": "element matrices/s",
+                "h2d_bytes_per_step": int(plan.n_cells * plan.n_q * 8),
+                "d2h_bytes_per_step": int(2 * plan.nnz * 4), "ms_per_step": e2e_step,
+                "api": "fe_assemble_host (pinned host kappa in, pinned host CSR values out)"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "per_precision": extra,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args, plan, kap_h, els, v, c)
+    return result
+
+
+def cpu_baseline(args, plan=None, kap=None, gpu_els=None, v=None, c=None, budget_s=None):
+    """Time the FP64 oracle (single thread, as it stands) on a bounded sample
+    of cells of the same workload; with GPU results at hand, also report the
+    measured error of the GPU's BF16 element matrices on those cells."""
+    import oracle
+    from paper_2410_12614_gb300 import inputs
+
+    if v is None:
+        v, c = make_inputs()
+    pts, w = oracle.collapsed_rule("tetrahedron", DEGREE + 1)
+    ref = oracle.Problem(v, c, DEGREE, pts, w)
+    if kap is None:
+        kap = inputs.lognormal_kappa(ref.n_cells, ref.n_q, SEED_KAPPA)
+    budget = budget_s if budget_s is not None else args.cpu_seconds
+    # calibrate on 64 cells, then size the sample to the budget
+    ids = np.arange(64)
+    t0 = time.perf_counter()
+    for form in ("stiffness", "mass"):
+        ref.element_matrices_subset(kap, form, ids)
+    per_cell = (time.perf_counter() - t0) / 64
+    n = int(max(128, min(ref.n_cells, budget / max(per_cell, 1e-9))))
+    rng = np.random.default_rng(99)
+    ids = np.sort(rng.choice(ref.n_cells, size=n, replace=False))
+    ref.csr_pattern()  # the pattern is set-up work, outside the timed region
+    t0 = time.perf_counter()
+    A = {f: ref.element_matrices_subset(kap, f, ids) for f in ("stiffness", "mass")}
+    for f in ("stiffness", "mass"):
+        ref.assemble_subset(A[f], ids)
+    dt = time.perf_counter() - t0
+    out = {"value": 2 * n / dt, "unit": "element matrices/s", "cores": 1, "kind": "oracle",
+           "sample": f"{n} random cells of the workload: both forms by FP64 literal quadrature loops, "
+                     "assembled into the CSR values", "seconds": dt}
+    if gpu_els is not None:
+        import oracle as orc
+        errs = {}
+        for f in ("stiffness", "mass"):
+            got = gpu_els[f][ids].double().cpu().numpy()
+            e = np.abs(got - A[f]).reshape(n, -1).max(1) / np.abs(A[f]).reshape(n, -1).max(1)
+            kq = ref.kappa_q(kap, f, A[f], cell_ids=ids)
+            K = ref.n_q * (6 if f == "stiffness" else 1)
+            bnd = orc.error_bound(kq, 2.0 ** -8, K)
+            errs[f] = {"max_rel_err": float(e.max()), "max_rel_err_over_u_s": float(e.max() / 2.0 ** -8),
+                       "bound_at_worst_cell": float(bnd[np.argmax(e)]), "within_bound": bool(np.all(e <= bnd))}
+        out["bf16_accuracy_on_sample"] = errs
+    return out
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    budget = max(2.0, min(30.0, 120.0 / max(1, args.steps + args.warmup)))
+    times, val = [], None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(args, budget_s=budget)
+        if i >= args.warmup:
+            times.append(r)
+    value = statistics.mean(t["value"] for t in times)
+    ms = 2 * 82944 / value * 1e3
+    return {
+        "impl": "reference",
+        "metric": METRIC.replace("mixed BF16 tensor-core path", "FP64 CPU oracle"),
+        "value": value, "unit": "element matrices/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded structured mesh + lognormal kappa)",
+        "config": {"workload": WORKLOAD, "step": "element matrices of both forms + their assembly, on a bounded cell sample"},
+        "cpu_baseline": {"value": value, "unit": "element matrices/s", "cores": 1, "kind": "oracle",
+                         "sample": times[-1]["sample"]},
+        "e2e": {"value": value, "unit": "element matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * fe_gb300.h -- C ABI of the GB300 (sm_103a) library for batched
+ * finite-element cell kernels and global assembly, after Croci & Wells,
+ * "Mixed-precision finite element kernels and assembly: rounding error
+ * analysis and hardware acceleration".
+ *
+ * The library computes, for a mesh of affine simplices (triangles or
+ * tetrahedra) and continuous degree-p Lagrange elements:
+ *   - per-cell geometry J, det J, J^{-1} and G = |det J| J^{-1} J^{-T}
+ *     (Sec. 4.2) in FP64,
+ *   - the factors C_st = diag_q(w_q kappa_cq G_st) (Sec. 3.1, Eq. for C_st)
+ *     with the coefficient kappa given at the quadrature points,
+ *   - element matrices A^c = sum_{s,t} B_s C_st B_t^T (Sec. 3.1, triple
+ *     products; Algorithm 1) for the mass and Poisson (stiffness) forms, as
+ *     one dense contraction per tile of cells on the tensor cores (BF16,
+ *     FP16, TF32, split TF32 or FP8 e4m3 operands, FP32 accumulation) or on
+ *     the FP64 units,
+ *   - global assembly A^g = L D L^T (Sec. 3.3, Eq. global assembly) into a
+ *     CSR matrix by a deterministic segmented reduction,
+ *   - the adjoint of L = v^T A^g u with respect to kappa at the quadrature
+ *     points and to the vertex coordinates (not in the paper).
+ *
+ * Conventions
+ *   - Every function returns an fe_status.  On failure a thread-local
+ *     message is available from fe_last_error().
+ *   - Pointers marked "device" must be CUDA device (or managed) memory on the
+ *     current device; pointers marked "host" are ordinary host memory.  The
+ *     caller owns every buffer it passes; the library never frees them and
+ *     never keeps them after the call returns.
+ *   - Compute calls are asynchronous on the plan's CUDA stream.  Errors that
+ *     kernels detect (degenerate or non-finite cells, exhausted bounded
+ *     waits) are recorded in a device status word and reported by
+ *     fe_sync_status() or by the next synchronous call.
+ *   - Element matrices are stored row-major per cell, [n_cells][n_phi][n_phi],
+ *     A[c][k][l] = a(phi_l, phi_k) on cell c (Sec. 3.1, A_ji = a(phi_i, phi_j)),
+ *     in double for FE_PREC_FP64 and in float otherwise.
+ *   - Local node order: barycentric lattice multi-indices a (|a| = p) sorted
+ *     by support size, then by the support's vertex tuple, then by a in
+ *     descending lexicographic order (vertices, edges 01,02,03,12,13,23,
+ *     faces, interior).  Reference cells: (0,0),(1,0),(0,1) and the
+ *     tetrahedron (0,0,0),(1,0,0),(0,1,0),(0,0,1) (Sec. 5.1).
+ *   - Global numbering (the paper fixes none): vertex dofs take the vertex
+ *     id; every other node has the key {(g_i, a_i) : a_i > 0} sorted by the
+ *     global vertex id g_i, and these keys are numbered from n_vertices in
+ *     increasing (support size, vertex ids, multiplicities) order.
+ */
+#ifndef FE_GB300_H
+#define FE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FE_OK = 0,
+    FE_ERR_INVALID_ARG = -1,     /* null pointer, size or enum out of range  */
+    FE_ERR_UNSUPPORTED = -2,     /* degree, cell type or size not supported  */
+    FE_ERR_DEGENERATE_CELL = -3, /* det J == 0 on some cell                   */
+    FE_ERR_NONFINITE = -4,       /* non-finite coordinate, coefficient or J   */
+    FE_ERR_OOM = -5,             /* device or host allocation failed          */
+    FE_ERR_CUDA = -6,            /* a CUDA runtime call failed                */
+    FE_ERR_TIMEOUT = -7,         /* a bounded wait inside a kernel gave up    */
+    FE_ERR_NO_DEVICE = -8        /* no CUDA device is visible                 */
+} fe_status;
+
+typedef enum { FE_TRIANGLE = 2, FE_TETRAHEDRON = 3 } fe_cell_type;
+
+/* Forms (bitmask).  Sec. 3.1: mass a(w,v) = int z w v and Poisson
+ * a(w,v) = int z grad w . grad v with coefficient z = kappa. */
+enum { FE_FORM_MASS = 1, FE_FORM_STIFFNESS = 2 };
+
+/* Contraction precisions (List 1: the storage precision u_s of C and of the
+ * tabulated operand; products and accumulation are FP32 on the tensor cores,
+ * geometry and tabulation FP64).  FE_PREC_FP64 runs the whole kernel in
+ * FP64 on the CUDA cores.  FE_PREC_TF32X3 splits each operand into a TF32
+ * head and tail and sums three TF32 products (u_s ~ 2^-21). */
+typedef enum {
+    FE_PREC_FP64 = 0,
+    FE_PREC_TF32X3 = 1,
+    FE_PREC_TF32 = 2,
+    FE_PREC_BF16 = 3,
+    FE_PREC_FP16 = 4,
+    FE_PREC_E4M3 = 5
+} fe_precision;
+#define FE_PREC_MASK(p) (1u << (unsigned)(p))
+
+/* Quadrature families for fe_quadrature_rule. */
+enum {
+    FE_QUAD_COLLAPSED_GAUSS_JACOBI = 0, /* m points per direction, exact to 2m-1 */
+    FE_QUAD_TRIANGLE_3POINT = 1         /* (1/6,1/6),(2/3,1/6),(1/6,2/3), w = 1/6 */
+};
+
+typedef struct fe_plan fe_plan;
+typedef struct fe_pattern fe_pattern;
+
+typedef struct {
+    fe_cell_type type;
+    int64_t n_vertices;
+    const double *vertices; /* host, [n_vertices][d] */
+    int64_t n_cells;
+    const int32_t *cells;   /* host, [n_cells][d+1], vertex ids */
+} fe_mesh;
+
+typedef struct {
+    int32_t n_q;
+    const double *points;   /* host, [n_q][d], reference-cell coordinates */
+    const double *weights;  /* host, [n_q] */
+} fe_quadrature;
+
+/* ---------------------------------------------------------------------- */
+/* Host helpers (no GPU needed)                                           */
+/* ---------------------------------------------------------------------- */
+
+/* Reference-cell quadrature rule (Sec. 3.1 assumes exact rules).
+ * FE_QUAD_COLLAPSED_GAUSS_JACOBI: collapsed (Duffy) product of m-point
+ * Gauss-Jacobi rules with weights (1-t)^0, (1-t)^1 (and (1-t)^2 on
+ * tetrahedra), exact to degree 2m-1, n_q = m^d, point q = ia + m (ib + m ic)
+ * with the 1-D nodes ascending; x = a(1-b)(1-c), y = b(1-c), z = c.
+ * FE_QUAD_TRIANGLE_3POINT: the degree-2 interior rule (m ignored).
+ * points/weights (host) may be NULL to query n_q only.  m in 1..32. */
+fe_status fe_quadrature_rule(fe_cell_type type, int family, int m, int32_t *n_q, double *points,
+                             double *weights);
+
+/* Continuous Lagrange dof map and CSR pattern (Sec. 3.3, assembly matrix L).
+ * cells: host [n_cells][d+1].  degree 1..8 (tetrahedra) or 1..10
+ * (triangles).  The pattern of row i is the sorted set of global dofs that
+ * share a cell with dof i; the diagonal is always present. */
+fe_status fe_pattern_create(fe_pattern **out, fe_cell_type type, int64_t n_vertices, int64_t n_cells,
+                            const int32_t *cells, int degree);
+/* n_dofs, nnz, n_phi, and the longest row; any output pointer may be NULL. */
+fe_status fe_pattern_sizes(const fe_pattern *pat, int64_t *n_dofs, int64_t *nnz, int32_t *n_phi,
+                           int32_t *max_row);
+/* Copies into host buffers: cell_dofs [n_cells][n_phi], row_ptr [n_dofs+1],
+ * col_idx [nnz].  Any output pointer may be NULL. */
+fe_status fe_pattern_copy(const fe_pattern *pat, int32_t *cell_dofs, int64_t *row_ptr, int32_t *col_idx);
+fe_status fe_pattern_destroy(fe_pattern *pat);
+
+/* Thread-local description of the last error ("" if none). */
+const char *fe_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Plans                                                                   */
+/* ---------------------------------------------------------------------- */
+
+/* Build a plan for one mesh, degree and quadrature rule (Algorithm 1, step 1
+ * and the setup of Sec. 3.3): FP64 tabulation of phi and grad phi at the
+ * rule's points (Appendix A product form), the per-precision contraction
+ * operands rounded once to the storage format (List 1, u_s), the dof map,
+ * the CSR pattern and the assembly index streams.  The plan copies the mesh
+ * and the rule to the device; the caller's host arrays are not retained.
+ * form_mask: FE_FORM_* bits the plan must serve.  prec_mask: FE_PREC_MASK()
+ * bits of the precisions the plan must serve.  cuda_stream: a cudaStream_t
+ * (NULL = legacy default stream) on which all later calls run.
+ * Synchronous.  Returns FE_ERR_UNSUPPORTED for degrees outside 1..8 on
+ * tetrahedra or 1..10 on triangles, FE_ERR_NO_DEVICE without a GPU. */
+fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const fe_quadrature *rule,
+                         unsigned form_mask, unsigned prec_mask, void *cuda_stream);
+fe_status fe_plan_destroy(fe_plan *plan);
+fe_status fe_plan_set_stream(fe_plan *plan, void *cuda_stream);
+/* Any output pointer may be NULL. */
+fe_status fe_plan_sizes(const fe_plan *plan, int64_t *n_cells, int64_t *n_vertices, int64_t *n_dofs,
+                        int64_t *nnz, int32_t *n_phi, int32_t *n_q);
+/* Device copies of the pattern: row_ptr int64 [n_dofs+1], col_idx int32 [nnz]. */
+fe_status fe_csr_pattern(const fe_plan *plan, int64_t *row_ptr, int32_t *col_idx);
+/* Device copy of the dof map, int32 [n_cells][n_phi]. */
+fe_status fe_cell_dofs(const fe_plan *plan, int32_t *cell_dofs);
+
+/* Element matrices (Algorithm 1 for every cell; Sec. 3.1).
+ * forms: FE_FORM_* bits (subset of the plan's form_mask).
+ * vertices: device [n_vertices][d] FP64, or NULL for the plan's copy.
+ * kappa: device [n_cells][n_q] FP64, the coefficient at the quadrature points.
+ * A_stiffness / A_mass: device [n_cells][n_phi][n_phi], double for
+ * FE_PREC_FP64 else float; the pointer of a form not in `forms` is ignored. */
+fe_status fe_element_matrices(fe_plan *plan, unsigned forms, fe_precision prec, const double *vertices,
+                              const double *kappa, void *A_stiffness, void *A_mass);
+
+/* Element matrices followed by global assembly A^g = L D L^T (Sec. 3.3).
+ * A_stiffness / A_mass may be NULL: the element matrices then live in a plan
+ * workspace.  csr_stiffness / csr_mass: device [nnz] values in the plan's
+ * pattern (double for FE_PREC_FP64 else float).  Each CSR value is the sum
+ * of its element entries in increasing (cell, k, l) order starting from 0,
+ * so results are bitwise reproducible. */
+fe_status fe_assemble(fe_plan *plan, unsigned forms, fe_precision prec, const double *vertices,
+                      const double *kappa, void *A_stiffness, void *A_mass, void *csr_stiffness,
+                      void *csr_mass);
+
+/* Same as fe_assemble with HOST buffers: copies kappa (host [n_cells][n_q])
+ * to the device, computes, and copies the CSR values back to the host
+ * buffers (host [nnz]; NULL skips a form's copy).  Synchronous.  Pinned host
+ * memory gives the fastest copies. */
+fe_status fe_assemble_host(fe_plan *plan, unsigned forms, fe_precision prec, const double *kappa_host,
+                           void *csr_stiffness_host, void *csr_mass_host);
+
+/* Assembly only, from caller element matrices (device, layout as above). */
+fe_status fe_assemble_elements(fe_plan *plan, unsigned forms, fe_precision prec, const void *A_stiffness,
+                               const void *A_mass, void *csr_stiffness, void *csr_mass);
+
+/* Adjoint of L = v^T A^g u for the stiffness form (not in the paper):
+ *   g_kappa[c][q] = dL/dkappa_cq = w_q |det J| (J^{-T} grad u_h(X_q)).(J^{-T} grad v_h(X_q))
+ *   g_vertices[v][i] = dL/dx_{v,i}, kappa at the quadrature points held fixed,
+ * with the geometry recomputed from the vertices (nothing stored from the
+ * forward pass).  u, v: device float [n_dofs]; vertices: device or NULL;
+ * kappa: device; g_kappa: device double [n_cells][n_q] or NULL; g_vertices:
+ * device double [n_vertices][d] or NULL (overwritten, not accumulated);
+ * L_out: device double [1] or NULL.  Computed in FP64 on the CUDA cores. */
+fe_status fe_adjoint(fe_plan *plan, const double *vertices, const double *kappa, const float *u,
+                     const float *v, double *g_kappa, double *g_vertices, double *L_out);
+
+/* Wait for the plan's stream and report the device status word (and clear it). */
+fe_status fe_sync_status(fe_plan *plan);
+
+/* Per-stage GPU times (milliseconds) of the most recent call made while
+ * timing was enabled: [0] element-matrix kernel(s), [1] assembly kernel,
+ * [2] adjoint kernel(s).  Timing uses CUDA events on the plan's stream. */
+fe_status fe_plan_enable_timing(fe_plan *plan, int enable);
+fe_status fe_plan_stage_times(fe_plan *plan, float *ms, int n);
+
+/* Number of kernel launches made by the most recent compute call. */
+fe_status fe_plan_last_launches(const fe_plan *plan, int32_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FE_GB300_H */

@@ -372,6 +372,16 @@ class Problem:
                                    row_ptr, col, col.shape[0], int(absval), vals), "assemble")
         return vals
 
+    def assemble_subset(self, A_subset, cell_ids, absval: bool = False):
+        """Assemble only the listed cells' element matrices into the full pattern."""
+        dofs, nd = self.cell_dofs()
+        row_ptr, col = self.csr_pattern()
+        sub = _c(dofs[np.asarray(cell_ids)], np.int32)
+        vals = np.zeros(col.shape[0])
+        _check(_load().fo_assemble(sub.shape[0], self.n_phi, sub.reshape(-1), _c(A_subset, np.float64).reshape(-1),
+                                   row_ptr, col, col.shape[0], int(absval), vals), "assemble_subset")
+        return vals
+
     def dof_points(self):
         """Physical coordinates of every global dof (from the cell that first lists it)."""
         dofs, nd = self.cell_dofs()

@@ -1,0 +1,260 @@
+"""PyTorch-facing binding of the C ABI.
+
+PyTorch provides device memory, streams and autograd plumbing only; every
+step of the computation runs in the library's CUDA kernels.  All names follow
+include/fe_gb300.h.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import FE_FORM_MASS, FE_FORM_STIFFNESS, PRECISIONS, check, load
+
+FORMS = {"stiffness": FE_FORM_STIFFNESS, "mass": FE_FORM_MASS}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def quadrature_rule(cell_type: str, m: int, family: int = _lib.FE_QUAD_COLLAPSED_GAUSS_JACOBI):
+    """Reference rule from the library's host helper: (points [n_q, d], weights [n_q]) float64 numpy."""
+    lib = load()
+    t = _lib.FE_TETRAHEDRON if cell_type in ("tet", "tetrahedron") else _lib.FE_TRIANGLE
+    nq = ctypes.c_int32(0)
+    check(lib.fe_quadrature_rule(t, family, m, ctypes.byref(nq), None, None), "fe_quadrature_rule")
+    d = 3 if t == _lib.FE_TETRAHEDRON else 2
+    pts = np.zeros((nq.value, d))
+    wts = np.zeros(nq.value)
+    check(lib.fe_quadrature_rule(t, family, m, ctypes.byref(nq), pts.ctypes.data, wts.ctypes.data),
+          "fe_quadrature_rule")
+    return pts, wts
+
+
+class Pattern:
+    """Host-only dof map and CSR pattern (fe_pattern_*)."""
+
+    def __init__(self, cell_type: str, n_vertices: int, cells, degree: int):
+        lib = load()
+        cells = np.ascontiguousarray(cells, dtype=np.int32)
+        t = _lib.FE_TETRAHEDRON if cell_type in ("tet", "tetrahedron") else _lib.FE_TRIANGLE
+        h = ctypes.c_void_p()
+        check(lib.fe_pattern_create(ctypes.byref(h), t, n_vertices, cells.shape[0], cells.ctypes.data, degree),
+              "fe_pattern_create")
+        self._h = h
+        nd, nnz = ctypes.c_int64(), ctypes.c_int64()
+        nph, mr = ctypes.c_int32(), ctypes.c_int32()
+        check(lib.fe_pattern_sizes(h, ctypes.byref(nd), ctypes.byref(nnz), ctypes.byref(nph), ctypes.byref(mr)))
+        self.n_dofs, self.nnz, self.n_phi, self.max_row = nd.value, nnz.value, nph.value, mr.value
+        self.n_cells = cells.shape[0]
+
+    def arrays(self):
+        dofs = np.zeros((self.n_cells, self.n_phi), dtype=np.int32)
+        rp = np.zeros(self.n_dofs + 1, dtype=np.int64)
+        ci = np.zeros(self.nnz, dtype=np.int32)
+        check(load().fe_pattern_copy(self._h, dofs.ctypes.data, rp.ctypes.data, ci.ctypes.data), "fe_pattern_copy")
+        return dofs, rp, ci
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load().fe_pattern_destroy(h)
+            self._h = None
+
+
+class Plan:
+    """One mesh, degree and quadrature rule on the current CUDA device (fe_plan_*)."""
+
+    def __init__(self, cell_type: str, vertices, cells, degree: int, points=None, weights=None,
+                 forms=("stiffness", "mass"), precisions=("bf16",), stream: torch.cuda.Stream | None = None):
+        lib = load()
+        self.cell_type = "tetrahedron" if cell_type in ("tet", "tetrahedron") else "triangle"
+        self.d = 3 if self.cell_type == "tetrahedron" else 2
+        vertices = np.ascontiguousarray(np.asarray(vertices, dtype=np.float64))
+        cells = np.ascontiguousarray(np.asarray(cells, dtype=np.int32))
+        if points is None:
+            points, weights = quadrature_rule(self.cell_type, degree + 1)
+        points = np.ascontiguousarray(points, dtype=np.float64)
+        weights = np.ascontiguousarray(weights, dtype=np.float64)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        mesh = _lib.FeMesh(_lib.FE_TETRAHEDRON if self.d == 3 else _lib.FE_TRIANGLE, vertices.shape[0],
+                           vertices.ctypes.data, cells.shape[0], cells.ctypes.data)
+        rule = _lib.FeQuadrature(weights.shape[0], points.ctypes.data, weights.ctypes.data)
+        fmask = 0
+        for f in forms:
+            fmask |= FORMS[f]
+        pmask = 0
+        for p in precisions:
+            pmask |= 1 << PRECISIONS[p]
+        h = ctypes.c_void_p()
+        check(lib.fe_plan_create(ctypes.byref(h), ctypes.byref(mesh), degree, ctypes.byref(rule), fmask, pmask,
+                                 ctypes.c_void_p(self.stream.cuda_stream)), "fe_plan_create")
+        self._h = h
+        nc, nv, nd, nnz = (ctypes.c_int64() for _ in range(4))
+        nph, nq = ctypes.c_int32(), ctypes.c_int32()
+        check(lib.fe_plan_sizes(h, ctypes.byref(nc), ctypes.byref(nv), ctypes.byref(nd), ctypes.byref(nnz),
+                                ctypes.byref(nph), ctypes.byref(nq)))
+        self.n_cells, self.n_vertices, self.n_dofs, self.nnz = nc.value, nv.value, nd.value, nnz.value
+        self.n_phi, self.n_q = nph.value, nq.value
+        self.degree = degree
+        self.forms = tuple(forms)
+        self.precisions = tuple(precisions)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    # -- helpers ----------------------------------------------------------
+    def _dtype(self, prec):
+        return torch.float64 if prec == "fp64" else torch.float32
+
+    def _forms_mask(self, forms):
+        m = 0
+        for f in forms:
+            m |= FORMS[f]
+        return m
+
+    def _check_dev(self, t, dtype, shape, name):
+        if t is None:
+            return
+        if not t.is_cuda or t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor of shape {tuple(shape)}")
+
+    def empty_elements(self, prec):
+        return torch.empty((self.n_cells, self.n_phi, self.n_phi), dtype=self._dtype(prec), device=self.device)
+
+    def empty_values(self, prec):
+        return torch.empty(self.nnz, dtype=self._dtype(prec), device=self.device)
+
+    # -- queries ------------------------------------------------------------
+    def csr_pattern(self):
+        rp = torch.empty(self.n_dofs + 1, dtype=torch.int64, device=self.device)
+        ci = torch.empty(self.nnz, dtype=torch.int32, device=self.device)
+        check(load().fe_csr_pattern(self._h, _ptr(rp), _ptr(ci)), "fe_csr_pattern")
+        return rp, ci
+
+    def cell_dofs(self):
+        out = torch.empty((self.n_cells, self.n_phi), dtype=torch.int32, device=self.device)
+        check(load().fe_cell_dofs(self._h, _ptr(out)), "fe_cell_dofs")
+        return out
+
+    # -- compute ------------------------------------------------------------
+    def element_matrices(self, kappa, forms=("stiffness", "mass"), prec="bf16", vertices=None, out=None):
+        self._check_dev(kappa, torch.float64, (self.n_cells, self.n_q), "kappa")
+        self._check_dev(vertices, torch.float64, (self.n_vertices, self.d), "vertices")
+        out = dict(out or {})
+        for f in forms:
+            if f not in out:
+                out[f] = self.empty_elements(prec)
+            self._check_dev(out[f], self._dtype(prec), (self.n_cells, self.n_phi, self.n_phi), f)
+        check(load().fe_element_matrices(self._h, self._forms_mask(forms), PRECISIONS[prec], _ptr(vertices),
+                                         _ptr(kappa), _ptr(out.get("stiffness")), _ptr(out.get("mass"))),
+              "fe_element_matrices")
+        return out
+
+    def assemble(self, kappa, forms=("stiffness", "mass"), prec="bf16", vertices=None, elements=None, out=None):
+        """CSR values per form; ``elements`` (dict) receives the element matrices if given."""
+        self._check_dev(kappa, torch.float64, (self.n_cells, self.n_q), "kappa")
+        self._check_dev(vertices, torch.float64, (self.n_vertices, self.d), "vertices")
+        out = dict(out or {})
+        for f in forms:
+            if f not in out:
+                out[f] = self.empty_values(prec)
+            self._check_dev(out[f], self._dtype(prec), (self.nnz,), f)
+        el = elements or {}
+        check(load().fe_assemble(self._h, self._forms_mask(forms), PRECISIONS[prec], _ptr(vertices), _ptr(kappa),
+                                 _ptr(el.get("stiffness")), _ptr(el.get("mass")), _ptr(out.get("stiffness")),
+                                 _ptr(out.get("mass"))), "fe_assemble")
+        return out
+
+    def assemble_elements(self, elements, prec="bf16", out=None):
+        forms = tuple(elements.keys())
+        out = dict(out or {})
+        for f in forms:
+            if f not in out:
+                out[f] = self.empty_values(prec)
+        check(load().fe_assemble_elements(self._h, self._forms_mask(forms), PRECISIONS[prec],
+                                          _ptr(elements.get("stiffness")), _ptr(elements.get("mass")),
+                                          _ptr(out.get("stiffness")), _ptr(out.get("mass"))), "fe_assemble_elements")
+        return out
+
+    def assemble_host(self, kappa_host, forms=("stiffness", "mass"), prec="bf16", out=None):
+        """End to end with host buffers: kappa (CPU float64, pinned preferred) -> CSR values (CPU)."""
+        if kappa_host.is_cuda or kappa_host.dtype != torch.float64 or not kappa_host.is_contiguous():
+            raise ValueError("kappa_host must be a contiguous CPU float64 tensor")
+        out = dict(out or {})
+        for f in forms:
+            if f not in out:
+                out[f] = torch.empty(self.nnz, dtype=self._dtype(prec), pin_memory=True)
+        check(load().fe_assemble_host(self._h, self._forms_mask(forms), PRECISIONS[prec], _ptr(kappa_host),
+                                      _ptr(out.get("stiffness")), _ptr(out.get("mass"))), "fe_assemble_host")
+        return out
+
+    def adjoint(self, kappa, u, v, vertices=None, want_kappa=True, want_vertices=True, want_L=True):
+        """(L, dL/dkappa, dL/dvertices) for L = v^T A_stiffness u, computed in FP64."""
+        self._check_dev(kappa, torch.float64, (self.n_cells, self.n_q), "kappa")
+        self._check_dev(u, torch.float32, (self.n_dofs,), "u")
+        self._check_dev(v, torch.float32, (self.n_dofs,), "v")
+        self._check_dev(vertices, torch.float64, (self.n_vertices, self.d), "vertices")
+        gk = torch.empty((self.n_cells, self.n_q), dtype=torch.float64, device=self.device) if want_kappa else None
+        gx = torch.empty((self.n_vertices, self.d), dtype=torch.float64, device=self.device) if want_vertices else None
+        L = torch.empty(1, dtype=torch.float64, device=self.device) if want_L else None
+        check(load().fe_adjoint(self._h, _ptr(vertices), _ptr(kappa), _ptr(u), _ptr(v), _ptr(gk), _ptr(gx), _ptr(L)),
+              "fe_adjoint")
+        return L, gk, gx
+
+    def sync(self):
+        check(load().fe_sync_status(self._h), "fe_sync_status")
+
+    def enable_timing(self, on=True):
+        check(load().fe_plan_enable_timing(self._h, int(on)))
+
+    def stage_times(self):
+        ms = (ctypes.c_float * 3)()
+        check(load().fe_plan_stage_times(self._h, ms, 3))
+        return list(ms)
+
+    def last_launches(self):
+        n = ctypes.c_int32()
+        check(load().fe_plan_last_launches(self._h, ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load().fe_plan_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class QuadraticForm(torch.autograd.Function):
+    """L = v^T A(kappa, vertices) u for the stiffness form of a plan.
+
+    Forward and backward both run the library's FP64 adjoint kernels
+    (fe_adjoint); the backward recomputes the geometry from the vertices.
+    Gradients flow to kappa and to the vertex coordinates (kappa at the
+    quadrature points held fixed when the vertices move); u and v are treated
+    as constants.
+    """
+
+    @staticmethod
+    def forward(ctx, kappa, vertices, u, v, plan):
+        L, _, _ = plan.adjoint(kappa, u, v, vertices=vertices, want_kappa=False, want_vertices=False)
+        ctx.save_for_backward(kappa, vertices, u, v)
+        ctx.plan = plan
+        return L[0]
+
+    @staticmethod
+    def backward(ctx, grad_L):
+        kappa, vertices, u, v = ctx.saved_tensors
+        _, gk, gx = ctx.plan.adjoint(kappa, u, v, vertices=vertices, want_L=False,
+                                     want_kappa=ctx.needs_input_grad[0], want_vertices=ctx.needs_input_grad[1])
+        gk = gk * grad_L if gk is not None else None
+        gx = gx * grad_L if gx is not None else None
+        return gk, gx, None, None, None

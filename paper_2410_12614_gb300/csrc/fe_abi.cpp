@@ -1,0 +1,619 @@
+// C ABI of the library: plan lifecycle, argument validation, device memory
+// owned by plans, kernel launches and the status / error conventions of
+// fe_gb300.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "fe_host.h"
+#include "fe_internal.h"
+
+using namespace fe;
+
+namespace {
+
+thread_local std::string g_err;
+
+fe_status fail(fe_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+fe_status cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) return fail(FE_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(FE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define FE_CUDA(call, what)                          \
+    do {                                             \
+        cudaError_t _e = (call);                     \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+int form_index(unsigned form) { return form == FE_FORM_STIFFNESS ? 0 : 1; }
+
+bool supported_degree(int d, int p) { return p >= 1 && ((d == 3 && p <= 8) || (d == 2 && p <= 10)); }
+
+}  // namespace
+
+struct fe_pattern {
+    host::Pattern P;
+};
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t b) {
+        if (p && bytes >= b) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, b ? b : 16);
+        if (e == cudaSuccess) bytes = b;
+        return e;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+struct fe_plan {
+    int d = 0, p = 0, n_phi = 0, n_q = 0, n_pairs = 0, n_sym = 0;
+    unsigned form_mask = 0, prec_mask = 0;
+    int64_t n_cells = 0, n_vertices = 0, n_dofs = 0, nnz = 0;
+    int max_row = 0;
+    cudaStream_t stream = nullptr;
+    int sms = 0;
+    DevBuf vertices, cells, weights, cell_dofs, row_ptr, col_idx, inc_ptr, inc_elem, inc_slot, vinc_ptr, vinc;
+    DevBuf phi, dphi, sym_kl, full2sym, status;
+    DevBuf img[6][2];
+    TcOperand op[6][2];
+    DevBuf ws_elem[2], ws_kappa, ws_csr[2], ws_adj_x, ws_adj_L, ws_Lsum;
+    bool timing = false;
+    cudaEvent_t ev[6] = {};
+    float stage_ms[3] = {0, 0, 0};
+    int last_launches = 0;
+    int stage_marks = 0;
+    std::vector<int> host_status;
+    ~fe_plan() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+static uint32_t idesc_for(int prec) {
+    uint32_t fmt = 0;
+    if (prec == FE_PREC_BF16) fmt = 1;
+    else if (prec == FE_PREC_TF32 || prec == FE_PREC_TF32X3) fmt = 2;
+    else fmt = 0;  // FP16, E4M3
+    uint32_t d = (1u << 4);                     // FP32 accumulator
+    d |= (fmt << 7) | (fmt << 10);              // A and B formats
+    d |= (uint32_t)(TC_M >> 4) << 24;           // M = 128
+    return d;
+}
+
+template <class T>
+static cudaError_t upload(DevBuf &b, const std::vector<T> &v, cudaStream_t s) {
+    cudaError_t e = b.alloc(sizeof(T) * v.size());
+    if (e != cudaSuccess) return e;
+    if (v.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s);
+}
+
+extern "C" {
+
+const char *fe_last_error(void) { return g_err.c_str(); }
+
+fe_status fe_quadrature_rule(fe_cell_type type, int family, int m, int32_t *n_q, double *points, double *weights) {
+    g_err.clear();
+    if (!n_q) return fail(FE_ERR_INVALID_ARG, "n_q is NULL");
+    const int d = (int)type;
+    if (d != 2 && d != 3) return fail(FE_ERR_INVALID_ARG, "unknown cell type %d", (int)type);
+    if (family == FE_QUAD_TRIANGLE_3POINT) {
+        if (d != 2) return fail(FE_ERR_INVALID_ARG, "the 3-point rule is for triangles");
+        *n_q = 3;
+        if (points && weights) {
+            const double P[6] = {1.0 / 6, 1.0 / 6, 2.0 / 3, 1.0 / 6, 1.0 / 6, 2.0 / 3};
+            for (int i = 0; i < 6; ++i) points[i] = P[i];
+            for (int i = 0; i < 3; ++i) weights[i] = 1.0 / 6;
+        }
+        return FE_OK;
+    }
+    if (family != FE_QUAD_COLLAPSED_GAUSS_JACOBI) return fail(FE_ERR_INVALID_ARG, "unknown family %d", family);
+    if (m < 1 || m > 32) return fail(FE_ERR_UNSUPPORTED, "m must lie in 1..32");
+    int nq = 1;
+    for (int i = 0; i < d; ++i) nq *= m;
+    *n_q = nq;
+    if (!points || !weights) return FE_OK;
+    std::vector<double> pts, wts;
+    if (!host::collapsed_rule(d, m, pts, wts)) return fail(FE_ERR_INVALID_ARG, "rule construction failed");
+    std::memcpy(points, pts.data(), sizeof(double) * pts.size());
+    std::memcpy(weights, wts.data(), sizeof(double) * wts.size());
+    return FE_OK;
+}
+
+fe_status fe_pattern_create(fe_pattern **out, fe_cell_type type, int64_t n_vertices, int64_t n_cells,
+                            const int32_t *cells, int degree) {
+    g_err.clear();
+    if (!out || !cells) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    const int d = (int)type;
+    if (d != 2 && d != 3) return fail(FE_ERR_INVALID_ARG, "unknown cell type %d", (int)type);
+    if (!supported_degree(d, degree)) return fail(FE_ERR_UNSUPPORTED, "degree %d not supported", degree);
+    if (n_vertices <= 0 || n_cells <= 0) return fail(FE_ERR_INVALID_ARG, "empty mesh");
+    auto pat = std::make_unique<fe_pattern>();
+    std::string err = host::build_pattern(d, degree, n_vertices, n_cells, cells, pat->P, false);
+    if (!err.empty()) return fail(FE_ERR_INVALID_ARG, "%s", err.c_str());
+    *out = pat.release();
+    return FE_OK;
+}
+
+fe_status fe_pattern_sizes(const fe_pattern *pat, int64_t *n_dofs, int64_t *nnz, int32_t *n_phi, int32_t *max_row) {
+    if (!pat) return fail(FE_ERR_INVALID_ARG, "NULL pattern");
+    if (n_dofs) *n_dofs = pat->P.n_dofs;
+    if (nnz) *nnz = pat->P.nnz;
+    if (n_phi) *n_phi = pat->P.n_phi;
+    if (max_row) *max_row = pat->P.max_row;
+    return FE_OK;
+}
+
+fe_status fe_pattern_copy(const fe_pattern *pat, int32_t *cell_dofs, int64_t *row_ptr, int32_t *col_idx) {
+    if (!pat) return fail(FE_ERR_INVALID_ARG, "NULL pattern");
+    const auto &P = pat->P;
+    if (cell_dofs) std::memcpy(cell_dofs, P.cell_dofs.data(), sizeof(int32_t) * P.cell_dofs.size());
+    if (row_ptr) std::memcpy(row_ptr, P.row_ptr.data(), sizeof(int64_t) * P.row_ptr.size());
+    if (col_idx) std::memcpy(col_idx, P.col_idx.data(), sizeof(int32_t) * P.col_idx.size());
+    return FE_OK;
+}
+
+fe_status fe_pattern_destroy(fe_pattern *pat) {
+    delete pat;
+    return FE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// plans
+// ---------------------------------------------------------------------------
+fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const fe_quadrature *rule,
+                         unsigned form_mask, unsigned prec_mask, void *cuda_stream) {
+    g_err.clear();
+    if (!out || !mesh || !rule || !mesh->vertices || !mesh->cells || !rule->points || !rule->weights)
+        return fail(FE_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    const int d = (int)mesh->type;
+    if (d != 2 && d != 3) return fail(FE_ERR_INVALID_ARG, "unknown cell type %d", (int)mesh->type);
+    if (!supported_degree(d, degree)) return fail(FE_ERR_UNSUPPORTED, "degree %d not supported for d=%d", degree, d);
+    if (mesh->n_vertices <= 0 || mesh->n_cells <= 0) return fail(FE_ERR_INVALID_ARG, "empty mesh");
+    if (rule->n_q <= 0 || rule->n_q > 4096) return fail(FE_ERR_UNSUPPORTED, "n_q must lie in 1..4096");
+    if (form_mask == 0 || (form_mask & ~3u)) return fail(FE_ERR_INVALID_ARG, "bad form mask");
+    if (prec_mask == 0 || (prec_mask & ~63u)) return fail(FE_ERR_INVALID_ARG, "bad precision mask");
+    for (int64_t i = 0; i < mesh->n_vertices * d; ++i)
+        if (!std::isfinite(mesh->vertices[i])) return fail(FE_ERR_NONFINITE, "non-finite vertex coordinate");
+    for (int i = 0; i < rule->n_q; ++i)
+        if (!std::isfinite(rule->weights[i])) return fail(FE_ERR_NONFINITE, "non-finite quadrature weight");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(FE_ERR_NO_DEVICE, "no CUDA device");
+    }
+    auto pl = std::make_unique<fe_plan>();
+    fe_plan &P = *pl;
+    P.d = d;
+    P.p = degree;
+    P.n_phi = host::n_phi(d, degree);
+    P.n_q = rule->n_q;
+    P.n_pairs = d * (d + 1) / 2;
+    P.n_sym = P.n_phi * (P.n_phi + 1) / 2;
+    P.form_mask = form_mask;
+    P.prec_mask = prec_mask;
+    P.n_cells = mesh->n_cells;
+    P.n_vertices = mesh->n_vertices;
+    P.stream = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&P.sms, cudaDevAttrMultiProcessorCount, dev);
+
+    host::Pattern pat;
+    std::string err = host::build_pattern(d, degree, mesh->n_vertices, mesh->n_cells, mesh->cells, pat, true);
+    if (!err.empty()) return fail(FE_ERR_INVALID_ARG, "%s", err.c_str());
+    P.n_dofs = pat.n_dofs;
+    P.nnz = pat.nnz;
+    P.max_row = pat.max_row;
+
+    std::vector<double> phi, dphi;
+    host::tabulate(d, degree, rule->points, rule->n_q, phi, dphi);
+
+    cudaStream_t s = P.stream;
+    std::vector<double> verts(mesh->vertices, mesh->vertices + mesh->n_vertices * d);
+    std::vector<int32_t> cl(mesh->cells, mesh->cells + mesh->n_cells * (d + 1));
+    std::vector<double> wts(rule->weights, rule->weights + rule->n_q);
+    FE_CUDA(upload(P.vertices, verts, s), "upload vertices");
+    FE_CUDA(upload(P.cells, cl, s), "upload cells");
+    FE_CUDA(upload(P.weights, wts, s), "upload weights");
+    FE_CUDA(upload(P.cell_dofs, pat.cell_dofs, s), "upload dofs");
+    FE_CUDA(upload(P.row_ptr, pat.row_ptr, s), "upload row_ptr");
+    FE_CUDA(upload(P.col_idx, pat.col_idx, s), "upload col_idx");
+    FE_CUDA(upload(P.inc_ptr, pat.inc_ptr, s), "upload inc_ptr");
+    FE_CUDA(upload(P.inc_elem, pat.inc_elem, s), "upload inc_elem");
+    FE_CUDA(upload(P.inc_slot, pat.inc_slot, s), "upload inc_slot");
+    FE_CUDA(upload(P.vinc_ptr, pat.vinc_ptr, s), "upload vinc_ptr");
+    FE_CUDA(upload(P.vinc, pat.vinc, s), "upload vinc");
+    FE_CUDA(upload(P.phi, phi, s), "upload phi");
+    FE_CUDA(upload(P.dphi, dphi, s), "upload dphi");
+    std::vector<int32_t> symkl;
+    std::vector<int16_t> f2s((size_t)P.n_phi * P.n_phi);
+    for (int k = 0; k < P.n_phi; ++k)
+        for (int l = k; l < P.n_phi; ++l) {
+            f2s[(size_t)k * P.n_phi + l] = f2s[(size_t)l * P.n_phi + k] = (int16_t)symkl.size();
+            symkl.push_back(k | (l << 16));
+        }
+    if (P.n_sym > 32767) f2s.assign(f2s.size(), 0);  // only used by single-pass shapes (n_sym <= 256)
+    FE_CUDA(upload(P.sym_kl, symkl, s), "upload sym table");
+    FE_CUDA(upload(P.full2sym, f2s, s), "upload sym map");
+    std::vector<int> zero(4, 0);
+    FE_CUDA(upload(P.status, zero, s), "status word");
+
+    for (int prec = 1; prec <= 5; ++prec) {
+        if (!(prec_mask & FE_PREC_MASK(prec))) continue;
+        for (unsigned form : {(unsigned)FE_FORM_STIFFNESS, (unsigned)FE_FORM_MASS}) {
+            if (!(form_mask & form)) continue;
+            host::OperandImage img;
+            host::build_operand(prec, (int)form, d, P.n_phi, P.n_q, phi, dphi, img);
+            const int fi = form_index(form);
+            FE_CUDA(upload(P.img[prec][fi], img.bytes, s), "upload operand image");
+            TcOperand &o = P.op[prec][fi];
+            o.img = P.img[prec][fi].as<uint8_t>();
+            o.n_kchunks = img.n_kchunks;
+            o.n_pass = img.n_pass;
+            o.NP = img.NP;
+            o.n_cols = img.n_cols;
+            o.K_blk = img.K_blk;
+            o.n_blk = img.n_blk;
+            o.p_inv_scale = (float)img.p_inv_scale;
+        }
+    }
+    FE_CUDA(cudaStreamSynchronize(s), "plan upload");
+    for (auto &e : P.ev) FE_CUDA(cudaEventCreate(&e), "event");
+    *out = pl.release();
+    return FE_OK;
+}
+
+fe_status fe_plan_destroy(fe_plan *plan) {
+    if (plan) {
+        cudaStreamSynchronize(plan->stream);
+        delete plan;
+    }
+    return FE_OK;
+}
+
+fe_status fe_plan_set_stream(fe_plan *plan, void *stream) {
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    plan->stream = static_cast<cudaStream_t>(stream);
+    return FE_OK;
+}
+
+fe_status fe_plan_sizes(const fe_plan *plan, int64_t *n_cells, int64_t *n_vertices, int64_t *n_dofs, int64_t *nnz,
+                        int32_t *n_phi, int32_t *n_q) {
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (n_cells) *n_cells = plan->n_cells;
+    if (n_vertices) *n_vertices = plan->n_vertices;
+    if (n_dofs) *n_dofs = plan->n_dofs;
+    if (nnz) *nnz = plan->nnz;
+    if (n_phi) *n_phi = plan->n_phi;
+    if (n_q) *n_q = plan->n_q;
+    return FE_OK;
+}
+
+fe_status fe_csr_pattern(const fe_plan *plan, int64_t *row_ptr, int32_t *col_idx) {
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (row_ptr)
+        FE_CUDA(cudaMemcpyAsync(row_ptr, plan->row_ptr.p, sizeof(int64_t) * (plan->n_dofs + 1),
+                                cudaMemcpyDeviceToDevice, plan->stream), "copy row_ptr");
+    if (col_idx)
+        FE_CUDA(cudaMemcpyAsync(col_idx, plan->col_idx.p, sizeof(int32_t) * plan->nnz, cudaMemcpyDeviceToDevice,
+                                plan->stream), "copy col_idx");
+    return FE_OK;
+}
+
+fe_status fe_cell_dofs(const fe_plan *plan, int32_t *cell_dofs) {
+    if (!plan || !cell_dofs) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+    FE_CUDA(cudaMemcpyAsync(cell_dofs, plan->cell_dofs.p, sizeof(int32_t) * plan->n_cells * plan->n_phi,
+                            cudaMemcpyDeviceToDevice, plan->stream), "copy dofs");
+    return FE_OK;
+}
+
+fe_status fe_plan_enable_timing(fe_plan *plan, int enable) {
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    plan->timing = enable != 0;
+    return FE_OK;
+}
+
+fe_status fe_plan_stage_times(fe_plan *plan, float *ms, int n) {
+    if (!plan || !ms) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+    if (plan->timing && plan->stage_marks) {
+        FE_CUDA(cudaStreamSynchronize(plan->stream), "timing sync");
+        for (int i = 0; i < 3; ++i) {
+            plan->stage_ms[i] = 0.f;
+            if (plan->stage_marks & (1 << i)) cudaEventElapsedTime(&plan->stage_ms[i], plan->ev[2 * i], plan->ev[2 * i + 1]);
+        }
+        plan->stage_marks = 0;
+    }
+    for (int i = 0; i < n && i < 3; ++i) ms[i] = plan->stage_ms[i];
+    return FE_OK;
+}
+
+fe_status fe_plan_last_launches(const fe_plan *plan, int32_t *launches) {
+    if (!plan || !launches) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+    *launches = plan->last_launches;
+    return FE_OK;
+}
+
+fe_status fe_sync_status(fe_plan *plan) {
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    int st = 0;
+    FE_CUDA(cudaMemcpyAsync(&st, plan->status.p, sizeof(int), cudaMemcpyDeviceToHost, plan->stream), "read status");
+    FE_CUDA(cudaStreamSynchronize(plan->stream), "sync");
+    if (st) FE_CUDA(cudaMemsetAsync(plan->status.p, 0, sizeof(int), plan->stream), "clear status");
+    if (st & ST_TIMEOUT) return fail(FE_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
+    if (st & ST_NONFINITE) return fail(FE_ERR_NONFINITE, "non-finite geometry or coefficient");
+    if (st & ST_DEGENERATE) return fail(FE_ERR_DEGENERATE_CELL, "degenerate cell (det J == 0)");
+    if (st & ST_SATURATED) return fail(FE_ERR_NONFINITE, "e4m3 operand saturated");
+    return FE_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// compute
+// ---------------------------------------------------------------------------
+static void mark(fe_plan *P, int stage, bool begin) {
+    if (!P->timing) return;
+    cudaEventRecord(P->ev[2 * stage + (begin ? 0 : 1)], P->stream);
+    if (!begin) P->stage_marks |= 1 << stage;
+}
+
+static fe_status check_call(fe_plan *plan, unsigned forms, fe_precision prec) {
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (forms == 0 || (forms & ~plan->form_mask)) return fail(FE_ERR_INVALID_ARG, "forms not served by the plan");
+    if ((int)prec < 0 || (int)prec > 5) return fail(FE_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (prec != FE_PREC_FP64 && !(plan->prec_mask & FE_PREC_MASK(prec)))
+        return fail(FE_ERR_INVALID_ARG, "precision %d not prepared by the plan", (int)prec);
+    return FE_OK;
+}
+
+static fe_status run_elements(fe_plan *P, unsigned forms, fe_precision prec, const double *vertices,
+                              const double *kappa, void *A[2], int &launches) {
+    const double *verts = vertices ? vertices : P->vertices.as<double>();
+    mark(P, 0, true);
+    if (prec == FE_PREC_FP64) {
+        for (unsigned form : {(unsigned)FE_FORM_STIFFNESS, (unsigned)FE_FORM_MASS}) {
+            if (!(forms & form)) continue;
+            F64Args a{};
+            a.vertices = verts;
+            a.cells = P->cells.as<int32_t>();
+            a.n_cells = P->n_cells;
+            a.d = P->d;
+            a.kappa = kappa;
+            a.weights = P->weights.as<double>();
+            a.n_q = P->n_q;
+            a.n_phi = P->n_phi;
+            a.tab = (form == FE_FORM_STIFFNESS) ? P->dphi.as<double>() : P->phi.as<double>();
+            a.form = (int)form;
+            a.out = static_cast<double *>(A[form_index(form)]);
+            a.status = P->status.as<int>();
+            int r = launch_f64_elements(a, P->stream);
+            if (r < 0) return cuda_fail((cudaError_t)(-r), "FP64 element kernel launch");
+            launches += r;
+        }
+    } else {
+        TcArgs a{};
+        a.vertices = verts;
+        a.cells = P->cells.as<int32_t>();
+        a.n_cells = P->n_cells;
+        a.d = P->d;
+        a.kappa = kappa;
+        a.weights = P->weights.as<double>();
+        a.n_q = P->n_q;
+        a.n_phi = P->n_phi;
+        a.n_pairs = P->n_pairs;
+        a.prec = (int)prec;
+        a.elem_bytes = host::format_of(prec).elem_bytes;
+        a.idesc = idesc_for(prec);
+        a.target_exp = host::format_of(prec).target_exp;
+        a.form_mask = 0;
+        for (unsigned form : {(unsigned)FE_FORM_STIFFNESS, (unsigned)FE_FORM_MASS}) {
+            if (!(forms & form)) continue;
+            const int fi = form_index(form);
+            a.form_mask |= 1 << fi;
+            a.op[fi] = P->op[prec][fi];
+            a.out[fi] = static_cast<float *>(A[fi]);
+        }
+        a.sym_kl = P->sym_kl.as<int32_t>();
+        a.full2sym = P->full2sym.as<int16_t>();
+        bool single = true;
+        for (int fi = 0; fi < 2; ++fi)
+            if ((a.form_mask >> fi) & 1) single = single && (a.op[fi].n_pass == 1);
+        a.staged = single ? 1 : 0;
+        a.status = P->status.as<int>();
+        a.timeout_ns = 1000000000ull;  // 1 s per CTA (a tile needs far less)
+        const size_t smem = tc_smem_bytes(a);
+        int r = launch_tc_elements(a, smem, P->stream);
+        if (r < 0) return cuda_fail((cudaError_t)(-r), "tensor-core element kernel launch");
+        launches += r;
+    }
+    mark(P, 0, false);
+    return FE_OK;
+}
+
+static fe_status ensure_ws(DevBuf &b, size_t bytes, const char *what) {
+    cudaError_t e = b.alloc(bytes);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return FE_OK;
+}
+
+static fe_status run_assembly(fe_plan *P, unsigned forms, bool fp64, const void *A[2], void *csr[2], int &launches) {
+    AsmArgs a{};
+    a.n_rows = P->n_dofs;
+    a.row_ptr = P->row_ptr.as<int64_t>();
+    a.inc_ptr = P->inc_ptr.as<int64_t>();
+    a.inc_elem = P->inc_elem.as<int32_t>();
+    a.inc_slot = P->inc_slot.as<uint16_t>();
+    a.n_phi = P->n_phi;
+    a.max_row = P->max_row;
+    int nf = 0;
+    for (int fi = 0; fi < 2; ++fi) {
+        unsigned form = fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS;
+        if (!(forms & form)) continue;
+        if (!csr[fi]) return fail(FE_ERR_INVALID_ARG, "NULL CSR output");
+        a.A[nf] = A[fi];
+        a.out[nf] = csr[fi];
+        ++nf;
+    }
+    a.n_forms = nf;
+    mark(P, 1, true);
+    int r = launch_assemble(a, fp64, P->stream);
+    if (r < 0) return cuda_fail((cudaError_t)(-r), "assembly kernel launch");
+    launches += r;
+    mark(P, 1, false);
+    return FE_OK;
+}
+
+extern "C" {
+
+fe_status fe_element_matrices(fe_plan *plan, unsigned forms, fe_precision prec, const double *vertices,
+                              const double *kappa, void *A_stiffness, void *A_mass) {
+    g_err.clear();
+    fe_status st = check_call(plan, forms, prec);
+    if (st) return st;
+    if (!kappa) return fail(FE_ERR_INVALID_ARG, "NULL kappa");
+    void *A[2] = {A_stiffness, A_mass};
+    if ((forms & FE_FORM_STIFFNESS) && !A_stiffness) return fail(FE_ERR_INVALID_ARG, "NULL stiffness output");
+    if ((forms & FE_FORM_MASS) && !A_mass) return fail(FE_ERR_INVALID_ARG, "NULL mass output");
+    int launches = 0;
+    st = run_elements(plan, forms, prec, vertices, kappa, A, launches);
+    plan->last_launches = launches;
+    return st;
+}
+
+fe_status fe_assemble(fe_plan *plan, unsigned forms, fe_precision prec, const double *vertices, const double *kappa,
+                      void *A_stiffness, void *A_mass, void *csr_stiffness, void *csr_mass) {
+    g_err.clear();
+    fe_status st = check_call(plan, forms, prec);
+    if (st) return st;
+    if (!kappa) return fail(FE_ERR_INVALID_ARG, "NULL kappa");
+    const bool fp64 = prec == FE_PREC_FP64;
+    const size_t ebytes = (fp64 ? 8 : 4) * (size_t)plan->n_cells * plan->n_phi * plan->n_phi;
+    void *A[2] = {A_stiffness, A_mass};
+    for (int fi = 0; fi < 2; ++fi) {
+        unsigned form = fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS;
+        if ((forms & form) && !A[fi]) {
+            st = ensure_ws(plan->ws_elem[fi], ebytes, "element workspace");
+            if (st) return st;
+            A[fi] = plan->ws_elem[fi].p;
+        }
+    }
+    int launches = 0;
+    st = run_elements(plan, forms, prec, vertices, kappa, A, launches);
+    if (st) return st;
+    const void *Ac[2] = {A[0], A[1]};
+    void *csr[2] = {csr_stiffness, csr_mass};
+    st = run_assembly(plan, forms, fp64, Ac, csr, launches);
+    plan->last_launches = launches;
+    return st;
+}
+
+fe_status fe_assemble_elements(fe_plan *plan, unsigned forms, fe_precision prec, const void *A_stiffness,
+                               const void *A_mass, void *csr_stiffness, void *csr_mass) {
+    g_err.clear();
+    fe_status st = check_call(plan, forms, prec);
+    if (st) return st;
+    const void *A[2] = {A_stiffness, A_mass};
+    for (int fi = 0; fi < 2; ++fi)
+        if ((forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS)) && !A[fi])
+            return fail(FE_ERR_INVALID_ARG, "NULL element matrices");
+    void *csr[2] = {csr_stiffness, csr_mass};
+    int launches = 0;
+    st = run_assembly(plan, forms, prec == FE_PREC_FP64, A, csr, launches);
+    plan->last_launches = launches;
+    return st;
+}
+
+fe_status fe_assemble_host(fe_plan *plan, unsigned forms, fe_precision prec, const double *kappa_host,
+                           void *csr_stiffness_host, void *csr_mass_host) {
+    g_err.clear();
+    fe_status st = check_call(plan, forms, prec);
+    if (st) return st;
+    if (!kappa_host) return fail(FE_ERR_INVALID_ARG, "NULL kappa");
+    const bool fp64 = prec == FE_PREC_FP64;
+    const size_t kbytes = sizeof(double) * (size_t)plan->n_cells * plan->n_q;
+    const size_t vbytes = (fp64 ? 8 : 4) * (size_t)plan->nnz;
+    st = ensure_ws(plan->ws_kappa, kbytes, "kappa workspace");
+    if (st) return st;
+    void *csr[2] = {nullptr, nullptr};
+    for (int fi = 0; fi < 2; ++fi) {
+        if (!(forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS))) continue;
+        st = ensure_ws(plan->ws_csr[fi], vbytes, "CSR workspace");
+        if (st) return st;
+        csr[fi] = plan->ws_csr[fi].p;
+    }
+    FE_CUDA(cudaMemcpyAsync(plan->ws_kappa.p, kappa_host, kbytes, cudaMemcpyHostToDevice, plan->stream), "copy kappa");
+    st = fe_assemble(plan, forms, prec, nullptr, plan->ws_kappa.as<double>(), nullptr, nullptr, csr[0], csr[1]);
+    if (st) return st;
+    void *hout[2] = {csr_stiffness_host, csr_mass_host};
+    for (int fi = 0; fi < 2; ++fi)
+        if (csr[fi] && hout[fi])
+            FE_CUDA(cudaMemcpyAsync(hout[fi], csr[fi], vbytes, cudaMemcpyDeviceToHost, plan->stream), "copy CSR");
+    return fe_sync_status(plan);
+}
+
+fe_status fe_adjoint(fe_plan *plan, const double *vertices, const double *kappa, const float *u, const float *v,
+                     double *g_kappa, double *g_vertices, double *L_out) {
+    g_err.clear();
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (!(plan->form_mask & FE_FORM_STIFFNESS)) return fail(FE_ERR_INVALID_ARG, "plan does not serve stiffness");
+    if (!kappa || !u || !v) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+    fe_status st;
+    if (g_vertices) {
+        st = ensure_ws(plan->ws_adj_x, sizeof(double) * plan->n_cells * (plan->d + 1) * plan->d, "adjoint workspace");
+        if (st) return st;
+    }
+    st = ensure_ws(plan->ws_adj_L, sizeof(double) * plan->n_cells, "adjoint workspace");
+    if (st) return st;
+    AdjArgs a{};
+    a.vertices = vertices ? vertices : plan->vertices.as<double>();
+    a.cells = plan->cells.as<int32_t>();
+    a.n_cells = plan->n_cells;
+    a.n_vertices = plan->n_vertices;
+    a.d = plan->d;
+    a.kappa = kappa;
+    a.weights = plan->weights.as<double>();
+    a.n_q = plan->n_q;
+    a.n_phi = plan->n_phi;
+    a.dphi = plan->dphi.as<double>();
+    a.cell_dofs = plan->cell_dofs.as<int32_t>();
+    a.u = u;
+    a.v = v;
+    a.g_kappa = g_kappa;
+    a.g_cell_x = g_vertices ? plan->ws_adj_x.as<double>() : nullptr;
+    a.L_cell = plan->ws_adj_L.as<double>();
+    a.status = plan->status.as<int>();
+    mark(plan, 2, true);
+    int r = launch_adjoint(a, plan->vinc_ptr.as<int64_t>(), plan->vinc.as<int32_t>(), g_vertices, L_out, plan->stream);
+    if (r < 0) return cuda_fail((cudaError_t)(-r), "adjoint kernel launch");
+    mark(plan, 2, false);
+    plan->last_launches = r;
+    return FE_OK;
+}
+
+}  // extern "C"

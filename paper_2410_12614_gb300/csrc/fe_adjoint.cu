@@ -1,0 +1,156 @@
+// Adjoint of L = v^T A^g u for the stiffness form (calculus; the paper has
+// no adjoint).  With the reference gradients of the FE functions at the
+// quadrature points, gu_q = sum_l B_{.lq} u_dof(c,l) and gv_q likewise, and
+// K = J^{-1} = C^T / det J (cofactors, recomputed here from the vertices):
+//   L_c            = sum_q w_q kappa_cq |det J| (K^T gu_q).(K^T gv_q)
+//   dL/dkappa_cq   = w_q |det J| (K^T gu_q).(K^T gv_q)
+//   S              = sum_q w_q kappa_cq gu_q gv_q^T
+//   dL_c/dJ        = |det J| [ tr(K K^T S) K^T - K^T S^T K K^T - K^T S K K^T ]
+//   dL/dx^(j)      = column j-1 of dL_c/dJ (j >= 1), minus their sum (j = 0).
+// Kernel 1 (one thread per cell, FP64) writes g_kappa, the per-cell vertex
+// contributions and L_c; kernel 2 sums the contributions of each vertex in
+// increasing cell order (vertex incidence stream, no atomics); kernel 3 sums
+// L_c in a fixed order.  Everything is deterministic.
+#include "fe_device.cuh"
+
+namespace fe {
+
+namespace {
+
+__global__ void __launch_bounds__(128) adjoint_cell_kernel(const __grid_constant__ AdjArgs a) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.n_cells) return;
+    const int d = a.d, nph = a.n_phi, nq = a.n_q;
+    CellGeom geo;
+    int st = cell_geometry(a.vertices, a.cells, c, d, geo);
+    double *gx = a.g_cell_x ? a.g_cell_x + c * (d + 1) * d : nullptr;
+    if (st) {
+        atomicOr(a.status, st);
+        if (a.g_kappa)
+            for (int q = 0; q < nq; ++q) a.g_kappa[c * nq + q] = 0.0;
+        if (gx)
+            for (int i = 0; i < (d + 1) * d; ++i) gx[i] = 0.0;
+        a.L_cell[c] = 0.0;
+        return;
+    }
+    // K = J^{-1} = C^T / det  ->  K[r][i] = C[i][r] / det
+    double K[3][3];
+    const double idet = 1.0 / geo.det;
+    for (int r = 0; r < d; ++r)
+        for (int i = 0; i < d; ++i) K[r][i] = geo.C[i * d + r] * idet;
+    double S[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double L = 0.0;
+    const int32_t *dofs = a.cell_dofs + c * nph;
+    for (int q = 0; q < nq; ++q) {
+        double gu[3] = {0, 0, 0}, gv[3] = {0, 0, 0};
+        for (int l = 0; l < nph; ++l) {
+            const int32_t g = __ldg(dofs + l);
+            const double ul = (double)__ldg(a.u + g), vl = (double)__ldg(a.v + g);
+            for (int s = 0; s < d; ++s) {
+                const double b = __ldg(a.dphi + ((size_t)s * nph + l) * nq + q);
+                gu[s] = fma(b, ul, gu[s]);
+                gv[s] = fma(b, vl, gv[s]);
+            }
+        }
+        double dot = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double pu = 0.0, pv = 0.0;
+            for (int r = 0; r < d; ++r) {
+                pu = fma(K[r][i], gu[r], pu);
+                pv = fma(K[r][i], gv[r], pv);
+            }
+            dot = fma(pu, pv, dot);
+        }
+        const double w = __ldg(a.weights + q);
+        const double kap = __ldg(a.kappa + c * nq + q);
+        if (a.g_kappa) a.g_kappa[c * nq + q] = w * geo.absdet * dot;
+        const double wk = w * kap;
+        L = fma(wk * geo.absdet, dot, L);
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) S[i][j] = fma(wk * gu[i], gv[j], S[i][j]);
+    }
+    a.L_cell[c] = L;
+    if (!gx) return;
+    double KKt[3][3], tr = 0.0;
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += K[i][k] * K[j][k];
+            KKt[i][j] = s;
+        }
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) tr += KKt[i][j] * S[j][i];
+    // M1 = S K K^T and M2 = S^T K K^T, then T = K^T (M1 + M2)
+    double dJ[3][3];
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double t = 0.0;
+            for (int r = 0; r < d; ++r) {
+                double m = 0.0;
+                for (int b = 0; b < d; ++b) m += (S[r][b] + S[b][r]) * KKt[b][j];
+                t += K[r][i] * m;
+            }
+            dJ[i][j] = geo.absdet * (tr * K[j][i] - t);
+        }
+    for (int i = 0; i < d; ++i) {
+        double sum = 0.0;
+        for (int j = 0; j < d; ++j) {
+            gx[(j + 1) * d + i] = dJ[i][j];
+            sum += dJ[i][j];
+        }
+        gx[0 * d + i] = -sum;
+    }
+}
+
+// Sum each vertex's per-cell contributions in increasing cell order.
+__global__ void vertex_gather_kernel(int64_t n_vertices, int d, const int64_t *__restrict__ vinc_ptr,
+                                     const int32_t *__restrict__ vinc, const double *__restrict__ g_cell_x,
+                                     double *__restrict__ g_vertices) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_vertices * d) return;
+    const int64_t v = t / d;
+    const int i = (int)(t - v * d);
+    double s = 0.0;
+    for (int64_t e = vinc_ptr[v]; e < vinc_ptr[v + 1]; ++e) s += g_cell_x[(int64_t)vinc[e] * d + i];
+    g_vertices[t] = s;
+}
+
+// Fixed-order sum of n values by one block.
+__global__ void ordered_sum_kernel(const double *__restrict__ x, int64_t n, double *__restrict__ out) {
+    __shared__ double part[1024];
+    const int t = threadIdx.x;
+    double s = 0.0;
+    for (int64_t i = t; i < n; i += blockDim.x) s += x[i];
+    part[t] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (t < w) part[t] += part[t + w];
+        __syncthreads();
+    }
+    if (t == 0) *out = part[0];
+}
+
+}  // namespace
+
+int launch_adjoint(const AdjArgs &a, const int64_t *vinc_ptr, const int32_t *vinc, double *g_vertices, double *L_out,
+                   cudaStream_t s) {
+    if (a.n_cells <= 0) return 0;
+    int launches = 0;
+    adjoint_cell_kernel<<<(unsigned)((a.n_cells + 127) / 128), 128, 0, s>>>(a);
+    ++launches;
+    if (g_vertices) {
+        const int64_t n = a.n_vertices * a.d;
+        vertex_gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a.n_vertices, a.d, vinc_ptr, vinc,
+                                                                          a.g_cell_x, g_vertices);
+        ++launches;
+    }
+    if (L_out) {
+        ordered_sum_kernel<<<1, 1024, 0, s>>>(a.L_cell, a.n_cells, L_out);
+        ++launches;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return -(int)e;
+    return launches;
+}
+
+}  // namespace fe

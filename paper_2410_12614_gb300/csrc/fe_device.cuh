@@ -1,0 +1,235 @@
+// Device helpers: affine simplex geometry in FP64 and thin inline-PTX
+// wrappers for mbarriers, bulk copies and the tcgen05 tensor-core
+// instructions of sm_103a.
+#pragma once
+
+#include <cstdint>
+
+#include "fe_internal.h"
+
+namespace fe {
+
+// --------------------------------------------------------------------------
+// Geometry (Sec. 4.2): J = [x1 - x0, ..., xd - x0], det J, and the Poisson
+// geometry tensor G = |det J| J^{-1} J^{-T} (Sec. 3.1).  Computed from the
+// cofactor matrix C of J: J^{-1} = C^T / det, so G = C^T C / |det J|.
+// Returns the status bits (0 if the cell is valid).
+// --------------------------------------------------------------------------
+struct CellGeom {
+    double absdet;
+    double det;
+    double C[9];   // cofactor matrix, row-major d x d
+    double G[6];   // symmetric pairs (0,0),(0,1),(0,2),(1,1),(1,2),(2,2) (d=3) or (0,0),(0,1),(1,1)
+};
+
+__device__ __forceinline__ int cell_geometry(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
+                                             int64_t c, int d, CellGeom &g) {
+    double x[4][3];
+    const int nv = d + 1;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (k < nv) {
+            int64_t v = __ldg(cells + c * nv + k);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) x[k][i] = (i < d) ? __ldg(vertices + v * d + i) : 0.0;
+        }
+    }
+    double J[3][3];
+    if (d == 3) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) J[i][j] = x[j + 1][i] - x[0][i];
+        g.C[0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        g.C[1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        g.C[2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        g.C[3] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+        g.C[4] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+        g.C[5] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+        g.C[6] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+        g.C[7] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+        g.C[8] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        g.det = J[0][0] * g.C[0] + J[0][1] * g.C[1] + J[0][2] * g.C[2];
+    } else {
+        J[0][0] = x[1][0] - x[0][0];
+        J[0][1] = x[2][0] - x[0][0];
+        J[1][0] = x[1][1] - x[0][1];
+        J[1][1] = x[2][1] - x[0][1];
+        g.C[0] = J[1][1];
+        g.C[1] = -J[1][0];
+        g.C[2] = -J[0][1];
+        g.C[3] = J[0][0];
+        g.det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    }
+    g.absdet = fabs(g.det);
+    int st = 0;
+    if (!isfinite(g.det)) st |= ST_NONFINITE;
+    else if (g.det == 0.0) st |= ST_DEGENERATE;
+    const double inv = (st == 0) ? 1.0 / g.absdet : 0.0;
+    if (d == 3) {
+        int j = 0;
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+#pragma unroll
+            for (int t = s; t < 3; ++t) {
+                g.G[j++] = (g.C[0 * 3 + s] * g.C[0 * 3 + t] + g.C[1 * 3 + s] * g.C[1 * 3 + t] +
+                            g.C[2 * 3 + s] * g.C[2 * 3 + t]) * inv;
+            }
+    } else {
+        g.G[0] = (g.C[0] * g.C[0] + g.C[2] * g.C[2]) * inv;
+        g.G[1] = (g.C[0] * g.C[1] + g.C[2] * g.C[3]) * inv;
+        g.G[2] = (g.C[1] * g.C[1] + g.C[3] * g.C[3]) * inv;
+        g.G[3] = g.G[4] = g.G[5] = 0.0;
+    }
+    return st;
+}
+
+// --------------------------------------------------------------------------
+// PTX wrappers
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false once the deadline (globaltimer ns) passes.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long deadline) {
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() > deadline) return false;
+    }
+    return true;
+}
+
+// 1-D bulk copy global -> shared memory, completion counted on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// --- tcgen05 -----------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t *holder, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(holder)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand in 128-byte swizzled
+// rows, 8-row atoms of 1024 bytes stacked along M/N (stride 1024 bytes).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t desc = 0;
+    desc |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    desc |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
+    desc |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset
+    desc |= (uint64_t)1 << 46;                      // descriptor version
+    desc |= (uint64_t)2 << 61;                      // 128-byte swizzle
+    return desc;
+}
+
+template <int KIND>  // 0: f16/bf16, 1: tf32, 2: f8f6f4
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    if constexpr (KIND == 0) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    } else if constexpr (KIND == 1) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 lanes x 32 bit, 16 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// --- conversions (round to nearest even) -----------------------------------
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ uint32_t pack_f16x2(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ uint32_t pack_e4m3x2(float lo, float hi) {
+    uint16_t r;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+// FP32 -> TF32 (10 explicit mantissa bits), round to nearest even, kept in FP32 bits.
+__device__ __forceinline__ uint32_t round_tf32(float x) {
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x7f800000u) == 0x7f800000u) return u;
+    u += 0xFFFu + ((u >> 13) & 1u);
+    return u & 0xFFFFE000u;
+}
+
+}  // namespace fe

@@ -1,0 +1,570 @@
+// Host-side plan construction for the GB300 finite-element library.
+//
+//  * Quadrature (Sec. 3.1 assumes exact rules): collapsed product of
+//    Gauss-Jacobi rules; the 1-D nodes are found by Newton's method with
+//    deflation on the three-term recurrence of the Jacobi polynomials and the
+//    weights from the classical Christoffel formula.
+//  * Reference basis (Appendix A): equispaced Lagrange nodes, product form
+//    phi_a = prod_i prod_{j<a_i} (p lambda_i - j)/(j+1), evaluated together
+//    with its gradient by forward-mode dual arithmetic (value, gradient).
+//  * Dof map: canonical numbering by mesh entity (vertices, edges, faces,
+//    cell interiors), each entity ranked by its sorted vertex ids and each
+//    node inside an entity by its multiplicities.
+//  * CSR pattern, the (row, cell)-sorted incidence stream and the column
+//    slots used by the segmented assembly (Sec. 3.3).
+//  * Contraction operands: the tabulated products of Algorithm 1 arranged as
+//    the shared B operand of one GEMM per tile of cells, rounded once to the
+//    storage format (List 1, u_s) and laid out as 128-byte-swizzled K-major
+//    tiles for the tensor cores.
+#include "fe_host.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <numeric>
+#include <thread>
+
+#include "../../include/fe_gb300.h"
+
+namespace fe {
+namespace host {
+
+unsigned hardware_threads() {
+    unsigned n = std::thread::hardware_concurrency();
+    return n == 0 ? 1u : std::min(n, 64u);
+}
+
+template <class F>
+static void parallel_for(int64_t n, F &&f) {
+    unsigned nt = hardware_threads();
+    if (n < 4096 || nt == 1) {
+        f(0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    int64_t chunk = (n + nt - 1) / nt;
+    for (unsigned t = 0; t < nt; ++t) {
+        int64_t b = t * chunk, e = std::min(n, b + chunk);
+        if (b >= e) break;
+        th.emplace_back([&f, b, e] { f(b, e); });
+    }
+    for (auto &x : th) x.join();
+}
+
+// --------------------------------------------------------------------------
+// Quadrature
+// --------------------------------------------------------------------------
+// P_n^{(alpha,0)}(x) and its derivative by the three-term recurrence.
+static void jacobi_eval(int n, double a, double x, double &p, double &dp) {
+    const double b = 0.0;
+    double p0 = 1.0, p1 = 0.5 * ((a - b) + (a + b + 2.0) * x);
+    if (n == 0) { p = 1.0; dp = 0.0; return; }
+    for (int k = 2; k <= n; ++k) {
+        double s = 2.0 * k + a + b;
+        double c1 = 2.0 * k * (k + a + b) * (s - 2.0);
+        double c2 = (s - 1.0) * (s * (s - 2.0) * x + a * a - b * b);
+        double c3 = 2.0 * (k + a - 1.0) * (k + b - 1.0) * s;
+        double p2 = (c2 * p1 - c3 * p0) / c1;
+        p0 = p1;
+        p1 = p2;
+    }
+    p = p1;
+    // (2n+a+b)(1-x^2) P_n' = n[(a-b) - (2n+a+b) x] P_n + 2(n+a)(n+b) P_{n-1}
+    double s = 2.0 * n + a + b;
+    dp = (n * ((a - b) - s * x) * p1 + 2.0 * (n + a) * (n + b) * p0) / (s * (1.0 - x * x));
+}
+
+bool gauss_jacobi(int m, int alpha, std::vector<double> &t, std::vector<double> &w) {
+    if (m < 1 || m > 64 || alpha < 0 || alpha > 2) return false;
+    const double a = alpha;
+    std::vector<double> x(m);
+    for (int i = 0; i < m; ++i) {
+        // Chebyshev-like start, refined by deflated Newton.
+        double z = -std::cos(M_PI * (i + 0.75) / (m + 0.5));
+        if (i > 0 && z <= x[i - 1]) z = x[i - 1] + 1e-3 * (1.0 - x[i - 1]);
+        for (int it = 0; it < 200; ++it) {
+            double p, dp;
+            jacobi_eval(m, a, z, p, dp);
+            double defl = 0.0;
+            for (int j = 0; j < i; ++j) defl += 1.0 / (z - x[j]);
+            double delta = p / (dp - p * defl);
+            z -= delta;
+            if (std::fabs(delta) <= 1e-17 * std::max(1.0, std::fabs(z))) break;
+        }
+        x[i] = z;
+    }
+    std::sort(x.begin(), x.end());
+    t.resize(m);
+    w.resize(m);
+    for (int i = 0; i < m; ++i) {
+        double p, dp;
+        jacobi_eval(m, a, x[i], p, dp);
+        // w = 2^{a+1} / ((1 - x^2) P_m'(x)^2) for beta = 0; mapped to [0,1] by / 2^{a+1}
+        double wx = std::ldexp(1.0, alpha + 1) / ((1.0 - x[i] * x[i]) * dp * dp);
+        t[i] = 0.5 * (1.0 + x[i]);
+        w[i] = wx / std::ldexp(1.0, alpha + 1);
+    }
+    return true;
+}
+
+bool collapsed_rule(int d, int m, std::vector<double> &pts, std::vector<double> &wts) {
+    std::vector<double> ta, wa, tb, wb, tc, wc;
+    if (!gauss_jacobi(m, 0, ta, wa) || !gauss_jacobi(m, 1, tb, wb)) return false;
+    pts.clear();
+    wts.clear();
+    if (d == 2) {
+        for (int ib = 0; ib < m; ++ib)
+            for (int ia = 0; ia < m; ++ia) {
+                pts.push_back(ta[ia] * (1.0 - tb[ib]));
+                pts.push_back(tb[ib]);
+                wts.push_back(wa[ia] * wb[ib]);
+            }
+        return true;
+    }
+    if (!gauss_jacobi(m, 2, tc, wc)) return false;
+    for (int ic = 0; ic < m; ++ic)
+        for (int ib = 0; ib < m; ++ib)
+            for (int ia = 0; ia < m; ++ia) {
+                pts.push_back(ta[ia] * (1.0 - tb[ib]) * (1.0 - tc[ic]));
+                pts.push_back(tb[ib] * (1.0 - tc[ic]));
+                pts.push_back(tc[ic]);
+                wts.push_back(wa[ia] * wb[ib] * wc[ic]);
+            }
+    return true;
+}
+
+// --------------------------------------------------------------------------
+// Reference basis
+// --------------------------------------------------------------------------
+int n_phi(int d, int p) {
+    int64_t n = 1;
+    for (int i = 1; i <= d; ++i) n = n * (p + i) / i;
+    return (int)n;
+}
+
+std::vector<int> lattice_nodes(int d, int p) {
+    std::vector<std::vector<int>> all;
+    std::vector<int> a(d + 1, 0);
+    // enumerate all multi-indices with |a| = p
+    std::function<void(int, int)> rec = [&](int i, int left) {
+        if (i == d) {
+            a[d] = left;
+            all.push_back(a);
+            return;
+        }
+        for (int v = 0; v <= left; ++v) {
+            a[i] = v;
+            rec(i + 1, left - v);
+        }
+    };
+    rec(0, p);
+    auto key_less = [d](const std::vector<int> &x, const std::vector<int> &y) {
+        std::vector<int> sx, sy;
+        for (int i = 0; i <= d; ++i) {
+            if (x[i] > 0) sx.push_back(i);
+            if (y[i] > 0) sy.push_back(i);
+        }
+        if (sx.size() != sy.size()) return sx.size() < sy.size();
+        if (sx != sy) return sx < sy;
+        return x > y;  // descending lexicographic
+    };
+    std::sort(all.begin(), all.end(), key_less);
+    std::vector<int> out;
+    for (auto &v : all) out.insert(out.end(), v.begin(), v.end());
+    return out;
+}
+
+namespace {
+struct Dual {
+    double v;
+    double g[3];
+};
+}  // namespace
+
+void tabulate(int d, int p, const double *pts, int n_q, std::vector<double> &phi, std::vector<double> &dphi) {
+    const int nph = n_phi(d, p);
+    std::vector<int> nodes = lattice_nodes(d, p);
+    phi.assign((size_t)nph * n_q, 0.0);
+    dphi.assign((size_t)d * nph * n_q, 0.0);
+    for (int q = 0; q < n_q; ++q) {
+        // barycentric coordinates as duals in the reference coordinates X
+        Dual lam[4];
+        double s = 0.0;
+        for (int i = 0; i < d; ++i) s += pts[q * d + i];
+        lam[0].v = 1.0 - s;
+        for (int k = 0; k < 3; ++k) lam[0].g[k] = (k < d) ? -1.0 : 0.0;
+        for (int i = 1; i <= d; ++i) {
+            lam[i].v = pts[q * d + i - 1];
+            for (int k = 0; k < 3; ++k) lam[i].g[k] = (k == i - 1) ? 1.0 : 0.0;
+        }
+        for (int n = 0; n < nph; ++n) {
+            Dual acc{1.0, {0.0, 0.0, 0.0}};
+            for (int i = 0; i <= d; ++i) {
+                int ai = nodes[n * (d + 1) + i];
+                for (int j = 0; j < ai; ++j) {
+                    double inv = 1.0 / (j + 1);
+                    Dual f{(p * lam[i].v - j) * inv, {p * lam[i].g[0] * inv, p * lam[i].g[1] * inv, p * lam[i].g[2] * inv}};
+                    Dual r;
+                    r.v = acc.v * f.v;
+                    for (int k = 0; k < 3; ++k) r.g[k] = acc.v * f.g[k] + f.v * acc.g[k];
+                    acc = r;
+                }
+            }
+            phi[(size_t)n * n_q + q] = acc.v;
+            for (int k = 0; k < d; ++k) dphi[((size_t)k * nph + n) * n_q + q] = acc.g[k];
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Canonical dof map by mesh entities
+// --------------------------------------------------------------------------
+namespace {
+// Lexicographic ranks of compositions of p into s positive parts.
+struct CompositionRanks {
+    int p, s;
+    std::vector<int> rank;  // indexed by base-(p+1) code of the tuple
+    int count = 0;
+    CompositionRanks(int p_, int s_) : p(p_), s(s_) {
+        int sz = 1;
+        for (int i = 0; i < s; ++i) sz *= (p + 1);
+        rank.assign(sz, -1);
+        std::vector<int> t(s);
+        std::function<void(int, int)> rec = [&](int i, int left) {
+            if (i == s - 1) {
+                if (left >= 1) {
+                    t[i] = left;
+                    rank[code(t.data())] = count++;
+                }
+                return;
+            }
+            for (int v = 1; v <= left - (s - 1 - i); ++v) {
+                t[i] = v;
+                rec(i + 1, left - v);
+            }
+        };
+        if (s >= 1 && p >= s) rec(0, p);
+    }
+    int code(const int *t) const {
+        int c = 0;
+        for (int i = 0; i < s; ++i) c = c * (p + 1) + t[i];
+        return c;
+    }
+};
+}  // namespace
+
+static std::string build_dofmap(int d, int p, int64_t n_vertices, int64_t n_cells, const int32_t *cells,
+                                std::vector<int32_t> &cell_dofs, int64_t &n_dofs) {
+    const int nv = d + 1;
+    const int nph = n_phi(d, p);
+    std::vector<int> nodes = lattice_nodes(d, p);
+    cell_dofs.assign((size_t)n_cells * nph, -1);
+    // Unique entities of sizes 2..d+1 as sorted vertex tuples.
+    std::vector<std::vector<std::array<int32_t, 4>>> ent(5);
+    for (int s = 2; s <= nv; ++s) {
+        auto &E = ent[s];
+        // subsets of size s of the local vertices
+        std::vector<std::vector<int>> subsets;
+        for (int mask = 0; mask < (1 << nv); ++mask)
+            if (__builtin_popcount(mask) == s) {
+                std::vector<int> sub;
+                for (int i = 0; i < nv; ++i)
+                    if (mask & (1 << i)) sub.push_back(i);
+                subsets.push_back(sub);
+            }
+        E.reserve((size_t)n_cells * subsets.size());
+        for (int64_t c = 0; c < n_cells; ++c)
+            for (auto &sub : subsets) {
+                std::array<int32_t, 4> t{-1, -1, -1, -1};
+                for (int i = 0; i < s; ++i) t[i] = cells[c * nv + sub[i]];
+                std::sort(t.begin(), t.begin() + s);
+                E.push_back(t);
+            }
+        std::sort(E.begin(), E.end());
+        E.erase(std::unique(E.begin(), E.end()), E.end());
+    }
+    std::vector<CompositionRanks> ranks;
+    for (int s = 0; s <= 4; ++s) ranks.emplace_back(p, s);
+    // offsets of each entity size class
+    int64_t off[6];
+    off[2] = n_vertices;
+    for (int s = 2; s <= nv; ++s) off[s + 1] = off[s] + (int64_t)ent[s].size() * ranks[s].count;
+    n_dofs = off[nv + 1];
+    if (n_dofs > INT32_MAX) return "too many degrees of freedom for int32 indices";
+    for (int64_t c = 0; c < n_cells; ++c) {
+        for (int n = 0; n < nph; ++n) {
+            const int *a = &nodes[n * nv];
+            std::array<std::pair<int32_t, int>, 4> sup;
+            int s = 0;
+            for (int i = 0; i < nv; ++i)
+                if (a[i] > 0) sup[s++] = {cells[c * nv + i], a[i]};
+            if (s == 1) {
+                cell_dofs[c * nph + n] = sup[0].first;
+                continue;
+            }
+            std::sort(sup.begin(), sup.begin() + s);
+            std::array<int32_t, 4> t{-1, -1, -1, -1};
+            int mult[4];
+            for (int i = 0; i < s; ++i) {
+                t[i] = sup[i].first;
+                mult[i] = sup[i].second;
+            }
+            auto &E = ent[s];
+            auto it = std::lower_bound(E.begin(), E.end(), t);
+            int64_t er = it - E.begin();
+            int r = ranks[s].rank[ranks[s].code(mult)];
+            cell_dofs[c * nph + n] = (int32_t)(off[s] + er * ranks[s].count + r);
+        }
+    }
+    return "";
+}
+
+std::string build_pattern(int d, int p, int64_t n_vertices, int64_t n_cells, const int32_t *cells, Pattern &P,
+                          bool with_streams) {
+    if (d != 2 && d != 3) return "cell type must be triangle or tetrahedron";
+    const int nv = d + 1;
+    for (int64_t i = 0; i < n_cells * nv; ++i)
+        if (cells[i] < 0 || cells[i] >= n_vertices) return "cell vertex index out of range";
+    for (int64_t c = 0; c < n_cells; ++c)
+        for (int i = 0; i < nv; ++i)
+            for (int j = i + 1; j < nv; ++j)
+                if (cells[c * nv + i] == cells[c * nv + j]) return "cell with a repeated vertex";
+    P.d = d;
+    P.p = p;
+    P.n_phi = n_phi(d, p);
+    P.n_vertices = n_vertices;
+    P.n_cells = n_cells;
+    const int nph = P.n_phi;
+    std::string err = build_dofmap(d, p, n_vertices, n_cells, cells, P.cell_dofs, P.n_dofs);
+    if (!err.empty()) return err;
+    const int64_t nd = P.n_dofs;
+    // incidence dof -> (c, k) with c ascending (counting sort, stable)
+    std::vector<int64_t> iptr(nd + 1, 0);
+    for (int64_t i = 0; i < n_cells * nph; ++i) iptr[P.cell_dofs[i] + 1]++;
+    for (int64_t i = 0; i < nd; ++i) iptr[i + 1] += iptr[i];
+    std::vector<int32_t> ielem((size_t)n_cells * nph);
+    {
+        std::vector<int64_t> fill(iptr.begin(), iptr.end() - 1);
+        for (int64_t c = 0; c < n_cells; ++c)
+            for (int k = 0; k < nph; ++k) ielem[fill[P.cell_dofs[c * nph + k]]++] = (int32_t)(c * nph + k);
+    }
+    if ((int64_t)n_cells * nph > INT32_MAX) return "too many element rows for int32 indices";
+    // rows: sorted unique union of the dofs of the incident cells
+    std::vector<int64_t> rlen(nd, 0);
+    unsigned nt = hardware_threads();
+    std::vector<std::vector<int32_t>> parts(nt);
+    std::vector<int64_t> part_begin(nt + 1, nd);
+    {
+        int64_t chunk = (nd + nt - 1) / nt;
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nt; ++t) {
+            int64_t b = std::min<int64_t>(nd, t * chunk), e = std::min<int64_t>(nd, b + chunk);
+            part_begin[t] = b;
+            th.emplace_back([&, t, b, e] {
+                std::vector<int32_t> buf;
+                auto &out = parts[t];
+                for (int64_t i = b; i < e; ++i) {
+                    buf.clear();
+                    for (int64_t j = iptr[i]; j < iptr[i + 1]; ++j) {
+                        int64_t c = ielem[j] / nph;
+                        buf.insert(buf.end(), &P.cell_dofs[c * nph], &P.cell_dofs[c * nph] + nph);
+                    }
+                    std::sort(buf.begin(), buf.end());
+                    buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+                    rlen[i] = (int64_t)buf.size();
+                    out.insert(out.end(), buf.begin(), buf.end());
+                }
+            });
+        }
+        for (auto &x : th) x.join();
+    }
+    P.row_ptr.assign(nd + 1, 0);
+    for (int64_t i = 0; i < nd; ++i) P.row_ptr[i + 1] = P.row_ptr[i] + rlen[i];
+    P.nnz = P.row_ptr[nd];
+    P.col_idx.resize(P.nnz);
+    int64_t maxr = 0;
+    for (int64_t i = 0; i < nd; ++i) maxr = std::max(maxr, rlen[i]);
+    P.max_row = (int)maxr;
+    {
+        int64_t pos = 0;
+        for (unsigned t = 0; t < nt; ++t) {
+            std::copy(parts[t].begin(), parts[t].end(), P.col_idx.begin() + pos);
+            pos += (int64_t)parts[t].size();
+            std::vector<int32_t>().swap(parts[t]);
+        }
+    }
+    if (!with_streams) return "";
+    if (maxr > 65535) return "row longer than 65535 entries: slot stream would overflow";
+    P.inc_ptr = iptr;
+    P.inc_elem = ielem;
+    P.inc_slot.resize((size_t)n_cells * nph * nph);
+    parallel_for(nd, [&](int64_t b, int64_t e) {
+        for (int64_t i = b; i < e; ++i) {
+            const int32_t *cb = P.col_idx.data() + P.row_ptr[i];
+            const int32_t *ce = P.col_idx.data() + P.row_ptr[i + 1];
+            for (int64_t j = iptr[i]; j < iptr[i + 1]; ++j) {
+                int64_t c = ielem[j] / nph;
+                for (int l = 0; l < nph; ++l) {
+                    const int32_t *it = std::lower_bound(cb, ce, P.cell_dofs[c * nph + l]);
+                    P.inc_slot[(size_t)j * nph + l] = (uint16_t)(it - cb);
+                }
+            }
+        }
+    });
+    // vertex incidence for the adjoint's vertex scatter
+    P.vinc_ptr.assign(n_vertices + 1, 0);
+    for (int64_t i = 0; i < n_cells * nv; ++i) P.vinc_ptr[cells[i] + 1]++;
+    for (int64_t i = 0; i < n_vertices; ++i) P.vinc_ptr[i + 1] += P.vinc_ptr[i];
+    P.vinc.resize((size_t)n_cells * nv);
+    {
+        std::vector<int64_t> fill(P.vinc_ptr.begin(), P.vinc_ptr.end() - 1);
+        for (int64_t c = 0; c < n_cells; ++c)
+            for (int j = 0; j < nv; ++j) P.vinc[fill[cells[c * nv + j]]++] = (int32_t)(c * nv + j);
+    }
+    return "";
+}
+
+// --------------------------------------------------------------------------
+// Storage formats and operand images
+// --------------------------------------------------------------------------
+double round_to_format(double x, int mbits, int emin, double maxfinite) {
+    if (x == 0.0 || !std::isfinite(x)) return x;
+    int e;
+    std::frexp(x, &e);
+    int E = e - 1;
+    if (E < emin) E = emin;
+    double ulp = std::ldexp(1.0, E - mbits);
+    double r = std::nearbyint(x / ulp) * ulp;
+    if (std::fabs(r) > maxfinite) r = std::copysign(maxfinite, x);
+    return r;
+}
+
+Format format_of(int prec) {
+    switch (prec) {
+        case FE_PREC_BF16: return {2, 7, -126, 3.3895313892515355e38, 1};
+        case FE_PREC_FP16: return {2, 10, -14, 65504.0, 15};
+        case FE_PREC_TF32:
+        case FE_PREC_TF32X3: return {4, 10, -126, 3.4028234663852886e38, 1};
+        case FE_PREC_E4M3: return {1, 3, -6, 448.0, 8};
+        default: return {8, 52, -1022, 1.7976931348623157e308, 1};
+    }
+}
+
+uint32_t encode(int prec, double r) {
+    if (prec == FE_PREC_BF16 || prec == FE_PREC_TF32 || prec == FE_PREC_TF32X3) {
+        float f = (float)r;  // exact: r is representable
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        return prec == FE_PREC_BF16 ? (u >> 16) : u;
+    }
+    uint32_t sign = std::signbit(r) ? 1u : 0u;
+    double a = std::fabs(r);
+    if (prec == FE_PREC_FP16) {
+        if (a == 0.0) return sign << 15;
+        int e;
+        std::frexp(a, &e);
+        int E = e - 1;
+        if (E < -14) return (sign << 15) | (uint32_t)std::lrint(a * std::ldexp(1.0, 24));
+        uint32_t mant = (uint32_t)std::lrint((a * std::ldexp(1.0, -E) - 1.0) * 1024.0);
+        return (sign << 15) | ((uint32_t)(E + 15) << 10) | mant;
+    }
+    // e4m3
+    if (a == 0.0) return sign << 7;
+    int e;
+    std::frexp(a, &e);
+    int E = e - 1;
+    if (E < -6) return (sign << 7) | (uint32_t)std::lrint(a * std::ldexp(1.0, 9));
+    uint32_t mant = (uint32_t)std::lrint((a * std::ldexp(1.0, -E) - 1.0) * 8.0);
+    return (sign << 7) | ((uint32_t)(E + 7) << 3) | mant;
+}
+
+void build_operand(int prec, int form, int d, int n_phi_, int n_q, const std::vector<double> &phi,
+                   const std::vector<double> &dphi, OperandImage &img) {
+    const Format F = format_of(prec);
+    const int eb = F.elem_bytes;
+    const int KCE = 128 / eb;
+    const bool stiff = (form == FE_FORM_STIFFNESS);
+    const int n_pairs = stiff ? d * (d + 1) / 2 : 1;
+    const int K_true = n_q * n_pairs;
+    const int n_sym = n_phi_ * (n_phi_ + 1) / 2;
+    std::vector<std::pair<int, int>> pairs;
+    for (int s = 0; s < d; ++s)
+        for (int t = s; t < d; ++t) pairs.push_back({s, t});
+    std::vector<std::pair<int, int>> sym;
+    for (int k = 0; k < n_phi_; ++k)
+        for (int l = k; l < n_phi_; ++l) sym.push_back({k, l});
+    auto B = [&](int s, int k, int q) { return dphi[((size_t)s * n_phi_ + k) * n_q + q]; };
+    // P[K][col] in FP64: the product of two tabulated factors (Sec. 3.1, triple products)
+    std::vector<double> Pv((size_t)K_true * n_sym);
+    double maxabs = 0.0;
+    for (int q = 0; q < n_q; ++q)
+        for (int j = 0; j < n_pairs; ++j) {
+            int K = q * n_pairs + j;
+            for (int c = 0; c < n_sym; ++c) {
+                int k = sym[c].first, l = sym[c].second;
+                double v;
+                if (stiff) {
+                    int s = pairs[j].first, t = pairs[j].second;
+                    v = B(s, k, q) * B(t, l, q);
+                    if (s != t) v += B(t, k, q) * B(s, l, q);
+                } else {
+                    v = phi[(size_t)k * n_q + q] * phi[(size_t)l * n_q + q];
+                }
+                Pv[(size_t)K * n_sym + c] = v;
+                maxabs = std::max(maxabs, std::fabs(v));
+            }
+        }
+    int eP = 0;
+    if (prec == FE_PREC_FP16 || prec == FE_PREC_E4M3) {
+        int e;
+        std::frexp(maxabs, &e);
+        eP = F.target_exp - e;
+    }
+    img.p_inv_scale = std::ldexp(1.0, -eP);
+    img.n_blk = (prec == FE_PREC_TF32X3) ? 3 : 1;
+    img.K_blk = (K_true + KCE - 1) / KCE * KCE;
+    img.n_kchunks = img.n_blk * img.K_blk / KCE;
+    img.n_cols = n_sym;
+    if (n_sym <= 256) {
+        img.NP = (n_sym + 15) / 16 * 16;
+        img.n_pass = 1;
+    } else {
+        img.NP = 256;
+        img.n_pass = (n_sym + 255) / 256;
+    }
+    // rounded values (and TF32 tails)
+    std::vector<double> hi(Pv.size()), lo;
+    for (size_t i = 0; i < Pv.size(); ++i) hi[i] = round_to_format(std::ldexp(Pv[i], eP), F.mbits, F.emin, F.maxfinite);
+    if (img.n_blk == 3) {
+        lo.resize(Pv.size());
+        for (size_t i = 0; i < Pv.size(); ++i) lo[i] = round_to_format(std::ldexp(Pv[i], eP) - hi[i], F.mbits, F.emin, F.maxfinite);
+    }
+    const size_t block = (size_t)img.NP * 128;
+    img.bytes.assign(block * img.n_kchunks * img.n_pass, 0);
+    for (int n = 0; n < img.n_pass; ++n)
+        for (int kc = 0; kc < img.n_kchunks; ++kc) {
+            uint8_t *base = img.bytes.data() + ((size_t)n * img.n_kchunks + kc) * block;
+            for (int r = 0; r < img.NP; ++r) {
+                int col = n * img.NP + r;
+                for (int e = 0; e < KCE; ++e) {
+                    int Kg = kc * KCE + e;
+                    int blk = Kg / img.K_blk, Kin = Kg % img.K_blk;
+                    double v = 0.0;
+                    if (col < n_sym && Kin < K_true) {
+                        const std::vector<double> &src = (blk == 1) ? lo : hi;
+                        v = src[(size_t)Kin * n_sym + col];
+                    }
+                    uint32_t bits = encode(prec, v);
+                    int byte = e * eb;
+                    size_t off = (size_t)(r >> 3) * 1024 + (r & 7) * 128 + ((((byte >> 4) ^ (r & 7)) & 7) << 4) + (byte & 15);
+                    std::memcpy(base + off, &bits, eb);  // little-endian low bytes
+                }
+            }
+        }
+}
+
+}  // namespace host
+}  // namespace fe

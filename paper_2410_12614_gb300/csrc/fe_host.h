@@ -1,0 +1,71 @@
+// Host-side plan construction: quadrature, reference basis, dof map, CSR
+// pattern, assembly index streams and the packed contraction operands.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace fe {
+namespace host {
+
+// Collapsed Gauss-Jacobi rule (see fe_quadrature_rule in the public header).
+bool gauss_jacobi(int m, int alpha, std::vector<double> &t, std::vector<double> &w);
+bool collapsed_rule(int d, int m, std::vector<double> &pts, std::vector<double> &wts);
+
+int n_phi(int d, int p);
+// Barycentric multi-indices of the local nodes, [n_phi][d+1], local order.
+std::vector<int> lattice_nodes(int d, int p);
+// phi [n_phi][n_q] and dphi [d][n_phi][n_q] at the points [n_q][d], FP64.
+void tabulate(int d, int p, const double *pts, int n_q, std::vector<double> &phi, std::vector<double> &dphi);
+
+struct Pattern {
+    int d = 0, p = 0, n_phi = 0;
+    int64_t n_vertices = 0, n_cells = 0, n_dofs = 0, nnz = 0;
+    int max_row = 0;
+    std::vector<int32_t> cell_dofs;   // [n_cells][n_phi]
+    std::vector<int64_t> row_ptr;     // [n_dofs+1]
+    std::vector<int32_t> col_idx;     // [nnz]
+    // assembly index streams (built on demand)
+    std::vector<int64_t> inc_ptr;     // [n_dofs+1]
+    std::vector<int32_t> inc_elem;    // c * n_phi + k, sorted by (dof, c)
+    std::vector<uint16_t> inc_slot;   // [n_inc][n_phi]
+    // vertex -> (cell, local vertex) incidence for the adjoint scatter
+    std::vector<int64_t> vinc_ptr;    // [n_vertices+1]
+    std::vector<int32_t> vinc;        // c * (d+1) + j, sorted by (vertex, c)
+};
+
+// Returns "" on success, else an error message.
+std::string build_pattern(int d, int p, int64_t n_vertices, int64_t n_cells, const int32_t *cells, Pattern &out,
+                          bool with_streams);
+
+// Round x to a binary format with `mbits` explicit mantissa bits, minimum
+// normal exponent `emin` and largest finite value `maxfinite`
+// (round-to-nearest-even, gradual underflow, saturating at +-maxfinite).
+double round_to_format(double x, int mbits, int emin, double maxfinite);
+
+// Storage formats of the contraction operands.
+struct Format {
+    int elem_bytes;
+    int mbits;
+    int emin;
+    double maxfinite;
+    int target_exp;   // scale the largest magnitude into [2^(t-1), 2^t)
+};
+Format format_of(int prec);
+// Bit pattern of an exactly representable value (as produced by round_to_format).
+uint32_t encode(int prec, double r);
+
+// Build the swizzled operand image of one form (see fe_plan.cpp).
+struct OperandImage {
+    std::vector<uint8_t> bytes;
+    int n_kchunks = 0, n_pass = 0, NP = 0, n_cols = 0, K_blk = 0, n_blk = 1;
+    double p_inv_scale = 1.0;
+};
+void build_operand(int prec, int form, int d, int n_phi, int n_q, const std::vector<double> &phi,
+                   const std::vector<double> &dphi, OperandImage &img);
+
+unsigned hardware_threads();
+
+}  // namespace host
+}  // namespace fe

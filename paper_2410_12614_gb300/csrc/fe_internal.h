@@ -1,0 +1,124 @@
+// Internal declarations shared by the host plan builder (fe_plan.cpp,
+// fe_abi.cpp) and the CUDA kernels.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fe_gb300.h"
+
+namespace fe {
+
+// Device status word bits (set by kernels with atomicOr, read by fe_sync_status).
+enum : int {
+    ST_DEGENERATE = 1,
+    ST_NONFINITE = 2,
+    ST_TIMEOUT = 4,
+    ST_SATURATED = 8,
+};
+
+// Tile of the tensor-core element kernel: 128 cells on the MMA M dimension.
+constexpr int TC_M = 128;
+constexpr int TC_THREADS = 128;
+constexpr int TC_STAGES = 2;
+constexpr int TC_CHUNK_BYTES = 128;      // one 128B-swizzled K-major row per chunk
+constexpr int TC_MAX_NP = 256;           // N of one MMA pass
+constexpr int MAX_FORMS = 2;             // 0 = stiffness, 1 = mass
+
+// Operand description of one form in one precision.
+struct TcOperand {
+    const uint8_t *img = nullptr;  // [n_pass][n_kchunks][NP][128 B] swizzled images
+    int n_kchunks = 0;             // K chunks of 128 bytes
+    int n_pass = 0;                // N passes
+    int NP = 0;                    // N per pass (multiple of 16, <= 256)
+    int n_cols = 0;                // valid sym columns (n_sym)
+    int K_blk = 0;                 // K elements per block (padded to the chunk)
+    int n_blk = 1;                 // 1, or 3 for split TF32
+    float p_inv_scale = 1.f;       // 2^-e_P
+};
+
+struct TcArgs {
+    const double *vertices;
+    const int32_t *cells;
+    int64_t n_cells;
+    int d;
+    const double *kappa;
+    const double *weights;
+    int n_q;
+    int n_phi;
+    int n_pairs;      // d(d+1)/2
+    int prec;         // fe_precision
+    int elem_bytes;   // storage bytes per operand element
+    uint32_t idesc;   // instruction descriptor without the N field
+    int target_exp;   // per-cell scale target: max|C| * 2^e in [2^(t-1), 2^t)
+    int form_mask;    // bit 0 stiffness, bit 1 mass (internal order)
+    TcOperand op[MAX_FORMS];
+    float *out[MAX_FORMS];
+    const int32_t *sym_kl;     // [n_sym_pad] k | l << 16
+    const int16_t *full2sym;   // [n_phi * n_phi]
+    int staged;                // 1: staged coalesced epilogue (single pass)
+    int *status;
+    unsigned long long timeout_ns;
+};
+
+struct F64Args {
+    const double *vertices;
+    const int32_t *cells;
+    int64_t n_cells;
+    int d;
+    const double *kappa;
+    const double *weights;
+    int n_q;
+    int n_phi;
+    const double *tab;   // stiffness: dphi [d][n_phi][n_q]; mass: phi [n_phi][n_q]
+    int form;            // FE_FORM_MASS or FE_FORM_STIFFNESS
+    double *out;
+    int tc;              // cells per block
+    int qc;              // quadrature points per chunk
+    int *status;
+};
+
+struct AsmArgs {
+    int64_t n_rows;
+    const int64_t *row_ptr;
+    const int64_t *inc_ptr;    // [n_rows + 1] into inc_elem
+    const int32_t *inc_elem;   // element-row ids c * n_phi + k, sorted by (row, c)
+    const uint16_t *inc_slot;  // [n_inc][n_phi] position of dof(c,l) inside the row
+    int n_phi;
+    int n_forms;
+    const void *A[MAX_FORMS];
+    void *out[MAX_FORMS];
+    int max_row;
+    int warps_per_block;
+};
+
+struct AdjArgs {
+    const double *vertices;
+    const int32_t *cells;
+    int64_t n_cells;
+    int64_t n_vertices;
+    int d;
+    const double *kappa;
+    const double *weights;
+    int n_q;
+    int n_phi;
+    const double *dphi;       // [d][n_phi][n_q]
+    const int32_t *cell_dofs; // [n_cells][n_phi]
+    const float *u;
+    const float *v;
+    double *g_kappa;
+    double *g_cell_x;         // per-cell vertex gradients [n_cells][d+1][d] (scratch)
+    double *L_cell;           // per-cell L contribution [n_cells] (scratch)
+    int *status;
+};
+
+// Kernel launchers (defined in the .cu files).  Return the number of
+// kernel launches made, or a negative cudaError_t on launch failure.
+int launch_tc_elements(const TcArgs &a, size_t smem_bytes, cudaStream_t s);
+size_t tc_smem_bytes(const TcArgs &a);
+int launch_f64_elements(const F64Args &a, cudaStream_t s);
+int launch_assemble(const AsmArgs &a, bool fp64, cudaStream_t s);
+int launch_adjoint(const AdjArgs &a, const int64_t *vert_inc_ptr, const int32_t *vert_inc, double *g_vertices,
+                   double *L_out, cudaStream_t s);
+
+}  // namespace fe
