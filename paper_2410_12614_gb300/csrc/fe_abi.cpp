@@ -1,6 +1,7 @@
 // C ABI of the library: plan lifecycle, argument validation, device memory
 // owned by plans, kernel launches and the status / error conventions of
 // fe_gb300.h.
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -224,6 +225,8 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&P.sms, cudaDevAttrMultiProcessorCount, dev);
 
+    if ((int64_t)mesh->n_cells * P.n_phi * P.n_phi >= INT32_MAX)
+        return fail(FE_ERR_UNSUPPORTED, "n_cells * n_phi^2 must stay below 2^31 (32-bit element offsets)");
     host::Pattern pat;
     std::string err = host::build_pattern(d, degree, mesh->n_vertices, mesh->n_cells, mesh->cells, pat, true);
     if (!err.empty()) return fail(FE_ERR_INVALID_ARG, "%s", err.c_str());
@@ -275,10 +278,11 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
             TcOperand &o = P.op[prec][fi];
             o.img = P.img[prec][fi].as<uint8_t>();
             o.n_kchunks = img.n_kchunks;
+            o.n_qw = img.n_qw;
+            o.n_pairs = img.n_pairs;
             o.n_pass = img.n_pass;
             o.NP = img.NP;
             o.n_cols = img.n_cols;
-            o.K_blk = img.K_blk;
             o.n_blk = img.n_blk;
             o.p_inv_scale = (float)img.p_inv_scale;
         }

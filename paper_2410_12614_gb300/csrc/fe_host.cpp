@@ -525,8 +525,9 @@ void build_operand(int prec, int form, int d, int n_phi_, int n_q, const std::ve
     }
     img.p_inv_scale = std::ldexp(1.0, -eP);
     img.n_blk = (prec == FE_PREC_TF32X3) ? 3 : 1;
-    img.K_blk = (K_true + KCE - 1) / KCE * KCE;
-    img.n_kchunks = img.n_blk * img.K_blk / KCE;
+    img.n_pairs = n_pairs;
+    img.n_qw = (n_q + KCE - 1) / KCE;
+    img.n_kchunks = img.n_qw * n_pairs * img.n_blk;
     img.n_cols = n_sym;
     if (n_sym <= 256) {
         img.NP = (n_sym + 15) / 16 * 16;
@@ -542,20 +543,23 @@ void build_operand(int prec, int form, int d, int n_phi_, int n_q, const std::ve
         lo.resize(Pv.size());
         for (size_t i = 0; i < Pv.size(); ++i) lo[i] = round_to_format(std::ldexp(Pv[i], eP) - hi[i], F.mbits, F.emin, F.maxfinite);
     }
+    (void)K_true;
     const size_t block = (size_t)img.NP * 128;
     img.bytes.assign(block * img.n_kchunks * img.n_pass, 0);
     for (int n = 0; n < img.n_pass; ++n)
-        for (int kc = 0; kc < img.n_kchunks; ++kc) {
-            uint8_t *base = img.bytes.data() + ((size_t)n * img.n_kchunks + kc) * block;
+        for (int ch = 0; ch < img.n_kchunks; ++ch) {
+            const int qw = ch / (n_pairs * img.n_blk);
+            const int j = (ch / img.n_blk) % n_pairs;
+            const int blk = ch % img.n_blk;
+            uint8_t *base = img.bytes.data() + ((size_t)n * img.n_kchunks + ch) * block;
             for (int r = 0; r < img.NP; ++r) {
                 int col = n * img.NP + r;
                 for (int e = 0; e < KCE; ++e) {
-                    int Kg = kc * KCE + e;
-                    int blk = Kg / img.K_blk, Kin = Kg % img.K_blk;
+                    const int q = qw * KCE + e;
                     double v = 0.0;
-                    if (col < n_sym && Kin < K_true) {
-                        const std::vector<double> &src = (blk == 1) ? lo : hi;
-                        v = src[(size_t)Kin * n_sym + col];
+                    if (col < n_sym && q < n_q) {
+                        const std::vector<double> &src = (blk == 1) ? lo : hi;  // C_hi P_hi, C_hi P_lo, C_lo P_hi
+                        v = src[(size_t)(q * n_pairs + j) * n_sym + col];
                     }
                     uint32_t bits = encode(prec, v);
                     int byte = e * eb;

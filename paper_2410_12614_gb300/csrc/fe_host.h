@@ -59,7 +59,7 @@ uint32_t encode(int prec, double r);
 // Build the swizzled operand image of one form (see fe_plan.cpp).
 struct OperandImage {
     std::vector<uint8_t> bytes;
-    int n_kchunks = 0, n_pass = 0, NP = 0, n_cols = 0, K_blk = 0, n_blk = 1;
+    int n_kchunks = 0, n_qw = 0, n_pairs = 1, n_pass = 0, NP = 0, n_cols = 0, n_blk = 1;
     double p_inv_scale = 1.0;
 };
 void build_operand(int prec, int form, int d, int n_phi, int n_q, const std::vector<double> &phi,

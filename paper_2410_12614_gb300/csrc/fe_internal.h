@@ -19,21 +19,26 @@ enum : int {
 
 // Tile of the tensor-core element kernel: 128 cells on the MMA M dimension.
 constexpr int TC_M = 128;
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;        // two threads per cell
 constexpr int TC_STAGES = 2;
 constexpr int TC_CHUNK_BYTES = 128;      // one 128B-swizzled K-major row per chunk
 constexpr int TC_MAX_NP = 256;           // N of one MMA pass
 constexpr int MAX_FORMS = 2;             // 0 = stiffness, 1 = mass
 
 // Operand description of one form in one precision.
+// K is split into 128-byte chunks; chunk ch holds the quadrature window
+// qw (KCE = 128/elem_bytes consecutive points) of pair j and split block
+// blk, ch = (qw * n_pairs + j) * n_blk + blk.  Each chunk of the shared
+// operand is stored as an NP x 128 B swizzled K-major tile.
 struct TcOperand {
     const uint8_t *img = nullptr;  // [n_pass][n_kchunks][NP][128 B] swizzled images
     int n_kchunks = 0;             // K chunks of 128 bytes
+    int n_qw = 0;                  // quadrature windows
+    int n_pairs = 1;               // symmetric (s,t) pairs (stiffness) or 1 (mass)
     int n_pass = 0;                // N passes
     int NP = 0;                    // N per pass (multiple of 16, <= 256)
     int n_cols = 0;                // valid sym columns (n_sym)
-    int K_blk = 0;                 // K elements per block (padded to the chunk)
-    int n_blk = 1;                 // 1, or 3 for split TF32
+    int n_blk = 1;                 // 1, or 3 for split TF32 (head, head, tail)
     float p_inv_scale = 1.f;       // 2^-e_P
 };
 
