@@ -76,7 +76,8 @@ struct fe_plan {
     int max_row = 0;
     cudaStream_t stream = nullptr;
     int sms = 0;
-    DevBuf vertices, cells, weights, cell_dofs, row_ptr, col_idx, inc_ptr, inc_elem, inc_slot, vinc_ptr, vinc;
+    DevBuf vertices, cells, weights, cell_dofs, row_ptr, col_idx, inc_ptr, inc_elem, vinc_ptr, vinc;
+    DevBuf contrib_cnt, contrib_base, contrib_code;
     DevBuf phi, dphi, sym_kl, full2sym, status;
     DevBuf img[6][2];
     TcOperand op[6][2];
@@ -249,7 +250,9 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
     FE_CUDA(upload(P.col_idx, pat.col_idx, s), "upload col_idx");
     FE_CUDA(upload(P.inc_ptr, pat.inc_ptr, s), "upload inc_ptr");
     FE_CUDA(upload(P.inc_elem, pat.inc_elem, s), "upload inc_elem");
-    FE_CUDA(upload(P.inc_slot, pat.inc_slot, s), "upload inc_slot");
+    FE_CUDA(upload(P.contrib_cnt, pat.contrib_cnt, s), "upload contribution counts");
+    FE_CUDA(upload(P.contrib_base, pat.contrib_base, s), "upload contribution bases");
+    FE_CUDA(upload(P.contrib_code, pat.contrib_code, s), "upload contribution codes");
     FE_CUDA(upload(P.vinc_ptr, pat.vinc_ptr, s), "upload vinc_ptr");
     FE_CUDA(upload(P.vinc, pat.vinc, s), "upload vinc");
     FE_CUDA(upload(P.phi, phi, s), "upload phi");
@@ -445,10 +448,7 @@ static fe_status run_elements(fe_plan *P, unsigned forms, fe_precision prec, con
         }
         a.sym_kl = P->sym_kl.as<int32_t>();
         a.full2sym = P->full2sym.as<int16_t>();
-        bool single = true;
-        for (int fi = 0; fi < 2; ++fi)
-            if ((a.form_mask >> fi) & 1) single = single && (a.op[fi].n_pass == 1);
-        a.staged = single ? 1 : 0;
+        a.staged = tc_can_stage(a) ? 1 : 0;
         a.status = P->status.as<int>();
         a.timeout_ns = 1000000000ull;  // 1 s per CTA (a tile needs far less)
         const size_t smem = tc_smem_bytes(a);
@@ -472,7 +472,10 @@ static fe_status run_assembly(fe_plan *P, unsigned forms, bool fp64, const void 
     a.row_ptr = P->row_ptr.as<int64_t>();
     a.inc_ptr = P->inc_ptr.as<int64_t>();
     a.inc_elem = P->inc_elem.as<int32_t>();
-    a.inc_slot = P->inc_slot.as<uint16_t>();
+    a.inc_slot = nullptr;
+    a.contrib_cnt = P->contrib_cnt.as<uint8_t>();
+    a.contrib_base = P->contrib_base.as<int64_t>();
+    a.contrib_code = P->contrib_code.as<uint16_t>();
     a.n_phi = P->n_phi;
     a.max_row = P->max_row;
     int nf = 0;

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -414,6 +415,41 @@ std::string build_pattern(int d, int p, int64_t n_vertices, int64_t n_cells, con
             }
         }
     });
+    // contribution lists of every CSR entry (segments of the sorted element entries)
+    {
+        int64_t max_inc = 0;
+        for (int64_t i = 0; i < nd; ++i) max_inc = std::max(max_inc, iptr[i + 1] - iptr[i]);
+        if (max_inc > 256 || nph > 256) return "more than 256 incidences per row or local dofs: code stream would overflow";
+        P.contrib_cnt.assign(P.nnz, 0);
+        P.contrib_base.assign(nd + 1, 0);
+        for (int64_t i = 0; i < nd; ++i) P.contrib_base[i + 1] = P.contrib_base[i] + (iptr[i + 1] - iptr[i]) * nph;
+        P.contrib_code.resize((size_t)n_cells * nph * nph);
+        std::atomic<int> overflow{0};
+        parallel_for(nd, [&](int64_t b, int64_t e) {
+            std::vector<int> fillpos;
+            for (int64_t i = b; i < e; ++i) {
+                const int64_t r0 = P.row_ptr[i];
+                const int len = (int)(P.row_ptr[i + 1] - r0);
+                const int ninc = (int)(iptr[i + 1] - iptr[i]);
+                // counts per slot, then offsets, then codes in incidence (= cell) order
+                for (int t = 0; t < ninc; ++t)
+                    for (int l = 0; l < nph; ++l) {
+                        const int sl = P.inc_slot[(size_t)(iptr[i] + t) * nph + l];
+                        if (P.contrib_cnt[r0 + sl] == 255) overflow = 1;
+                        else P.contrib_cnt[r0 + sl]++;
+                    }
+                fillpos.assign(len + 1, 0);
+                for (int j = 0; j < len; ++j) fillpos[j + 1] = fillpos[j] + P.contrib_cnt[r0 + j];
+                uint16_t *codes = P.contrib_code.data() + P.contrib_base[i];
+                for (int t = 0; t < ninc; ++t)
+                    for (int l = 0; l < nph; ++l) {
+                        const int sl = P.inc_slot[(size_t)(iptr[i] + t) * nph + l];
+                        codes[fillpos[sl]++] = (uint16_t)(t | (l << 8));
+                    }
+            }
+        });
+        if (overflow) return "a CSR entry has more than 255 contributions";
+    }
     // vertex incidence for the adjoint's vertex scatter
     P.vinc_ptr.assign(n_vertices + 1, 0);
     for (int64_t i = 0; i < n_cells * nv; ++i) P.vinc_ptr[cells[i] + 1]++;

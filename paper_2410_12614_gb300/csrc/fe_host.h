@@ -30,6 +30,11 @@ struct Pattern {
     std::vector<int64_t> inc_ptr;     // [n_dofs+1]
     std::vector<int32_t> inc_elem;    // c * n_phi + k, sorted by (dof, c)
     std::vector<uint16_t> inc_slot;   // [n_inc][n_phi]
+    // per CSR entry, its element-entry contributions in increasing cell order:
+    // code t | l << 8 (t = incidence index inside the row, l = local column)
+    std::vector<uint8_t> contrib_cnt;   // [nnz]
+    std::vector<int64_t> contrib_base;  // [n_dofs + 1] first code of each row
+    std::vector<uint16_t> contrib_code; // [n_cells * n_phi * n_phi]
     // vertex -> (cell, local vertex) incidence for the adjoint scatter
     std::vector<int64_t> vinc_ptr;    // [n_vertices+1]
     std::vector<int32_t> vinc;        // c * (d+1) + j, sorted by (vertex, c)

@@ -89,6 +89,9 @@ struct AsmArgs {
     const int64_t *inc_ptr;    // [n_rows + 1] into inc_elem
     const int32_t *inc_elem;   // element-row ids c * n_phi + k, sorted by (row, c)
     const uint16_t *inc_slot;  // [n_inc][n_phi] position of dof(c,l) inside the row
+    const uint8_t *contrib_cnt;     // [nnz] number of element entries summed into each CSR value
+    const int64_t *contrib_base;    // [n_rows + 1] first contribution code of each row
+    const uint16_t *contrib_code;   // incidence index | local column << 8, per row in slot order
     int n_phi;
     int n_forms;
     const void *A[MAX_FORMS];
@@ -121,6 +124,7 @@ struct AdjArgs {
 // kernel launches made, or a negative cudaError_t on launch failure.
 int launch_tc_elements(const TcArgs &a, size_t smem_bytes, cudaStream_t s);
 size_t tc_smem_bytes(const TcArgs &a);
+bool tc_can_stage(const TcArgs &a);
 int launch_f64_elements(const F64Args &a, cudaStream_t s);
 int launch_assemble(const AsmArgs &a, bool fp64, cudaStream_t s);
 int launch_adjoint(const AdjArgs &a, const int64_t *vert_inc_ptr, const int32_t *vert_inc, double *g_vertices,

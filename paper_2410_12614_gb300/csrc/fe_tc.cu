@@ -1,4 +1,5 @@
-// Tensor-core element-matrix kernel (sm_103a, tcgen05).
+// Tensor-core element-matrix kernel (sm_103a, tcgen05), persistent and
+// warp-specialised.
 //
 // Algorithm 1 of the paper for a tile of 128 cells at once, written as one
 // dense contraction per tile with the cells on the MMA M dimension:
@@ -16,17 +17,22 @@
 // strategy of Sec. 4.5.  Only the upper triangle k <= l is computed; the
 // epilogue mirrors it.
 //
-// CTA: 256 threads, two per cell.  K is streamed in 128-byte chunks through a
-// 2-stage ring.  A chunk holds one window of consecutive quadrature points of
-// one (s,t) pair, so a thread converts its cell's coefficient window
-// w_q = w_q kappa_cq to FP32 once and reuses it for every pair.  The shared
-// operand P arrives by a 1-D bulk copy of a pre-swizzled image (no
-// multicast); thread 0 issues tcgen05.mma into an FP32 TMEM accumulator of
-// N <= 256 columns and commits to mbarriers.  The epilogue mirrors the upper
-// triangle into a conflict-free shared-memory staging area and writes whole
-// element matrices with coalesced 16-byte stores.  Every wait is bounded
-// (globaltimer); a timeout sets the status word and the CTA exits after
-// releasing its tensor memory.
+// One CTA per SM walks its tiles; a job is one (tile, form, N pass).  Roles:
+//   warps 0-3  builders: FP64 geometry with one thread per cell; the FP32
+//              coefficient window w_q kappa_cq loaded coalesced (one lane per
+//              quadrature point, shared by every (s,t) pair and both forms)
+//              and the 128-byte swizzled K-major rows of C written one row
+//              per warp instruction into a 2-stage ring (arrive a_full).
+//   warps 4-11 epilogue, two warps per TMEM lane group: drain a finished
+//              accumulator into a conflict-free sym-packed staging area,
+//              release it, and write whole row-major element matrices with
+//              coalesced stores (mirroring k <= l to k > l).
+//   warp 12    bulk copies of the pre-swizzled P chunks into a 2-stage ring
+//              (one 1-D copy per chunk, no multicast) and tcgen05.mma into
+//              one of two 256-column FP32 TMEM accumulators (lane 0 issues).
+// So the build of tile t+1, the MMAs and the stores of tile t overlap.  Every
+// wait is bounded (globaltimer); a timeout sets the status word and all roles
+// leave after in-flight copies and MMAs have drained.
 #include <cstdio>
 
 #include "fe_device.cuh"
@@ -35,21 +41,25 @@ namespace fe {
 
 namespace {
 
-constexpr int TC_CELLS_PER_HALF = 16;  // epilogue staging granularity per lane group
+constexpr int V_THREADS = 416;   // 13 warps
+constexpr int W_EPI0 = 4;        // warps 4-11: epilogue, two per TMEM lane group
+constexpr int N_EPI = 8;
+constexpr int W_MMA = 12;
+constexpr int RING = 2;          // A and B ring stages
+constexpr int ACC_COLS = 256;    // columns per TMEM accumulator (2 of them)
+constexpr int MAX_F2S_IT = 16;   // n_phi^2 <= 512 for the staged epilogue
 
-struct TcSmem {
-    uint8_t *A;       // [TC_STAGES][128 rows][128 B]
-    uint8_t *B;       // [TC_STAGES][NPmax rows][128 B]
-    float *stage;     // epilogue staging (aliases A and B)
-    float *geo;       // [128][8]: G pairs, |det J|, spare
-    float *wmax;      // [2][128]
-    float *omega;     // [n_q] quadrature weights in FP32
-    int32_t *symkl;   // [n_sym_pad] k | l << 16
-    uint64_t *full;   // [TC_STAGES]
-    uint64_t *empty;  // [TC_STAGES]
-    uint64_t *acc;
+struct Smem {
+    uint8_t *A;        // [RING][128][128 B]
+    uint8_t *B;        // [RING][NPmax][128 B]
+    float *stage;      // [4][32][pitch]
+    float *meta;       // [2][128] unscale per cell for the two accumulators
+    float *rowc;       // [128][8] per cell: G pairs * scale (stiffness), |det J| * scale (mass)
+    float *omega;      // [n_q]
+    int16_t *f2s;      // [n_phi^2] full position -> sym column (staged only)
+    uint64_t *a_full, *a_empty, *b_full, *b_empty, *acc_full, *acc_empty, *meta_full, *meta_empty, *drain;
     uint32_t *tmem_holder;
-    int *flags;       // [0] abort, [1] status bits
+    int *flags;        // [0] abort, [1] status bits
 };
 
 __host__ __device__ inline int np_max(const TcArgs &a) {
@@ -59,45 +69,40 @@ __host__ __device__ inline int np_max(const TcArgs &a) {
     return m;
 }
 
-// the shared-memory copy of the sym table is used by the staged epilogue only
-__host__ __device__ inline int sym_pad(const TcArgs &a) {
-    if (!a.staged) return 0;
-    int n = a.n_phi * (a.n_phi + 1) / 2;
-    return (n + 3) & ~3;
+__host__ __device__ inline int stage_pitch(const TcArgs &a) { return np_max(a) + 1; }
+
+__host__ __device__ inline size_t align1k(size_t x) { return (x + 1023) & ~size_t(1023); }
+
+__host__ __device__ inline size_t bytes_A() { return (size_t)RING * TC_M * TC_CHUNK_BYTES; }
+__host__ __device__ inline size_t bytes_B(const TcArgs &a) { return (size_t)RING * np_max(a) * TC_CHUNK_BYTES; }
+__host__ __device__ inline size_t bytes_stage(const TcArgs &a) {
+    return a.staged ? align1k((size_t)4 * 32 * stage_pitch(a) * sizeof(float)) : 0;
 }
 
-__host__ __device__ inline uint32_t tmem_cols_for(int np) {
-    uint32_t c = 32;
-    while (c < (uint32_t)np) c <<= 1;
-    return c;
-}
-
-__host__ __device__ inline int stage_pitch(const TcArgs &a) { return (a.n_phi * a.n_phi) | 1; }
-
-__host__ __device__ inline size_t union_bytes(const TcArgs &a) {
-    size_t ring = (size_t)TC_STAGES * TC_M * TC_CHUNK_BYTES + (size_t)TC_STAGES * np_max(a) * TC_CHUNK_BYTES;
-    size_t stg = a.staged ? (size_t)4 * TC_CELLS_PER_HALF * stage_pitch(a) * sizeof(float) : 0;
-    size_t u = ring > stg ? ring : stg;
-    return (u + 1023) & ~size_t(1023);
-}
-
-__device__ inline TcSmem carve(uint8_t *raw, const TcArgs &a) {
+__device__ inline Smem carve(uint8_t *raw, const TcArgs &a) {
     uintptr_t p = (reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023);
-    TcSmem s;
+    Smem s;
     s.A = reinterpret_cast<uint8_t *>(p);
-    s.B = s.A + TC_STAGES * TC_M * TC_CHUNK_BYTES;
-    s.stage = reinterpret_cast<float *>(s.A);
-    uint8_t *q = s.A + union_bytes(a);
-    s.geo = reinterpret_cast<float *>(q);
-    s.wmax = s.geo + TC_M * 8;
-    s.omega = s.wmax + 2 * TC_M;
-    s.symkl = reinterpret_cast<int32_t *>(s.omega + ((a.n_q + 3) & ~3));
-    q = reinterpret_cast<uint8_t *>(s.symkl + sym_pad(a));
+    s.B = s.A + bytes_A();
+    s.stage = reinterpret_cast<float *>(s.B + bytes_B(a));
+    uint8_t *q = reinterpret_cast<uint8_t *>(s.stage) + bytes_stage(a);
+    s.meta = reinterpret_cast<float *>(q);
+    s.rowc = s.meta + 2 * TC_M;
+    s.omega = s.rowc + 8 * TC_M;
+    s.f2s = reinterpret_cast<int16_t *>(s.omega + ((a.n_q + 3) & ~3));
+    q = reinterpret_cast<uint8_t *>(s.f2s + (a.staged ? ((a.n_phi * a.n_phi + 3) & ~3) : 0));
     q = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(q) + 7) & ~uintptr_t(7));
-    s.full = reinterpret_cast<uint64_t *>(q);
-    s.empty = s.full + TC_STAGES;
-    s.acc = s.empty + TC_STAGES;
-    s.tmem_holder = reinterpret_cast<uint32_t *>(s.acc + 1);
+    uint64_t *b = reinterpret_cast<uint64_t *>(q);
+    s.a_full = b;
+    s.a_empty = b + RING;
+    s.b_full = b + 2 * RING;
+    s.b_empty = b + 3 * RING;
+    s.acc_full = b + 4 * RING;
+    s.acc_empty = s.acc_full + 2;
+    s.meta_full = s.acc_empty + 2;
+    s.meta_empty = s.meta_full + 2;
+    s.drain = s.meta_empty + 2;
+    s.tmem_holder = reinterpret_cast<uint32_t *>(s.drain + 1);
     s.flags = reinterpret_cast<int *>(s.tmem_holder + 2);
     return s;
 }
@@ -119,84 +124,82 @@ __device__ __forceinline__ float f64_to_f32_rne(double x, int &nonfinite) {
     return static_cast<float>(x);
 }
 
-template <int EB>
-struct Conv;
-template <>
-struct Conv<2> {
-    // 8 values -> 16 bytes
-    template <int PREC>
-    __device__ static uint4 pack(const float *v) {
-        uint4 r;
-        if constexpr (PREC == FE_PREC_BF16) {
-            r.x = pack_bf16x2(v[0], v[1]);
-            r.y = pack_bf16x2(v[2], v[3]);
-            r.z = pack_bf16x2(v[4], v[5]);
-            r.w = pack_bf16x2(v[6], v[7]);
-        } else {
-            r.x = pack_f16x2(v[0], v[1]);
-            r.y = pack_f16x2(v[2], v[3]);
-            r.z = pack_f16x2(v[4], v[5]);
-            r.w = pack_f16x2(v[6], v[7]);
+template <int PREC, int EP>
+__device__ __forceinline__ uint4 pack_piece(const float *v, int blk) {
+    uint4 r;
+    if constexpr (PREC == FE_PREC_BF16) {
+        r.x = pack_bf16x2(v[0], v[1]);
+        r.y = pack_bf16x2(v[2], v[3]);
+        r.z = pack_bf16x2(v[4], v[5]);
+        r.w = pack_bf16x2(v[6], v[7]);
+    } else if constexpr (PREC == FE_PREC_FP16) {
+        r.x = pack_f16x2(v[0], v[1]);
+        r.y = pack_f16x2(v[2], v[3]);
+        r.z = pack_f16x2(v[4], v[5]);
+        r.w = pack_f16x2(v[6], v[7]);
+    } else if constexpr (PREC == FE_PREC_TF32 || PREC == FE_PREC_TF32X3) {
+        uint32_t w4[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            uint32_t h = round_tf32(v[i]);
+            if (PREC == FE_PREC_TF32X3 && blk == 2) h = round_tf32(v[i] - __uint_as_float(h));
+            w4[i] = h;
         }
-        return r;
+        r = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+    } else {
+        uint32_t w4[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            w4[i] = pack_e4m3x2(v[4 * i], v[4 * i + 1]) | (pack_e4m3x2(v[4 * i + 2], v[4 * i + 3]) << 16);
+        r = make_uint4(w4[0], w4[1], w4[2], w4[3]);
     }
-};
+    return r;
+}
+
+__device__ __forceinline__ int first_form(const TcArgs &a) { return (a.form_mask & 1) ? 0 : 1; }
 
 template <int PREC>
-__global__ void __launch_bounds__(TC_THREADS, 2) tc_element_kernel(const __grid_constant__ TcArgs a) {
+__global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_constant__ TcArgs a) {
     constexpr int EB = (PREC == FE_PREC_E4M3) ? 1 : ((PREC == FE_PREC_TF32 || PREC == FE_PREC_TF32X3) ? 4 : 2);
     constexpr int KIND = (PREC == FE_PREC_E4M3) ? 2 : ((EB == 4) ? 1 : 0);
     constexpr int KCE = TC_CHUNK_BYTES / EB;  // quadrature points per chunk
-    constexpr int HW = KCE / 2;               // points per thread (half window)
     constexpr int EP = 16 / EB;               // elements per 16-byte piece
 
     // a CTA that starts after another one gave up does no work at all
     if (*reinterpret_cast<volatile int *>(a.status) & ST_TIMEOUT) return;
 
     extern __shared__ uint8_t smem_raw[];
-    TcSmem sm = carve(smem_raw, a);
+    Smem sm = carve(smem_raw, a);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int cl = tid & (TC_M - 1), half = tid >> 7;
-    const int64_t cell0 = (int64_t)blockIdx.x * TC_M;
-    const int64_t cell = cell0 + cl;
-    const bool valid = cell < a.n_cells;
+    const int64_t n_tiles = (a.n_cells + TC_M - 1) / TC_M;
     const int NPm = np_max(a);
-    const uint32_t ncols = tmem_cols_for(NPm);
     const int nph = a.n_phi, nph2 = nph * nph;
-    const int n_sym = nph * (nph + 1) / 2;
 
     if (tid == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
-            mbar_init(&sm.full[s], 1);
-            mbar_init(&sm.empty[s], 1);
+        for (int s = 0; s < RING; ++s) {
+            mbar_init(&sm.a_full[s], TC_M);
+            mbar_init(&sm.a_empty[s], 1);
+            mbar_init(&sm.b_full[s], 1);
+            mbar_init(&sm.b_empty[s], 1);
         }
-        mbar_init(sm.acc, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sm.acc_full[b], 1);
+            mbar_init(&sm.acc_empty[b], 32 * N_EPI);
+            mbar_init(&sm.meta_full[b], TC_M);
+            mbar_init(&sm.meta_empty[b], 32 * N_EPI);
+        }
+        mbar_init(sm.drain, 1);
         sm.flags[0] = 0;
         sm.flags[1] = 0;
         fence_mbar_init();
     }
-    for (int i = tid; i < a.n_q; i += TC_THREADS) sm.omega[i] = (float)__ldg(a.weights + i);
+    for (int i = tid; i < a.n_q; i += V_THREADS) sm.omega[i] = (float)__ldg(a.weights + i);
     if (a.staged)
-        for (int i = tid; i < n_sym; i += TC_THREADS) sm.symkl[i] = __ldg(a.sym_kl + i);
+        for (int i = tid; i < nph2; i += V_THREADS) sm.f2s[i] = __ldg(a.full2sym + i);
     if (warp == 0) {
-        tmem_alloc(sm.tmem_holder, ncols);
+        tmem_alloc(sm.tmem_holder, 2 * ACC_COLS);
         tmem_relinquish();
-    }
-    // ---- geometry in FP64, one cell per thread of the first half ----
-    if (half == 0) {
-        float *g = sm.geo + cl * 8;
-        int st = 0;
-        if (valid) {
-            CellGeom geo;
-            st = cell_geometry(a.vertices, a.cells, cell, a.d, geo);
-            for (int j = 0; j < 6; ++j) g[j] = st ? 0.f : (float)geo.G[j];
-            g[6] = st ? 0.f : (float)geo.absdet;
-        } else {
-            for (int j = 0; j < 7; ++j) g[j] = 0.f;
-        }
-        g[7] = __int_as_float(st);
-        if (st) atomicOr(&sm.flags[1], st);
     }
     fence_proxy_async();
     tc_fence_before();
@@ -204,268 +207,395 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_element_kernel(const __grid_
     tc_fence_after();
     const uint32_t tmem = *sm.tmem_holder;
     const unsigned long long deadline = global_ns() + a.timeout_ns;
-    const double *krow = a.kappa + (valid ? cell : 0) * (int64_t)a.n_q;
-    const bool ok = valid && (__float_as_int(sm.geo[cl * 8 + 7]) == 0);
-    int nonfinite = 0;
+    volatile int *abort_flag = sm.flags;
 
-    // per-cell scaling (formats with a narrow exponent range): the largest |w_q kappa_cq|
-    float wmax = 0.f;
-    if (a.target_exp > 1) {
-        if (ok)
-            for (int q = half; q < a.n_q; q += 2)
-                wmax = fmaxf(wmax, fabsf(f64_to_f32_rne(__ldg(krow + q), nonfinite) * sm.omega[q]));
-        sm.wmax[half * TC_M + cl] = wmax;
-    }
-    __syncthreads();
-    if (a.target_exp > 1) wmax = fmaxf(sm.wmax[cl], sm.wmax[TC_M + cl]);
-
-    int chunk = 0, pass_count = 0;
-    bool aborted = false;
-    float win[HW];
-#pragma unroll 1
-    for (int f = 0; f < MAX_FORMS && !aborted; ++f) {
-        if (!(a.form_mask & (1 << f))) continue;
-        const TcOperand &op = a.op[f];
-        float g[6];
-        float gmax = 0.f;
-        if (f == 0) {
+    if (warp < 4) {
+        // ======================= builders =======================
+        // Geometry with one thread per cell; the operand C with one lane per
+        // QL consecutive quadrature points and a loop over the warp's 32 cells,
+        // so that coefficient loads are coalesced and every lane writes one
+        // 32-bit word of a 128-byte operand row per step.
+        constexpr int QL = KCE / 32;            // points per lane: 2 (bf16/fp16), 1 (tf32), 4 (e4m3)
+        constexpr bool WIN_REG = (QL <= 2);     // keep the coefficient window in registers
+        constexpr int RB = 8 / QL;              // rows per batch of in-flight coefficient loads
+        const int cl = tid;
+        const int wrow0 = warp * 32;
+        int ac = 0, jb = 0, nonfinite = 0;
+        float win[WIN_REG ? 32 * QL : 1];
+        float om[QL];
+        auto load_rows = [&](int64_t tile_cell0, int qw, float *dst) {
+            // dst[r * QL + i] = w_q kappa_{cell r, q}, q = qw * KCE + lane * QL + i
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                g[j] = sm.geo[cl * 8 + j];
-                gmax = fmaxf(gmax, fabsf(g[j]));
+            for (int i = 0; i < QL; ++i) {
+                const int q = qw * KCE + lane * QL + i;
+                om[i] = q < a.n_q ? sm.omega[q] : 0.f;
             }
-        } else {
-            g[0] = sm.geo[cl * 8 + 6];
 #pragma unroll
-            for (int j = 1; j < 6; ++j) g[j] = 0.f;
-            gmax = g[0];
-        }
-        int e_c = 0;
-        if (a.target_exp > 1 && ok) {
-            const float cmax = wmax * gmax;
-            if (cmax > 0.f && isfinite(cmax)) {
-                int e;
-                frexpf(cmax, &e);
-                e_c = a.target_exp - e;
+            for (int r0 = 0; r0 < 32; r0 += RB) {
+                double raw[RB * QL];
+#pragma unroll
+                for (int r = 0; r < RB; ++r) {
+                    const int64_t cell_r = tile_cell0 + wrow0 + r0 + r;
+#pragma unroll
+                    for (int i = 0; i < QL; ++i) {
+                        const int q = qw * KCE + lane * QL + i;
+                        raw[r * QL + i] = (cell_r < a.n_cells && q < a.n_q) ? __ldg(a.kappa + cell_r * a.n_q + q) : 0.0;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < RB * QL; ++k) dst[r0 * QL + k] = f64_to_f32_rne(raw[k], nonfinite) * om[k % QL];
             }
-        }
-        const float scale = ldexpf(1.f, e_c);
-        const float unscale = ldexpf(op.p_inv_scale, -e_c);
-        const uint32_t idesc = a.idesc | ((uint32_t)(op.NP >> 3) << 17);
-        const uint32_t bbytes = (uint32_t)op.NP * TC_CHUNK_BYTES;
-        const int per_qw = op.n_pairs * op.n_blk;
-
-#pragma unroll 1
-        for (int n = 0; n < op.n_pass && !aborted; ++n) {
+        };
+        for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
+            const int64_t tile_cell0 = t * TC_M;
+            const int64_t cell = tile_cell0 + cl;
+            const bool valid = cell < a.n_cells;
+            float g6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, adet = 0.f;
+            int st = 0;
+            if (valid) {
+                CellGeom geo;
+                st = cell_geometry(a.vertices, a.cells, cell, a.d, geo);
+                if (!st) {
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) g6[j] = (float)geo.G[j];
+                    adet = (float)geo.absdet;
+                }
+            }
+            if (st) atomicOr(&sm.flags[1], st);
+            // per-cell largest |w_q kappa_cq| (for the narrow-exponent formats)
+            float wmax = 0.f;
+            if (a.target_exp > 1) {
+                for (int r = 0; r < 32; ++r) {
+                    const int64_t cell_r = tile_cell0 + wrow0 + r;
+                    float m = 0.f;
+                    if (cell_r < a.n_cells)
+                        for (int q = lane; q < a.n_q; q += 32)
+                            m = fmaxf(m, fabsf(f64_to_f32_rne(__ldg(a.kappa + cell_r * a.n_q + q), nonfinite) * sm.omega[q]));
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                    if (lane == r) wmax = m;
+                }
+            }
+            float unscale_f[MAX_FORMS] = {1.f, 1.f};
+            for (int f = 0; f < MAX_FORMS; ++f) {
+                if (!(a.form_mask & (1 << f))) continue;
+                float gmax = 0.f;
+                if (f == 0) {
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) gmax = fmaxf(gmax, fabsf(g6[j]));
+                } else {
+                    gmax = adet;
+                }
+                int e_c = 0;
+                if (a.target_exp > 1 && valid && !st) {
+                    const float cmax = wmax * gmax;
+                    if (cmax > 0.f && isfinite(cmax)) {
+                        int e;
+                        frexpf(cmax, &e);
+                        e_c = a.target_exp - e;
+                    }
+                }
+                const float scale = ldexpf(1.f, e_c);
+                unscale_f[f] = ldexpf(a.op[f].p_inv_scale, -e_c);
+                if (f == 0) {
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) sm.rowc[cl * 8 + j] = g6[j] * scale;
+                } else {
+                    sm.rowc[cl * 8 + 6] = adet * scale;
+                }
+            }
+            __syncwarp();
             int qw_loaded = -1;
-#pragma unroll 1
-            for (int ch = 0; ch < op.n_kchunks; ++ch) {
-                const int s = chunk % TC_STAGES;
-                const int use = chunk / TC_STAGES;
-                if (chunk >= TC_STAGES) {
-                    if (!mbar_wait(&sm.empty[s], (use - 1) & 1, deadline)) sm.flags[0] = 1;
-                }
-                uint8_t *stA = sm.A + s * (TC_M * TC_CHUNK_BYTES);
-                uint8_t *stB = sm.B + (size_t)s * NPm * TC_CHUNK_BYTES;
-                if (tid == 0 && !sm.flags[0]) {
-                    fence_proxy_async();
-                    mbar_arrive_expect_tx(&sm.full[s], bbytes);
-                    bulk_g2s(stB, op.img + ((size_t)n * op.n_kchunks + ch) * bbytes, bbytes, &sm.full[s]);
-                }
-                // ---- operand C: this thread's half of the cell's 128-byte row ----
-                const int qw = ch / per_qw;
-                const int j = (ch / op.n_blk) % op.n_pairs;
-                const int blk = ch % op.n_blk;
-                if (qw != qw_loaded) {
-                    qw_loaded = qw;
-#pragma unroll
-                    for (int i = 0; i < HW; ++i) {
-                        const int q = qw * KCE + half * HW + i;
-                        win[i] = (ok && q < a.n_q) ? f64_to_f32_rne(__ldg(krow + q), nonfinite) * sm.omega[q] : 0.f;
-                    }
-                }
-                float gj = 0.f;
-#pragma unroll
-                for (int jj = 0; jj < 6; ++jj)
-                    if (jj == j) gj = g[jj];
-                gj *= scale;
-                uint8_t *rowp = stA + (cl >> 3) * 1024 + (cl & 7) * 128;
-#pragma unroll
-                for (int pp = 0; pp < 4; ++pp) {
-                    const int piece = half * 4 + pp;
-                    uint4 val;
-                    float v[EP];
-#pragma unroll
-                    for (int i = 0; i < EP; ++i) v[i] = win[pp * EP + i] * gj;
-                    if constexpr (EB == 2) {
-                        val = Conv<2>::pack<PREC>(v);
-                    } else if constexpr (EB == 4) {
-                        uint32_t w4[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            uint32_t h = round_tf32(v[i]);
-                            if (PREC == FE_PREC_TF32X3 && blk == 2) h = round_tf32(v[i] - __uint_as_float(h));
-                            w4[i] = h;
-                        }
-                        val = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-                    } else {
-                        uint32_t w4[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            w4[i] = pack_e4m3x2(v[4 * i], v[4 * i + 1]) | (pack_e4m3x2(v[4 * i + 2], v[4 * i + 3]) << 16);
-                        val = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-                    }
-                    *reinterpret_cast<uint4 *>(rowp + ((piece ^ (cl & 7)) << 4)) = val;
-                }
-                fence_proxy_async();
-                __syncthreads();
-                if (sm.flags[0]) {
-                    aborted = true;
-                    break;
-                }
-                if (tid == 0) {
-                    if (!mbar_wait(&sm.full[s], use & 1, deadline)) {
+            for (int f = 0; f < MAX_FORMS; ++f) {
+                if (!(a.form_mask & (1 << f))) continue;
+                const TcOperand &op = a.op[f];
+                const int per_qw = op.n_pairs * op.n_blk;
+                for (int n = 0; n < op.n_pass; ++n) {
+                    const int b = jb & 1, ub = jb >> 1;
+                    if (jb >= 2 && !mbar_wait(&sm.meta_empty[b], (ub - 1) & 1, deadline)) {
                         sm.flags[0] = 1;
-                    } else {
-                        tc_fence_after();
-                        const uint32_t a0 = smem_u32(stA), b0 = smem_u32(stB);
-#pragma unroll
-                        for (int ks = 0; ks < TC_CHUNK_BYTES / 32; ++ks) {
-                            umma<KIND>(tmem, sdesc_sw128(a0 + 32 * ks), sdesc_sw128(b0 + 32 * ks), idesc,
-                                       (ch | ks) != 0 ? 1u : 0u);
+                        break;
+                    }
+                    sm.meta[b * TC_M + cl] = unscale_f[f];
+                    mbar_arrive(&sm.meta_full[b]);
+                    for (int ch = 0; ch < op.n_kchunks; ++ch) {
+                        const int s = ac % RING, ua = ac / RING;
+                        if (ac >= RING && !mbar_wait(&sm.a_empty[s], (ua - 1) & 1, deadline)) {
+                            sm.flags[0] = 1;
+                            break;
                         }
-                        umma_commit(&sm.empty[s]);
-                        if (ch == op.n_kchunks - 1) umma_commit(sm.acc);
+                        const int qw = ch / per_qw;
+                        const int j = (ch / op.n_blk) % op.n_pairs;
+                        const int blk = ch % op.n_blk;
+                        const int cidx = (f == 0) ? j : 6;
+                        float wtmp[WIN_REG ? 1 : 32 * QL];
+                        float *w = WIN_REG ? win : wtmp;
+                        if (!WIN_REG) {
+                            load_rows(tile_cell0, qw, w);
+                        } else if (qw != qw_loaded) {
+                            qw_loaded = qw;
+                            load_rows(tile_cell0, qw, w);
+                        }
+                        uint8_t *stA = sm.A + s * (TC_M * TC_CHUNK_BYTES);
+                        const int byte = lane * 4;   // this lane's word inside a 128-byte row
+#pragma unroll
+                        for (int r = 0; r < 32; ++r) {
+                            const int R = wrow0 + r;
+                            const float gj = sm.rowc[R * 8 + cidx];
+                            uint32_t word;
+                            if constexpr (PREC == FE_PREC_BF16) {
+                                word = pack_bf16x2(w[r * QL] * gj, w[r * QL + 1] * gj);
+                            } else if constexpr (PREC == FE_PREC_FP16) {
+                                word = pack_f16x2(w[r * QL] * gj, w[r * QL + 1] * gj);
+                            } else if constexpr (EB == 4) {
+                                const float v = w[r * QL] * gj;
+                                word = round_tf32(v);
+                                if (PREC == FE_PREC_TF32X3 && blk == 2) word = round_tf32(v - __uint_as_float(word));
+                            } else {
+                                word = pack_e4m3x2(w[r * QL] * gj, w[r * QL + 1] * gj) |
+                                       (pack_e4m3x2(w[r * QL + 2] * gj, w[r * QL + 3] * gj) << 16);
+                            }
+                            *reinterpret_cast<uint32_t *>(stA + (R >> 3) * 1024 + (R & 7) * 128 +
+                                                          ((((byte >> 4) ^ (R & 7)) & 7) << 4) + (byte & 15)) = word;
+                        }
+                        fence_proxy_async();
+                        mbar_arrive(&sm.a_full[s]);
+                        ++ac;
+                    }
+                    ++jb;
+                    if (*abort_flag) break;
+                }
+                if (*abort_flag) break;
+            }
+        }
+        if (nonfinite) atomicOr(&sm.flags[1], ST_NONFINITE);
+    } else if (warp == W_MMA) {
+        // ======================= bulk copies + MMA =======================
+        int64_t my_tiles = 0;
+        if (blockIdx.x < n_tiles) my_tiles = (n_tiles - 1 - blockIdx.x) / gridDim.x + 1;
+        int chunks_per_tile = 0;
+        for (int f = 0; f < MAX_FORMS; ++f)
+            if (a.form_mask & (1 << f)) chunks_per_tile += a.op[f].n_pass * a.op[f].n_kchunks;
+        const int64_t total = my_tiles * chunks_per_tile;
+        // B cursor (the shared operand does not depend on the tile)
+        int bf = first_form(a), bn = 0, bch = 0;
+        int64_t bc = 0;
+        auto issue_b = [&](int64_t upto) -> bool {
+            while (bc < upto) {
+                const int s = (int)(bc % RING);
+                const int64_t ub = bc / RING;
+                if (bc >= RING && !mbar_wait(&sm.b_empty[s], (uint32_t)((ub - 1) & 1), deadline)) return false;
+                const TcOperand &op = a.op[bf];
+                const uint32_t bytes = (uint32_t)op.NP * TC_CHUNK_BYTES;
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&sm.b_full[s], bytes);
+                    bulk_g2s(sm.B + (size_t)s * NPm * TC_CHUNK_BYTES,
+                             op.img + ((size_t)bn * op.n_kchunks + bch) * bytes, bytes, &sm.b_full[s]);
+                }
+                __syncwarp();
+                ++bc;
+                if (++bch == op.n_kchunks) {
+                    bch = 0;
+                    if (++bn == op.n_pass) {
+                        bn = 0;
+                        do { bf = (bf + 1) % MAX_FORMS; } while (!(a.form_mask & (1 << bf)));
                     }
                 }
-                ++chunk;
             }
-            if (aborted) break;
-            // ---- epilogue of pass n ----
-            const bool acc_ok = mbar_wait(sm.acc, pass_count & 1, deadline);
-            ++pass_count;
-            if (!acc_ok) sm.flags[0] = 1;
-            __syncthreads();
-            if (sm.flags[0]) {
-                aborted = true;
-                break;
-            }
-            tc_fence_after();
-            float *out = a.out[f];
-            const int lg = warp & 3;       // TMEM lane group = 32 cells
-            const int cpar = warp >> 2;    // column-chunk parity handled by this warp
-            const uint32_t tbase = tmem + ((uint32_t)(lg * 32) << 16);
-            if (a.staged) {
-                const int pitch = stage_pitch(a);
-                float *stg = sm.stage + lg * TC_CELLS_PER_HALF * pitch;
-#pragma unroll 1
-                for (int h2 = 0; h2 < 2; ++h2) {
-                    const bool active = (lane >> 4) == h2;
-                    float *mine = stg + (lane & 15) * pitch;
-#pragma unroll 1
-                    for (int c0 = 16 * cpar; c0 < op.NP; c0 += 32) {
-                        uint32_t r[16];
-                        tmem_ld16(tbase + (uint32_t)c0, r);
-                        if (active) {
+            return true;
+        };
+        int64_t mc = 0;
+        int jb = 0;
+        bool fail = false;
+        for (int64_t t = 0; t < my_tiles && !fail; ++t) {
+            for (int f = 0; f < MAX_FORMS && !fail; ++f) {
+                if (!(a.form_mask & (1 << f))) continue;
+                const TcOperand &op = a.op[f];
+                const uint32_t idesc = a.idesc | ((uint32_t)(op.NP >> 3) << 17);
+                for (int n = 0; n < op.n_pass && !fail; ++n) {
+                    const int b = jb & 1, ub = jb >> 1;
+                    if (jb >= 2 && !mbar_wait(&sm.acc_empty[b], (ub - 1) & 1, deadline)) {
+                        fail = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dacc = tmem + (uint32_t)(b * ACC_COLS);
+                    for (int ch = 0; ch < op.n_kchunks; ++ch) {
+                        if (!issue_b(mc + RING < total ? mc + RING : total)) {
+                            fail = true;
+                            break;
+                        }
+                        const int sa = (int)(mc % RING);
+                        const uint32_t par = (uint32_t)((mc / RING) & 1);
+                        if (!mbar_wait(&sm.a_full[sa], par, deadline) || !mbar_wait(&sm.b_full[sa], par, deadline)) {
+                            fail = true;
+                            break;
+                        }
+                        tc_fence_after();
+                        if (lane == 0) {
+                            const uint32_t a0 = smem_u32(sm.A + sa * (TC_M * TC_CHUNK_BYTES));
+                            const uint32_t b0 = smem_u32(sm.B + (size_t)sa * NPm * TC_CHUNK_BYTES);
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                const int col = c0 + i;
-                                if (col < op.n_cols) {
-                                    const int32_t kl = sm.symkl[col];
-                                    const int k = kl & 0xFFFF, l = kl >> 16;
-                                    const float v = __uint_as_float(r[i]) * unscale;
-                                    mine[k * nph + l] = v;
-                                    mine[l * nph + k] = v;
+                            for (int ks = 0; ks < TC_CHUNK_BYTES / 32; ++ks)
+                                umma<KIND>(dacc, sdesc_sw128(a0 + 32 * ks), sdesc_sw128(b0 + 32 * ks), idesc,
+                                           (ch | ks) != 0 ? 1u : 0u);
+                            umma_commit(&sm.a_empty[sa]);
+                            umma_commit(&sm.b_empty[sa]);
+                            if (ch == op.n_kchunks - 1) umma_commit(&sm.acc_full[b]);
+                        }
+                        __syncwarp();
+                        ++mc;
+                    }
+                    ++jb;
+                    if (*abort_flag) fail = true;
+                }
+            }
+        }
+        if (fail) sm.flags[0] = 1;
+        // drain: every issued MMA finished, every issued bulk copy landed
+        if (lane == 0) umma_commit(sm.drain);
+        __syncwarp();
+        const unsigned long long drain_deadline = global_ns() + 200000000ull;
+        mbar_wait(sm.drain, 0, drain_deadline);
+        for (int64_t c = mc; c < bc; ++c) mbar_wait(&sm.b_full[c % RING], (uint32_t)((c / RING) & 1), drain_deadline);
+    } else if (warp >= W_EPI0 && warp < W_EPI0 + N_EPI) {
+        // ======================= epilogue =======================
+        // warps 4-7 and 8-11: lane group g = warp % 4 (TMEM lanes 32g..32g+31),
+        // half h: alternate 32-column blocks when draining TMEM, cells
+        // 16h..16h+15 of the lane group when writing out.
+        const int g = warp & 3;
+        const int h = (warp - W_EPI0) >> 2;
+        const int pitch = stage_pitch(a);
+        float *stg = sm.stage + g * 32 * pitch;
+        int f2s_reg[MAX_F2S_IT];
+#pragma unroll
+        for (int it = 0; it < MAX_F2S_IT; ++it) {
+            const int pos = lane + 32 * it;
+            f2s_reg[it] = (a.staged && pos < nph2) ? sm.f2s[pos] : 0;
+        }
+        const int n_it = (nph2 + 31) / 32;
+        int jb = 0;
+        for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
+            for (int f = 0; f < MAX_FORMS; ++f) {
+                if (!(a.form_mask & (1 << f))) continue;
+                const TcOperand &op = a.op[f];
+                float *out = a.out[f];
+                for (int n = 0; n < op.n_pass; ++n) {
+                    const int b = jb & 1, ub = jb >> 1;
+                    if (!mbar_wait(&sm.acc_full[b], ub & 1, deadline) || !mbar_wait(&sm.meta_full[b], ub & 1, deadline)) {
+                        sm.flags[0] = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const float us = sm.meta[b * TC_M + g * 32 + lane];
+                    mbar_arrive(&sm.meta_empty[b]);
+                    const uint32_t tbase = tmem + (uint32_t)(b * ACC_COLS) + ((uint32_t)(g * 32) << 16);
+                    const int64_t cell0 = t * TC_M + g * 32;
+                    if (a.staged) {
+                        float *mine = stg + lane * pitch;
+                        for (int c0 = 32 * h; c0 < op.NP; c0 += 64) {
+                            uint32_t r[32];
+                            tmem_ld32(tbase + (uint32_t)c0, r);
+#pragma unroll
+                            for (int i = 0; i < 32; ++i)
+                                if (c0 + i < op.NP) mine[c0 + i] = __uint_as_float(r[i]) * us;
+                        }
+                        tc_fence_before();
+                        mbar_arrive(&sm.acc_empty[b]);
+                        named_bar_sync(1 + g, 64);
+                        // whole row-major matrices of 16 consecutive cells (loads first, then stores)
+                        if (out) {
+                            for (int cc = 16 * h; cc < 16 * h + 16; ++cc) {
+                                if (cell0 + cc >= a.n_cells) break;
+                                float *__restrict__ dst = out + (cell0 + cc) * (int64_t)nph2;
+                                const float *__restrict__ src = stg + cc * pitch;
+                                float vals[MAX_F2S_IT];
+#pragma unroll
+                                for (int it = 0; it < MAX_F2S_IT; ++it) vals[it] = (it < n_it) ? src[f2s_reg[it]] : 0.f;
+#pragma unroll
+                                for (int it = 0; it < MAX_F2S_IT; ++it) {
+                                    const int pos = lane + 32 * it;
+                                    if (it < n_it && pos < nph2) dst[pos] = vals[it];
                                 }
                             }
                         }
-                    }
-                    named_bar_sync(1 + lg, 64);
-                    // coalesced copy of 16 consecutive cells (contiguous in global memory)
-                    const int64_t cfirst = cell0 + lg * 32 + h2 * TC_CELLS_PER_HALF;
-                    const int64_t rem_cells = a.n_cells - cfirst;
-                    const int ncp = rem_cells < TC_CELLS_PER_HALF ? (int)rem_cells : TC_CELLS_PER_HALF;
-                    const int t64 = cpar * 32 + lane;
-                    if (ncp > 0 && out) {
-                        float *dst = out + cfirst * (int64_t)nph2;
-                        if ((nph2 & 3) == 0) {
-                            const int n4 = nph2 >> 2;
-                            for (int i = t64; i < ncp * n4; i += 64) {
-                                const int cc = i / n4, kl = (i - cc * n4) * 4;
-                                const float *src = stg + cc * pitch + kl;
-                                reinterpret_cast<float4 *>(dst)[i] = make_float4(src[0], src[1], src[2], src[3]);
-                            }
-                        } else {
-                            for (int i = t64; i < ncp * nph2; i += 64) {
-                                const int cc = i / nph2, kl = i - cc * nph2;
-                                dst[i] = stg[cc * pitch + kl];
-                            }
-                        }
-                    }
-                    named_bar_sync(1 + lg, 64);
-                }
-            } else if (out) {
-                // direct mirrored stores (multi-pass shapes)
-#pragma unroll 1
-                for (int c0 = 16 * cpar; c0 < op.NP; c0 += 32) {
-                    uint32_t r[16];
-                    tmem_ld16(tbase + (uint32_t)c0, r);
-                    const int64_t mycell = cell0 + lg * 32 + lane;
-                    if (mycell < a.n_cells) {
-                        float *dst = out + mycell * (int64_t)nph2;
+                        named_bar_sync(1 + g, 64);
+                    } else {
+                        const int64_t mycell = cell0 + lane;
+                        for (int c0 = 32 * h; c0 < op.NP; c0 += 64) {
+                            uint32_t r[32];
+                            tmem_ld32(tbase + (uint32_t)c0, r);
+                            if (mycell < a.n_cells && out) {
+                                float *dst = out + mycell * (int64_t)nph2;
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const int col = n * op.NP + c0 + i;
-                            if (col < op.n_cols) {
-                                const int32_t kl = __ldg(a.sym_kl + col);
-                                const int k = kl & 0xFFFF, l = kl >> 16;
-                                const float v = __uint_as_float(r[i]) * unscale;
-                                dst[k * nph + l] = v;
-                                dst[l * nph + k] = v;
+                                for (int i = 0; i < 32; ++i) {
+                                    const int col = n * op.NP + c0 + i;
+                                    if (c0 + i < op.NP && col < op.n_cols) {
+                                        const int32_t kl = __ldg(a.sym_kl + col);
+                                        const int k = kl & 0xFFFF, l = kl >> 16;
+                                        const float v = __uint_as_float(r[i]) * us;
+                                        dst[k * nph + l] = v;
+                                        dst[l * nph + k] = v;
+                                    }
+                                }
                             }
                         }
+                        tc_fence_before();
+                        mbar_arrive(&sm.acc_empty[b]);
                     }
+                    ++jb;
                 }
+                if (*abort_flag) break;
             }
-            tc_fence_before();
-            __syncthreads();
         }
     }
-    if (nonfinite) atomicOr(&sm.flags[1], ST_NONFINITE);
-    if (aborted || sm.flags[0]) {
-        if (tid == 0) atomicOr(&sm.flags[1], ST_TIMEOUT);
-    }
+    if (sm.flags[0] && tid == 0) atomicOr(&sm.flags[1], ST_TIMEOUT);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (tid == 0 && sm.flags[1]) atomicOr(a.status, sm.flags[1]);
-    if (warp == 0) tmem_dealloc(tmem, ncols);
+    if (warp == 0) tmem_dealloc(tmem, 2 * ACC_COLS);
 }
 
 }  // namespace
 
 size_t tc_smem_bytes(const TcArgs &a) {
     size_t b = 1024;  // alignment slack
-    b += union_bytes(a);
-    b += (size_t)TC_M * 8 * sizeof(float) + 2 * TC_M * sizeof(float);
+    b += bytes_A() + bytes_B(a) + bytes_stage(a);
+    b += 2 * TC_M * sizeof(float) + 8 * TC_M * sizeof(float);
     b += (size_t)((a.n_q + 3) & ~3) * sizeof(float);
-    b += (size_t)sym_pad(a) * sizeof(int32_t) + 8;
-    b += (2 * TC_STAGES + 1) * sizeof(uint64_t) + 8 + 16;
+    b += (size_t)(a.staged ? ((a.n_phi * a.n_phi + 3) & ~3) : 0) * sizeof(int16_t) + 8;
+    b += (4 * RING + 9) * sizeof(uint64_t) + 8 + 16;
     return b;
 }
 
+// The staged epilogue needs the whole sym row in one accumulator and its
+// staging area within the shared-memory budget.
+bool tc_can_stage(const TcArgs &a) {
+    TcArgs t = a;
+    t.staged = 1;
+    for (int f = 0; f < MAX_FORMS; ++f)
+        if ((a.form_mask >> f) & 1)
+            if (a.op[f].n_pass != 1) return false;
+    return a.n_phi * a.n_phi <= 32 * MAX_F2S_IT && tc_smem_bytes(t) <= 227 * 1024;
+}
+
 template <int PREC>
-static int launch_prec(const TcArgs &a, size_t smem, cudaStream_t s, int64_t grid) {
+static int launch_prec(const TcArgs &a, size_t smem, cudaStream_t s, int grid) {
     cudaError_t e = cudaFuncSetAttribute(tc_element_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return -(int)e;
-    tc_element_kernel<PREC><<<(unsigned)grid, TC_THREADS, smem, s>>>(a);
+    tc_element_kernel<PREC><<<(unsigned)grid, V_THREADS, smem, s>>>(a);
     e = cudaGetLastError();
     return e == cudaSuccess ? 1 : -(int)e;
 }
 
 int launch_tc_elements(const TcArgs &a, size_t smem, cudaStream_t s) {
     if (a.n_cells <= 0) return 0;
-    const int64_t grid = (a.n_cells + TC_M - 1) / TC_M;
+    const int64_t n_tiles = (a.n_cells + TC_M - 1) / TC_M;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)(n_tiles < sms ? n_tiles : sms);
     switch (a.prec) {
         case FE_PREC_BF16: return launch_prec<FE_PREC_BF16>(a, smem, s, grid);
         case FE_PREC_FP16: return launch_prec<FE_PREC_FP16>(a, smem, s, grid);
