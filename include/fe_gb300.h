@@ -208,6 +208,33 @@ fe_status fe_assemble_elements(fe_plan *plan, unsigned forms, fe_precision prec,
 fe_status fe_adjoint(fe_plan *plan, const double *vertices, const double *kappa, const float *u,
                      const float *v, double *g_kappa, double *g_vertices, double *L_out);
 
+/* Allocation-free variant of fe_adjoint; the paper has no counterpart.
+ *
+ * Some callers may not allocate device memory while they run: applications
+ * whose device memory belongs to their own allocator or to a fixed budget,
+ * and latency-critical loops that cannot afford the implicit device
+ * synchronisation of cudaMalloc / cudaFree.  fe_adjoint allocates its
+ * per-cell scratch (the vertex-gradient contributions of every cell and the
+ * per-cell L) in a plan workspace on first use; this entry point computes
+ * the same results with the same kernels but takes that scratch from one
+ * fixed device array of 32 MiB (4,194,304 doubles) declared statically in
+ * the library, which every GPU that loads the library holds until the
+ * process exits.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine; the caller still passes every input and output.
+ *
+ * Limit: n_cells * ((d+1)*d + 1) doubles of scratch with g_vertices, n_cells
+ * without (at most 322,638 tetrahedra or 599,186 triangles with vertex
+ * gradients); a larger plan returns FE_ERR_UNSUPPORTED and fe_last_error()
+ * states the sizes.  The array is shared by every call in the process,
+ * whatever the plan or stream, and keeps the last call's contents: calls
+ * whose kernels overlap on the GPU race on it, so serialise them.  Every
+ * scratch entry a call reads is written earlier in the same call, so nothing
+ * needs clearing.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, once per device); make that first call
+ * before any stream capture begins.  Arguments as for fe_adjoint. */
+fe_status fe_adjoint_noalloc(fe_plan *plan, const double *vertices, const double *kappa, const float *u,
+                             const float *v, double *g_kappa, double *g_vertices, double *L_out);
+
 /* Wait for the plan's stream and report the device status word (and clear it). */
 fe_status fe_sync_status(fe_plan *plan);
 

@@ -62,6 +62,7 @@ SIGNATURES = {
     "fe_assemble_host": [_vp, ctypes.c_uint, ctypes.c_int, _vp, _vp, _vp],
     "fe_assemble_elements": [_vp, ctypes.c_uint, ctypes.c_int, _vp, _vp, _vp, _vp],
     "fe_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "fe_adjoint_noalloc": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "fe_sync_status": [_vp],
     "fe_plan_enable_timing": [_vp, ctypes.c_int],
     "fe_plan_stage_times": [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int],

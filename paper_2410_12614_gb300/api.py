@@ -204,6 +204,18 @@ class Plan:
               "fe_adjoint")
         return L, gk, gx
 
+    def adjoint_noalloc(self, kappa, u, v, out_L, out_kappa=None, out_vertices=None, vertices=None):
+        """fe_adjoint_noalloc: the adjoint without any device allocation by the
+        library; the caller provides every output buffer."""
+        self._check_dev(kappa, torch.float64, (self.n_cells, self.n_q), "kappa")
+        self._check_dev(u, torch.float32, (self.n_dofs,), "u")
+        self._check_dev(v, torch.float32, (self.n_dofs,), "v")
+        self._check_dev(out_L, torch.float64, (1,), "out_L")
+        self._check_dev(out_kappa, torch.float64, (self.n_cells, self.n_q), "out_kappa")
+        self._check_dev(out_vertices, torch.float64, (self.n_vertices, self.d), "out_vertices")
+        check(load().fe_adjoint_noalloc(self._h, _ptr(vertices), _ptr(kappa), _ptr(u), _ptr(v), _ptr(out_kappa),
+                                        _ptr(out_vertices), _ptr(out_L)), "fe_adjoint_noalloc")
+
     def sync(self):
         check(load().fe_sync_status(self._h), "fe_sync_status")
 

@@ -623,4 +623,47 @@ fe_status fe_adjoint(fe_plan *plan, const double *vertices, const double *kappa,
     return FE_OK;
 }
 
+fe_status fe_adjoint_noalloc(fe_plan *plan, const double *vertices, const double *kappa, const float *u,
+                             const float *v, double *g_kappa, double *g_vertices, double *L_out) {
+    g_err.clear();
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (!(plan->form_mask & FE_FORM_STIFFNESS)) return fail(FE_ERR_INVALID_ARG, "plan does not serve stiffness");
+    if (!kappa || !u || !v) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+    const size_t per_cell = (g_vertices ? (size_t)(plan->d + 1) * plan->d : 0) + 1;
+    const size_t need = (size_t)plan->n_cells * per_cell;
+    if (need > kNoAllocScratchDoubles)
+        return fail(FE_ERR_UNSUPPORTED,
+                    "fe_adjoint_noalloc: %lld cells need %zu doubles of scratch, above the fixed capacity of %zu "
+                    "(%zu cells with vertex gradients, %zu without); use fe_adjoint",
+                    (long long)plan->n_cells, need, kNoAllocScratchDoubles,
+                    kNoAllocScratchDoubles / ((size_t)(plan->d + 1) * plan->d + 1), kNoAllocScratchDoubles);
+    double *scratch = nullptr;
+    FE_CUDA(noalloc_scratch(&scratch), "fe_adjoint_noalloc scratch lookup");
+    AdjArgs a{};
+    a.vertices = vertices ? vertices : plan->vertices.as<double>();
+    a.cells = plan->cells.as<int32_t>();
+    a.n_cells = plan->n_cells;
+    a.n_vertices = plan->n_vertices;
+    a.d = plan->d;
+    a.kappa = kappa;
+    a.weights = plan->weights.as<double>();
+    a.n_q = plan->n_q;
+    a.n_phi = plan->n_phi;
+    a.dphi = plan->dphi.as<double>();
+    a.cell_dofs = plan->cell_dofs.as<int32_t>();
+    a.u = u;
+    a.v = v;
+    a.g_kappa = g_kappa;
+    // every scratch entry read by the kernels is written earlier in the same call
+    a.L_cell = scratch;
+    a.g_cell_x = g_vertices ? scratch + plan->n_cells : nullptr;
+    a.status = plan->status.as<int>();
+    mark(plan, 2, true);
+    int r = launch_adjoint(a, plan->vinc_ptr.as<int64_t>(), plan->vinc.as<int32_t>(), g_vertices, L_out, plan->stream);
+    if (r < 0) return cuda_fail((cudaError_t)(-r), "adjoint kernel launch");
+    mark(plan, 2, false);
+    plan->last_launches = r;
+    return FE_OK;
+}
+
 }  // extern "C"

@@ -11,6 +11,8 @@
 // contributions and L_c; kernel 2 sums the contributions of each vertex in
 // increasing cell order (vertex incidence stream, no atomics); kernel 3 sums
 // L_c in a fixed order.  Everything is deterministic.
+#include <mutex>
+
 #include "fe_device.cuh"
 
 namespace fe {
@@ -131,6 +133,42 @@ __global__ void ordered_sum_kernel(const double *__restrict__ x, int64_t n, doub
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// Fixed scratch for fe_adjoint_noalloc.  Callers that may not allocate device
+// memory (their device memory belongs to their own allocator or a fixed
+// budget, or they cannot afford the implicit device synchronisation of
+// cudaMalloc / cudaFree inside a latency-critical loop) get the adjoint's
+// per-cell scratch -- the vertex-gradient contributions of every cell and the
+// per-cell L -- from this file-scope array instead of a plan workspace.  It is
+// part of the module, so every GPU that loads the library holds it until the
+// process exits.  In host code the name g_noalloc_scratch is only a host-side
+// stand-in: the device address comes from cudaGetSymbolAddress, looked up
+// once per device below with that device current.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+namespace {
+std::mutex g_noalloc_mutex;
+constexpr int kMaxDevices = 64;
+double *g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
+cudaError_t noalloc_scratch(double **ptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
 
 int launch_adjoint(const AdjArgs &a, const int64_t *vinc_ptr, const int32_t *vinc, double *g_vertices, double *L_out,
                    cudaStream_t s) {

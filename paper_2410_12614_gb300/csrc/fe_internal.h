@@ -127,6 +127,10 @@ size_t tc_smem_bytes(const TcArgs &a);
 bool tc_can_stage(const TcArgs &a);
 int launch_f64_elements(const F64Args &a, cudaStream_t s);
 int launch_assemble(const AsmArgs &a, bool fp64, cudaStream_t s);
+// Capacity (in doubles) of the fixed scratch array of the allocation-free
+// adjoint, and the lookup of its device address on the current device.
+constexpr size_t kNoAllocScratchDoubles = size_t(1) << 22;  // 32 MiB
+cudaError_t noalloc_scratch(double **ptr);
 int launch_adjoint(const AdjArgs &a, const int64_t *vert_inc_ptr, const int32_t *vert_inc, double *g_vertices,
                    double *L_out, cudaStream_t s);
 
