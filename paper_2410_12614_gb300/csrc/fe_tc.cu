@@ -107,21 +107,27 @@ __device__ inline Smem carve(uint8_t *raw, const TcArgs &a) {
     return s;
 }
 
-// FP64 -> FP32 with round-to-nearest-even (IEEE 754) done on the integer
-// units for results in the normal FP32 range; other inputs (zero,
-// subnormal, out of range, non-finite) take the hardware conversion.  The
-// exponent is rebiased in place and the 29 dropped mantissa bits are rounded
-// half to even.  Keeps the per-quadrature-point path off the FP64 pipe.
+// FP64 -> FP32 with round-to-nearest-even (IEEE 754), entirely on the
+// integer units so that the per-quadrature-point path never touches the FP64
+// pipe: the exponent is rebiased in place and the 29 dropped mantissa bits are
+// rounded half to even (a carry into the exponent gives the correctly rounded
+// power of two, and infinity past the largest finite value).  Magnitudes below
+// FP32's smallest normal number (2^-126) are flushed to a signed zero;
+// non-finite inputs set the flag and give infinity or NaN.
 __device__ __forceinline__ float f64_to_f32_rne(double x, int &nonfinite) {
     const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(x));
     const unsigned e = static_cast<unsigned>(u >> 52) & 0x7FFu;
-    if (e >= 1023u - 126u && e <= 1023u + 126u) {
-        const unsigned long long mag = (u & 0x7FFFFFFFFFFFFFFFull) - (static_cast<unsigned long long>(1023 - 127) << 52);
-        const unsigned long long r = mag + 0x0FFFFFFFull + ((mag >> 29) & 1ull);
-        return __uint_as_float(static_cast<unsigned>(r >> 29) | (static_cast<unsigned>(u >> 63) << 31));
+    const unsigned sign = static_cast<unsigned>(u >> 63) << 31;
+    const unsigned long long mag = (u & 0x7FFFFFFFFFFFFFFFull) - (static_cast<unsigned long long>(1023 - 127) << 52);
+    const unsigned long long r = mag + 0x0FFFFFFFull + ((mag >> 29) & 1ull);
+    unsigned bits = static_cast<unsigned>(r >> 29);
+    bits = (e < 1023u - 126u) ? 0u : bits;
+    bits = (e > 1023u + 127u) ? 0x7F800000u : bits;
+    if (e == 0x7FFu) {
+        nonfinite = 1;
+        bits = (u & 0xFFFFFFFFFFFFFull) ? 0x7FC00000u : 0x7F800000u;
     }
-    if (e == 0x7FFu) nonfinite = 1;
-    return static_cast<float>(x);
+    return __uint_as_float(bits | sign);
 }
 
 template <int PREC, int EP>
@@ -246,7 +252,20 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 for (int k = 0; k < RB * QL; ++k) dst[r0 * QL + k] = f64_to_f32_rne(raw[k], nonfinite) * om[k % QL];
             }
         };
+        // the coefficient and connectivity blocks of a tile are contiguous: pull the
+        // next tile's into L2 while this one is built
+        auto prefetch_tile = [&](int64_t tt) {
+            if (tt >= n_tiles || cl != 0) return;
+            const int64_t c0 = tt * TC_M;
+            const int64_t nc = (a.n_cells - c0) < TC_M ? (a.n_cells - c0) : TC_M;
+            const uint32_t kb = (uint32_t)((nc * a.n_q * 8) & ~int64_t(15));
+            const uint32_t cb = (uint32_t)((nc * (a.d + 1) * 4) & ~int64_t(15));
+            if (kb) prefetch_l2(a.kappa + c0 * a.n_q, kb);
+            if (cb) prefetch_l2(a.cells + c0 * (a.d + 1), cb);
+        };
+        prefetch_tile(blockIdx.x);
         for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
+            prefetch_tile(t + gridDim.x);
             const int64_t tile_cell0 = t * TC_M;
             const int64_t cell = tile_cell0 + cl;
             const bool valid = cell < a.n_cells;
