@@ -235,6 +235,37 @@ fe_status fe_adjoint(fe_plan *plan, const double *vertices, const double *kappa,
 fe_status fe_adjoint_noalloc(fe_plan *plan, const double *vertices, const double *kappa, const float *u,
                              const float *v, double *g_kappa, double *g_vertices, double *L_out);
 
+/* ---------------------------------------------------------------------- */
+/* Batches                                                                 */
+/* ---------------------------------------------------------------------- */
+
+/* A batch of plans run as one persistent tensor-core launch (the cell
+ * batching of Sec. 3.1, generalised to meshes of uneven size,
+ * cell type and degree) followed by one assembly launch over the rows of
+ * every plan, captured once in a CUDA graph and replayed by fe_batch_run.
+ * Each plan's tile shape (N-pass width) is the one its autotuner chose.
+ * plans: n_plans plans on the current device, each serving `forms` and
+ * `prec` (FE_PREC_FP64 runs the FP64 kernels, one per plan and form, inside
+ * the same graph).  kappa[i]: device coefficients of plan i.  A_stiffness /
+ * A_mass: arrays of n_plans device outputs (element matrices), or NULL (the
+ * batch owns workspaces); an entry may be NULL likewise.  csr_stiffness /
+ * csr_mass: arrays of n_plans device CSR value outputs, both NULL to skip
+ * assembly.  Every buffer must stay valid, at the same address, for the
+ * batch's lifetime: the graph reads and writes them at each run.
+ * cuda_stream must be a non-default stream.  Creation runs the batch once
+ * eagerly (errors surface there) and synchronises. */
+typedef struct fe_batch fe_batch;
+fe_status fe_batch_create(fe_batch **out, fe_plan *const *plans, int n_plans, unsigned forms, fe_precision prec,
+                          const double *const *kappa, void *const *A_stiffness, void *const *A_mass,
+                          void *const *csr_stiffness, void *const *csr_mass, void *cuda_stream);
+/* Replay the batch's graph on its stream (asynchronous). */
+fe_status fe_batch_run(fe_batch *batch);
+/* Wait for the batch's stream and report (and clear) its device status word. */
+fe_status fe_batch_sync(fe_batch *batch);
+/* Total cells and nnz over the plans, and kernel launches per run. */
+fe_status fe_batch_sizes(const fe_batch *batch, int64_t *n_cells, int64_t *nnz, int32_t *launches);
+fe_status fe_batch_destroy(fe_batch *batch);
+
 /* Wait for the plan's stream and report the device status word (and clear it). */
 fe_status fe_sync_status(fe_plan *plan);
 

@@ -64,6 +64,12 @@ SIGNATURES = {
     "fe_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "fe_adjoint_noalloc": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "fe_sync_status": [_vp],
+    "fe_batch_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_int,
+                        _vp, _vp, _vp, _vp, _vp, _vp],
+    "fe_batch_run": [_vp],
+    "fe_batch_sync": [_vp],
+    "fe_batch_sizes": [_vp, _pi64, _pi64, _pi32],
+    "fe_batch_destroy": [_vp],
     "fe_plan_enable_timing": [_vp, ctypes.c_int],
     "fe_plan_stage_times": [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int],
     "fe_plan_last_launches": [_vp, _pi32],

@@ -245,6 +245,63 @@ class Plan:
             pass
 
 
+class Batch:
+    """Several plans run as one persistent launch + one assembly launch, captured
+    in a CUDA graph (fe_batch_*).  Buffers are fixed at creation and reused by
+    every run()."""
+
+    def __init__(self, plans, kappas, forms=("stiffness", "mass"), prec="bf16", elements=True, assemble=True,
+                 stream: torch.cuda.Stream | None = None):
+        lib = load()
+        self.plans = list(plans)
+        n = len(self.plans)
+        self.forms = tuple(forms)
+        self.prec = prec
+        self.stream = stream if stream is not None else self.plans[0].stream
+        for p, k in zip(self.plans, kappas):
+            p._check_dev(k, torch.float64, (p.n_cells, p.n_q), "kappa")
+        self.kappas = list(kappas)
+        self.elements = {f: [p.empty_elements(prec) for p in self.plans] if elements else None for f in forms}
+        self.values = {f: [p.empty_values(prec) for p in self.plans] if assemble else None for f in forms}
+        arr = lambda xs: (ctypes.c_void_p * n)(*[ctypes.c_void_p(x.data_ptr()) for x in xs]) if xs is not None else None
+        self._keep = [(ctypes.c_void_p * n)(*[p._h for p in self.plans])]
+        kap = (ctypes.c_void_p * n)(*[ctypes.c_void_p(k.data_ptr()) for k in self.kappas])
+        a_s = arr(self.elements.get("stiffness")) if "stiffness" in forms and elements else None
+        a_m = arr(self.elements.get("mass")) if "mass" in forms and elements else None
+        c_s = arr(self.values.get("stiffness")) if "stiffness" in forms and assemble else None
+        c_m = arr(self.values.get("mass")) if "mass" in forms and assemble else None
+        self._keep += [kap, a_s, a_m, c_s, c_m]
+        mask = 0
+        for f in forms:
+            mask |= FORMS[f]
+        h = ctypes.c_void_p()
+        check(lib.fe_batch_create(ctypes.byref(h), self._keep[0], n, mask, PRECISIONS[prec], kap, a_s, a_m, c_s, c_m,
+                                  ctypes.c_void_p(self.stream.cuda_stream)), "fe_batch_create")
+        self._h = h
+        nc, nnz = ctypes.c_int64(), ctypes.c_int64()
+        nl = ctypes.c_int32()
+        check(lib.fe_batch_sizes(h, ctypes.byref(nc), ctypes.byref(nnz), ctypes.byref(nl)))
+        self.n_cells, self.nnz, self.launches = nc.value, nnz.value, nl.value
+
+    def run(self):
+        check(load().fe_batch_run(self._h), "fe_batch_run")
+
+    def sync(self):
+        check(load().fe_batch_sync(self._h), "fe_batch_sync")
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load().fe_batch_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class QuadraticForm(torch.autograd.Function):
     """L = v^T A(kappa, vertices) u for the stiffness form of a plan.
 

@@ -6,7 +6,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -88,6 +90,9 @@ struct fe_plan {
     int last_launches = 0;
     int stage_marks = 0;
     std::vector<int> host_status;
+    std::vector<double> h_phi, h_dphi;   // FP64 tabulation kept for re-packing operands
+    int tuned_np[6][2] = {};             // autotuned N-pass width per precision and form
+    int asm_wpb = 8;                     // autotuned assembly block size (warps)
     ~fe_plan() {
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
@@ -112,6 +117,9 @@ static cudaError_t upload(DevBuf &b, const std::vector<T> &v, cudaStream_t s) {
     if (v.empty()) return cudaSuccess;
     return cudaMemcpyAsync(b.p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s);
 }
+
+static fe_status pack_operand(fe_plan &P, int prec, int fi, int np_pass);
+static fe_status autotune_plan(fe_plan &P);
 
 extern "C" {
 
@@ -270,28 +278,22 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
     std::vector<int> zero(4, 0);
     FE_CUDA(upload(P.status, zero, s), "status word");
 
+    P.h_phi = phi;
+    P.h_dphi = dphi;
     for (int prec = 1; prec <= 5; ++prec) {
         if (!(prec_mask & FE_PREC_MASK(prec))) continue;
         for (unsigned form : {(unsigned)FE_FORM_STIFFNESS, (unsigned)FE_FORM_MASS}) {
             if (!(form_mask & form)) continue;
-            host::OperandImage img;
-            host::build_operand(prec, (int)form, d, P.n_phi, P.n_q, phi, dphi, img);
-            const int fi = form_index(form);
-            FE_CUDA(upload(P.img[prec][fi], img.bytes, s), "upload operand image");
-            TcOperand &o = P.op[prec][fi];
-            o.img = P.img[prec][fi].as<uint8_t>();
-            o.n_kchunks = img.n_kchunks;
-            o.n_qw = img.n_qw;
-            o.n_pairs = img.n_pairs;
-            o.n_pass = img.n_pass;
-            o.NP = img.NP;
-            o.n_cols = img.n_cols;
-            o.n_blk = img.n_blk;
-            o.p_inv_scale = (float)img.p_inv_scale;
+            fe_status st = pack_operand(P, prec, form_index(form), 0);
+            if (st) return st;
         }
     }
     FE_CUDA(cudaStreamSynchronize(s), "plan upload");
     for (auto &e : P.ev) FE_CUDA(cudaEventCreate(&e), "event");
+    {
+        fe_status st = autotune_plan(P);
+        if (st) return st;
+    }
     *out = pl.release();
     return FE_OK;
 }
@@ -399,6 +401,92 @@ static fe_status check_call(fe_plan *plan, unsigned forms, fe_precision prec) {
     return FE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// segments shared by single-plan calls and batches
+// ---------------------------------------------------------------------------
+static TcSeg make_tc_seg(fe_plan *P, unsigned forms, int prec, const double *vertices, const double *kappa,
+                         void *const A[2]) {
+    TcSeg g{};
+    g.vertices = vertices ? vertices : P->vertices.as<double>();
+    g.cells = P->cells.as<int32_t>();
+    g.n_cells = P->n_cells;
+    g.d = P->d;
+    g.kappa = kappa;
+    g.weights = P->weights.as<double>();
+    g.n_q = P->n_q;
+    g.n_phi = P->n_phi;
+    g.n_pairs = P->n_pairs;
+    g.form_mask = 0;
+    for (unsigned form : {(unsigned)FE_FORM_STIFFNESS, (unsigned)FE_FORM_MASS}) {
+        if (!(forms & form)) continue;
+        const int fi = form_index(form);
+        g.form_mask |= 1 << fi;
+        g.op[fi] = P->op[prec][fi];
+        g.out[fi] = static_cast<float *>(A[fi]);
+    }
+    g.sym_kl = P->sym_kl.as<int32_t>();
+    g.full2sym = P->full2sym.as<int16_t>();
+    g.staged = 0;
+    g.tile_begin = 0;
+    return g;
+}
+
+// Global launch shape over the segments: operand maxima, then the staged
+// epilogue for every segment that fits (greedy, in segment order).
+static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status) {
+    a.prec = prec;
+    a.elem_bytes = host::format_of(prec).elem_bytes;
+    a.idesc = idesc_for(prec);
+    a.target_exp = host::format_of(prec).target_exp;
+    a.np_max = 16;
+    a.nq_max = 1;
+    a.pitch_max = 0;
+    int64_t tiles = 0;
+    for (int i = 0; i < n; ++i) {
+        for (int f = 0; f < MAX_FORMS; ++f)
+            if ((segs[i].form_mask >> f) & 1) a.np_max = std::max(a.np_max, segs[i].op[f].NP);
+        a.nq_max = std::max(a.nq_max, segs[i].n_q);
+        segs[i].tile_begin = tiles;
+        tiles += (segs[i].n_cells + TC_M - 1) / TC_M;
+    }
+    a.n_tiles = tiles;
+    for (int i = 0; i < n; ++i) {
+        if (tc_can_stage(a, segs[i])) {
+            segs[i].staged = 1;
+            int np = 16;
+            for (int f = 0; f < MAX_FORMS; ++f)
+                if ((segs[i].form_mask >> f) & 1) np = std::max(np, segs[i].op[f].NP);
+            a.pitch_max = std::max(a.pitch_max, np + 1);
+        }
+    }
+    a.status = status;
+    a.timeout_ns = 2000000000ull;  // 2 s per CTA (a tile needs far less)
+}
+
+static AsmSeg make_asm_seg(fe_plan *P, unsigned forms, const void *const A[2], void *const csr[2]) {
+    AsmSeg g{};
+    g.n_rows = P->n_dofs;
+    g.row_ptr = P->row_ptr.as<int64_t>();
+    g.inc_ptr = P->inc_ptr.as<int64_t>();
+    g.inc_elem = P->inc_elem.as<int32_t>();
+    g.contrib_cnt = P->contrib_cnt.as<uint8_t>();
+    g.contrib_base = P->contrib_base.as<int64_t>();
+    g.contrib_code = P->contrib_code.as<uint16_t>();
+    g.n_phi = P->n_phi;
+    int nf = 0;
+    for (int fi = 0; fi < 2; ++fi) {
+        unsigned form = fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS;
+        if (!(forms & form)) continue;
+        g.A[nf] = A[fi];
+        g.out[nf] = csr[fi];
+        ++nf;
+    }
+    g.row_begin = 0;
+    return g;
+}
+
+static int n_forms_of(unsigned forms) { return ((forms & FE_FORM_STIFFNESS) ? 1 : 0) + ((forms & FE_FORM_MASS) ? 1 : 0); }
+
 static fe_status run_elements(fe_plan *P, unsigned forms, fe_precision prec, const double *vertices,
                               const double *kappa, void *A[2], int &launches) {
     const double *verts = vertices ? vertices : P->vertices.as<double>();
@@ -425,32 +513,10 @@ static fe_status run_elements(fe_plan *P, unsigned forms, fe_precision prec, con
         }
     } else {
         TcArgs a{};
-        a.vertices = verts;
-        a.cells = P->cells.as<int32_t>();
-        a.n_cells = P->n_cells;
-        a.d = P->d;
-        a.kappa = kappa;
-        a.weights = P->weights.as<double>();
-        a.n_q = P->n_q;
-        a.n_phi = P->n_phi;
-        a.n_pairs = P->n_pairs;
-        a.prec = (int)prec;
-        a.elem_bytes = host::format_of(prec).elem_bytes;
-        a.idesc = idesc_for(prec);
-        a.target_exp = host::format_of(prec).target_exp;
-        a.form_mask = 0;
-        for (unsigned form : {(unsigned)FE_FORM_STIFFNESS, (unsigned)FE_FORM_MASS}) {
-            if (!(forms & form)) continue;
-            const int fi = form_index(form);
-            a.form_mask |= 1 << fi;
-            a.op[fi] = P->op[prec][fi];
-            a.out[fi] = static_cast<float *>(A[fi]);
-        }
-        a.sym_kl = P->sym_kl.as<int32_t>();
-        a.full2sym = P->full2sym.as<int16_t>();
-        a.staged = tc_can_stage(a) ? 1 : 0;
-        a.status = P->status.as<int>();
-        a.timeout_ns = 1000000000ull;  // 1 s per CTA (a tile needs far less)
+        a.seg0 = make_tc_seg(P, forms, prec, verts, kappa, A);
+        a.segs = nullptr;
+        a.n_segs = 1;
+        tc_finalize(a, &a.seg0, 1, prec, P->status.as<int>());
         const size_t smem = tc_smem_bytes(a);
         int r = launch_tc_elements(a, smem, P->stream);
         if (r < 0) return cuda_fail((cudaError_t)(-r), "tensor-core element kernel launch");
@@ -467,32 +533,132 @@ static fe_status ensure_ws(DevBuf &b, size_t bytes, const char *what) {
 }
 
 static fe_status run_assembly(fe_plan *P, unsigned forms, bool fp64, const void *A[2], void *csr[2], int &launches) {
+    for (int fi = 0; fi < 2; ++fi)
+        if ((forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS)) && !csr[fi])
+            return fail(FE_ERR_INVALID_ARG, "NULL CSR output");
     AsmArgs a{};
+    a.seg0 = make_asm_seg(P, forms, A, csr);
+    a.segs = nullptr;
+    a.n_segs = 1;
     a.n_rows = P->n_dofs;
-    a.row_ptr = P->row_ptr.as<int64_t>();
-    a.inc_ptr = P->inc_ptr.as<int64_t>();
-    a.inc_elem = P->inc_elem.as<int32_t>();
-    a.inc_slot = nullptr;
-    a.contrib_cnt = P->contrib_cnt.as<uint8_t>();
-    a.contrib_base = P->contrib_base.as<int64_t>();
-    a.contrib_code = P->contrib_code.as<uint16_t>();
-    a.n_phi = P->n_phi;
-    a.max_row = P->max_row;
-    int nf = 0;
-    for (int fi = 0; fi < 2; ++fi) {
-        unsigned form = fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS;
-        if (!(forms & form)) continue;
-        if (!csr[fi]) return fail(FE_ERR_INVALID_ARG, "NULL CSR output");
-        a.A[nf] = A[fi];
-        a.out[nf] = csr[fi];
-        ++nf;
-    }
-    a.n_forms = nf;
+    a.n_forms = n_forms_of(forms);
     mark(P, 1, true);
-    int r = launch_assemble(a, fp64, P->stream);
+    int r = launch_assemble(a, fp64, P->stream, P->asm_wpb);
     if (r < 0) return cuda_fail((cudaError_t)(-r), "assembly kernel launch");
     launches += r;
     mark(P, 1, false);
+    return FE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// operand packing and the autotuner
+// ---------------------------------------------------------------------------
+static fe_status pack_operand(fe_plan &P, int prec, int fi, int np_pass) {
+    host::OperandImage img;
+    const unsigned form = fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS;
+    host::build_operand(prec, (int)form, P.d, P.n_phi, P.n_q, P.h_phi, P.h_dphi, img, np_pass);
+    FE_CUDA(upload(P.img[prec][fi], img.bytes, P.stream), "upload operand image");
+    TcOperand &o = P.op[prec][fi];
+    o.img = P.img[prec][fi].as<uint8_t>();
+    o.n_kchunks = img.n_kchunks;
+    o.n_qw = img.n_qw;
+    o.n_pairs = img.n_pairs;
+    o.n_pass = img.n_pass;
+    o.NP = img.NP;
+    o.n_cols = img.n_cols;
+    o.n_blk = img.n_blk;
+    o.p_inv_scale = (float)img.p_inv_scale;
+    P.tuned_np[prec][fi] = img.NP;
+    return FE_OK;
+}
+
+namespace {
+std::mutex g_tune_mutex;
+std::map<std::string, int> g_tune_cache;  // "(d,p,n_q,prec,form)" -> N-pass width
+}  // namespace
+
+// Autotuner for the tile shape of every (cell type, degree, quadrature size,
+// precision, form): the N-pass width of the contraction (how many upper-
+// triangle columns one accumulator holds).  Candidates come from
+// host::np_candidates; each is timed with CUDA events on a sample of this
+// plan's own cells (unit coefficient) and the fastest is kept.  Results are
+// cached per key for the life of the process.  FE_GB300_AUTOTUNE=0 keeps the
+// default shapes.
+static fe_status autotune_plan(fe_plan &P) {
+    const char *env = getenv("FE_GB300_AUTOTUNE");
+    if (env && env[0] == '0') return FE_OK;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int prec = 1; prec <= 5; ++prec) {
+        if (!(P.prec_mask & FE_PREC_MASK(prec))) continue;
+        for (int fi = 0; fi < 2; ++fi) {
+            const unsigned form = fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS;
+            if (!(P.form_mask & form)) continue;
+            std::vector<int> cand = host::np_candidates(P.n_sym);
+            if (cand.size() < 2) continue;
+            char key[96];
+            snprintf(key, sizeof(key), "%d,%d,%d,%d,%d", P.d, P.p, P.n_q, prec, fi);
+            int best = -1;
+            {
+                std::lock_guard<std::mutex> lock(g_tune_mutex);
+                auto it = g_tune_cache.find(key);
+                if (it != g_tune_cache.end()) best = it->second;
+            }
+            if (best < 0) {
+                // sample: at most one tile per SM and at most 256 MB of element output
+                int64_t n = std::min<int64_t>(P.n_cells, (int64_t)sms * TC_M);
+                n = std::min<int64_t>(n, std::max<int64_t>(TC_M, (256ll << 20) / (4ll * P.n_phi * P.n_phi)));
+                DevBuf kap, out;
+                FE_CUDA(kap.alloc(sizeof(double) * n * P.n_q), "autotune buffer");
+                FE_CUDA(out.alloc(sizeof(float) * n * P.n_phi * P.n_phi), "autotune buffer");
+                std::vector<double> ones((size_t)n * P.n_q, 1.0);
+                FE_CUDA(cudaMemcpyAsync(kap.p, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice,
+                                        P.stream), "autotune upload");
+                float best_ms = 1e30f;
+                for (int np : cand) {
+                    fe_status st = pack_operand(P, prec, fi, np);
+                    if (st) return st;
+                    void *A[2] = {nullptr, nullptr};
+                    A[fi] = out.p;
+                    TcArgs a{};
+                    a.seg0 = make_tc_seg(&P, form, prec, nullptr, kap.as<double>(), A);
+                    a.seg0.n_cells = n;
+                    a.n_segs = 1;
+                    tc_finalize(a, &a.seg0, 1, prec, P.status.as<int>());
+                    const size_t smem = tc_smem_bytes(a);
+                    float ms_min = 1e30f;
+                    for (int rep = 0; rep < 3; ++rep) {
+                        FE_CUDA(cudaEventRecord(P.ev[4], P.stream), "autotune event");
+                        int r = launch_tc_elements(a, smem, P.stream);
+                        if (r < 0) return cuda_fail((cudaError_t)(-r), "autotune launch");
+                        FE_CUDA(cudaEventRecord(P.ev[5], P.stream), "autotune event");
+                        FE_CUDA(cudaEventSynchronize(P.ev[5]), "autotune sync");
+                        float ms = 0.f;
+                        cudaEventElapsedTime(&ms, P.ev[4], P.ev[5]);
+                        if (rep > 0) ms_min = std::min(ms_min, ms);
+                    }
+                    if (ms_min < best_ms) {
+                        best_ms = ms_min;
+                        best = np;
+                    }
+                }
+                int stw = 0;
+                cudaMemcpy(&stw, P.status.p, sizeof(int), cudaMemcpyDeviceToHost);
+                if (stw) {
+                    cudaMemset(P.status.p, 0, sizeof(int));
+                    return fail(FE_ERR_CUDA, "autotune run reported status %d", stw);
+                }
+                std::lock_guard<std::mutex> lock(g_tune_mutex);
+                g_tune_cache[key] = best;
+            }
+            if (P.op[prec][fi].NP != best) {
+                fe_status st = pack_operand(P, prec, fi, best);
+                if (st) return st;
+            }
+        }
+    }
+    FE_CUDA(cudaStreamSynchronize(P.stream), "autotune");
     return FE_OK;
 }
 
@@ -663,6 +829,208 @@ fe_status fe_adjoint_noalloc(fe_plan *plan, const double *vertices, const double
     if (r < 0) return cuda_fail((cudaError_t)(-r), "adjoint kernel launch");
     mark(plan, 2, false);
     plan->last_launches = r;
+    return FE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct fe_batch {
+    std::vector<fe_plan *> plans;
+    unsigned forms = 0;
+    int prec = 0;
+    cudaStream_t stream = nullptr;
+    TcArgs targs{};
+    AsmArgs aargs{};
+    size_t smem = 0;
+    bool assemble = false;
+    DevBuf tc_segs, asm_segs, status;
+    std::vector<std::unique_ptr<DevBuf>> ws;
+    std::vector<F64Args> f64;   // FP64 path: one launch per plan and form
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t n_cells = 0, nnz = 0;
+    int launches = 0;
+    ~fe_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
+static fe_status batch_launch(fe_batch &B, int &launches) {
+    launches = 0;
+    if (B.prec == FE_PREC_FP64) {
+        for (const F64Args &f : B.f64) {
+            int r = launch_f64_elements(f, B.stream);
+            if (r < 0) return cuda_fail((cudaError_t)(-r), "FP64 element kernel launch");
+            launches += r;
+        }
+    } else {
+        int r = launch_tc_elements(B.targs, B.smem, B.stream);
+        if (r < 0) return cuda_fail((cudaError_t)(-r), "tensor-core element kernel launch");
+        launches += r;
+    }
+    if (B.assemble) {
+        int r = launch_assemble(B.aargs, B.prec == FE_PREC_FP64, B.stream, B.plans[0]->asm_wpb);
+        if (r < 0) return cuda_fail((cudaError_t)(-r), "assembly kernel launch");
+        launches += r;
+    }
+    return FE_OK;
+}
+
+extern "C" {
+
+fe_status fe_batch_create(fe_batch **out, fe_plan *const *plans, int n_plans, unsigned forms, fe_precision prec,
+                          const double *const *kappa, void *const *A_stiffness, void *const *A_mass,
+                          void *const *csr_stiffness, void *const *csr_mass, void *cuda_stream) {
+    g_err.clear();
+    if (!out || !plans || !kappa || n_plans <= 0) return fail(FE_ERR_INVALID_ARG, "NULL argument or empty batch");
+    *out = nullptr;
+    if (!cuda_stream) return fail(FE_ERR_INVALID_ARG, "a batch needs a non-default stream (it is captured in a graph)");
+    if ((int)prec < 0 || (int)prec > 5) return fail(FE_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+    if (forms == 0 || (forms & ~3u)) return fail(FE_ERR_INVALID_ARG, "bad form mask");
+    const bool want_csr = csr_stiffness || csr_mass;
+    for (int i = 0; i < n_plans; ++i) {
+        fe_status st = check_call(plans[i], forms, prec);
+        if (st) return st;
+        if (!kappa[i]) return fail(FE_ERR_INVALID_ARG, "NULL kappa for plan %d", i);
+        if (want_csr) {
+            if ((forms & FE_FORM_STIFFNESS) && (!csr_stiffness || !csr_stiffness[i]))
+                return fail(FE_ERR_INVALID_ARG, "NULL stiffness CSR output for plan %d", i);
+            if ((forms & FE_FORM_MASS) && (!csr_mass || !csr_mass[i]))
+                return fail(FE_ERR_INVALID_ARG, "NULL mass CSR output for plan %d", i);
+        }
+    }
+    auto bt = std::make_unique<fe_batch>();
+    fe_batch &B = *bt;
+    B.plans.assign(plans, plans + n_plans);
+    B.forms = forms;
+    B.prec = (int)prec;
+    B.stream = static_cast<cudaStream_t>(cuda_stream);
+    B.assemble = want_csr;
+    std::vector<int> zero(4, 0);
+    FE_CUDA(upload(B.status, zero, B.stream), "batch status");
+    const bool fp64 = prec == FE_PREC_FP64;
+    std::vector<TcSeg> tsegs;
+    std::vector<AsmSeg> asegs;
+    int64_t rows = 0;
+    for (int i = 0; i < n_plans; ++i) {
+        fe_plan *P = plans[i];
+        void *A[2] = {A_stiffness ? A_stiffness[i] : nullptr, A_mass ? A_mass[i] : nullptr};
+        const size_t ebytes = (fp64 ? 8 : 4) * (size_t)P->n_cells * P->n_phi * P->n_phi;
+        for (int fi = 0; fi < 2; ++fi) {
+            if (!(forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS)) || A[fi]) continue;
+            B.ws.emplace_back(new DevBuf);
+            fe_status st = ensure_ws(*B.ws.back(), ebytes, "batch element workspace");
+            if (st) return st;
+            A[fi] = B.ws.back()->p;
+        }
+        B.n_cells += P->n_cells;
+        B.nnz += P->nnz;
+        if (fp64) {
+            for (unsigned form : {(unsigned)FE_FORM_STIFFNESS, (unsigned)FE_FORM_MASS}) {
+                if (!(forms & form)) continue;
+                F64Args a{};
+                a.vertices = P->vertices.as<double>();
+                a.cells = P->cells.as<int32_t>();
+                a.n_cells = P->n_cells;
+                a.d = P->d;
+                a.kappa = kappa[i];
+                a.weights = P->weights.as<double>();
+                a.n_q = P->n_q;
+                a.n_phi = P->n_phi;
+                a.tab = (form == FE_FORM_STIFFNESS) ? P->dphi.as<double>() : P->phi.as<double>();
+                a.form = (int)form;
+                a.out = static_cast<double *>(A[form_index(form)]);
+                a.status = B.status.as<int>();
+                B.f64.push_back(a);
+            }
+        } else {
+            tsegs.push_back(make_tc_seg(P, forms, (int)prec, nullptr, kappa[i], A));
+        }
+        if (want_csr) {
+            void *csr[2] = {csr_stiffness ? csr_stiffness[i] : nullptr, csr_mass ? csr_mass[i] : nullptr};
+            const void *Ac[2] = {A[0], A[1]};
+            asegs.push_back(make_asm_seg(P, forms, Ac, csr));
+            asegs.back().row_begin = rows;
+            rows += P->n_dofs;
+        }
+    }
+    if (!fp64) {
+        TcArgs &a = B.targs;
+        tc_finalize(a, tsegs.data(), (int)tsegs.size(), (int)prec, B.status.as<int>());
+        FE_CUDA(upload(B.tc_segs, tsegs, B.stream), "upload batch segments");
+        a.segs = B.tc_segs.as<TcSeg>();
+        a.n_segs = (int)tsegs.size();
+        B.smem = tc_smem_bytes(a);
+        if (B.smem > 227 * 1024) return fail(FE_ERR_UNSUPPORTED, "batch shapes need %zu bytes of shared memory", B.smem);
+    }
+    if (want_csr) {
+        FE_CUDA(upload(B.asm_segs, asegs, B.stream), "upload batch assembly segments");
+        B.aargs.segs = B.asm_segs.as<AsmSeg>();
+        B.aargs.n_segs = (int)asegs.size();
+        B.aargs.n_rows = rows;
+        B.aargs.n_forms = n_forms_of(forms);
+    }
+    // one eager run (sets kernel attributes, checks the inputs), then capture
+    int launches = 0;
+    fe_status st = batch_launch(B, launches);
+    if (st) return st;
+    FE_CUDA(cudaStreamSynchronize(B.stream), "batch warm-up");
+    int stw = 0;
+    FE_CUDA(cudaMemcpy(&stw, B.status.p, sizeof(int), cudaMemcpyDeviceToHost), "batch status");
+    if (stw) return fail(stw & ST_TIMEOUT ? FE_ERR_TIMEOUT : (stw & ST_NONFINITE ? FE_ERR_NONFINITE : FE_ERR_DEGENERATE_CELL),
+                         "batch warm-up reported status %d", stw);
+    FE_CUDA(cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    st = batch_launch(B, launches);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(B.stream, &g);
+    if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    B.graph = g;
+    FE_CUDA(cudaGraphInstantiate(&B.exec, B.graph, 0), "graph instantiate");
+    B.launches = launches;
+    *out = bt.release();
+    return FE_OK;
+}
+
+fe_status fe_batch_run(fe_batch *batch) {
+    g_err.clear();
+    if (!batch) return fail(FE_ERR_INVALID_ARG, "NULL batch");
+    FE_CUDA(cudaGraphLaunch(batch->exec, batch->stream), "graph launch");
+    return FE_OK;
+}
+
+fe_status fe_batch_sync(fe_batch *batch) {
+    if (!batch) return fail(FE_ERR_INVALID_ARG, "NULL batch");
+    int st = 0;
+    FE_CUDA(cudaStreamSynchronize(batch->stream), "sync");
+    FE_CUDA(cudaMemcpy(&st, batch->status.p, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    if (st) FE_CUDA(cudaMemset(batch->status.p, 0, sizeof(int)), "clear status");
+    if (st & ST_TIMEOUT) return fail(FE_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
+    if (st & ST_NONFINITE) return fail(FE_ERR_NONFINITE, "non-finite geometry or coefficient");
+    if (st & ST_DEGENERATE) return fail(FE_ERR_DEGENERATE_CELL, "degenerate cell (det J == 0)");
+    return FE_OK;
+}
+
+fe_status fe_batch_sizes(const fe_batch *batch, int64_t *n_cells, int64_t *nnz, int32_t *launches) {
+    if (!batch) return fail(FE_ERR_INVALID_ARG, "NULL batch");
+    if (n_cells) *n_cells = batch->n_cells;
+    if (nnz) *nnz = batch->nnz;
+    if (launches) *launches = batch->launches;
+    return FE_OK;
+}
+
+fe_status fe_batch_destroy(fe_batch *batch) {
+    if (batch) {
+        cudaStreamSynchronize(batch->stream);
+        delete batch;
+    }
     return FE_OK;
 }
 

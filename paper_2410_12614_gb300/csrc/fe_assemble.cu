@@ -17,25 +17,38 @@ namespace fe {
 
 namespace {
 
+// Segment of a global row (binary search over the segments' first rows).
+__device__ __forceinline__ const AsmSeg &aseg_of(const AsmArgs &a, int64_t row) {
+    if (a.segs == nullptr) return a.seg0;
+    int lo = 0, hi = a.n_segs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.segs[mid].row_begin <= row) lo = mid; else hi = mid - 1;
+    }
+    return a.segs[lo];
+}
+
 template <typename T, int NF>
 __global__ void __launch_bounds__(256) assemble_kernel(const __grid_constant__ AsmArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const T *__restrict__ A0 = static_cast<const T *>(a.A[0]);
-    const T *__restrict__ A1 = static_cast<const T *>(a.A[NF > 1 ? 1 : 0]);
-    T *O0 = static_cast<T *>(a.out[0]);
-    T *O1 = static_cast<T *>(a.out[NF > 1 ? 1 : 0]);
-    const uint32_t nph = (uint32_t)a.n_phi;
     const int64_t total_warps = (int64_t)gridDim.x * a.warps_per_block;
-    for (int64_t row = (int64_t)blockIdx.x * a.warps_per_block + warp; row < a.n_rows; row += total_warps) {
-        const int64_t r0 = __ldg(a.row_ptr + row);
-        const int len = (int)(__ldg(a.row_ptr + row + 1) - r0);
-        const int64_t i0 = __ldg(a.inc_ptr + row);
-        const int ninc = (int)(__ldg(a.inc_ptr + row + 1) - i0);
-        const int myelem = (lane < ninc) ? __ldg(a.inc_elem + i0 + lane) : 0;
-        int64_t off = __ldg(a.contrib_base + row);
+    for (int64_t grow = (int64_t)blockIdx.x * a.warps_per_block + warp; grow < a.n_rows; grow += total_warps) {
+        const AsmSeg &S = aseg_of(a, grow);
+        const int64_t row = grow - S.row_begin;
+        const T *__restrict__ A0 = static_cast<const T *>(S.A[0]);
+        const T *__restrict__ A1 = static_cast<const T *>(S.A[NF > 1 ? 1 : 0]);
+        T *O0 = static_cast<T *>(S.out[0]);
+        T *O1 = static_cast<T *>(S.out[NF > 1 ? 1 : 0]);
+        const uint32_t nph = (uint32_t)S.n_phi;
+        const int64_t r0 = __ldg(S.row_ptr + row);
+        const int len = (int)(__ldg(S.row_ptr + row + 1) - r0);
+        const int64_t i0 = __ldg(S.inc_ptr + row);
+        const int ninc = (int)(__ldg(S.inc_ptr + row + 1) - i0);
+        const int myelem = (lane < ninc) ? __ldg(S.inc_elem + i0 + lane) : 0;
+        int64_t off = __ldg(S.contrib_base + row);
         for (int j0 = 0; j0 < len; j0 += 32) {
             const int j = j0 + lane;
-            const int cnt = (j < len) ? (int)__ldg(a.contrib_cnt + r0 + j) : 0;
+            const int cnt = (j < len) ? (int)__ldg(S.contrib_cnt + r0 + j) : 0;
             // exclusive scan and maximum of the counts over the warp
             int incl = cnt, mx = cnt;
 #pragma unroll
@@ -48,10 +61,10 @@ __global__ void __launch_bounds__(256) assemble_kernel(const __grid_constant__ A
             T s0 = T(0), s1 = T(0);
             for (int k = 0; k < mx; ++k) {
                 const bool v = k < cnt;
-                const uint32_t code = v ? (uint32_t)__ldg(a.contrib_code + start + k) : 0u;
+                const uint32_t code = v ? (uint32_t)__ldg(S.contrib_code + start + k) : 0u;
                 const int t = (int)(code & 0xFFu);
                 int el = __shfl_sync(0xffffffffu, myelem, t & 31);
-                if (t >= 32) el = __ldg(a.inc_elem + i0 + t);
+                if (t >= 32) el = __ldg(S.inc_elem + i0 + t);
                 if (v) {
                     const uint32_t e = (uint32_t)el * nph + (code >> 8);
                     s0 += __ldg(A0 + e);
@@ -68,15 +81,14 @@ __global__ void __launch_bounds__(256) assemble_kernel(const __grid_constant__ A
 }
 
 template <typename T>
-int launch_t(const AsmArgs &a0, cudaStream_t s) {
+int launch_t(const AsmArgs &a0, cudaStream_t s, int wpb) {
     AsmArgs a = a0;
-    const int wpb = 8;
     a.warps_per_block = wpb;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int64_t blocks = (a.n_rows + wpb - 1) / wpb;
-    const int64_t cap = (int64_t)sms * 8 * 4;
+    const int64_t cap = (int64_t)sms * (2048 / (32 * wpb)) * 4;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     if (a.n_forms == 2) assemble_kernel<T, 2><<<(unsigned)blocks, wpb * 32, 0, s>>>(a);
@@ -88,9 +100,10 @@ int launch_t(const AsmArgs &a0, cudaStream_t s) {
 
 }  // namespace
 
-int launch_assemble(const AsmArgs &a, bool fp64, cudaStream_t s) {
+int launch_assemble(const AsmArgs &a, bool fp64, cudaStream_t s, int warps_per_block) {
     if (a.n_rows <= 0) return 0;
-    return fp64 ? launch_t<double>(a, s) : launch_t<float>(a, s);
+    if (warps_per_block < 1 || warps_per_block > 8) warps_per_block = 8;
+    return fp64 ? launch_t<double>(a, s, warps_per_block) : launch_t<float>(a, s, warps_per_block);
 }
 
 }  // namespace fe

@@ -517,8 +517,25 @@ uint32_t encode(int prec, double r) {
     return (sign << 7) | ((uint32_t)(E + 7) << 3) | mant;
 }
 
+std::vector<int> np_candidates(int n_sym) {
+    std::vector<int> out;
+    if (n_sym <= 256) {
+        out.push_back((n_sym + 15) / 16 * 16);
+        return out;
+    }
+    const int passes = (n_sym + 255) / 256;
+    out.push_back(256);
+    // the narrowest multiple of 16 with the same number of passes
+    int np = ((n_sym + passes - 1) / passes + 15) / 16 * 16;
+    if (np != 256) out.push_back(np);
+    // one more pass with narrower tiles
+    int np2 = ((n_sym + passes) / (passes + 1) + 15) / 16 * 16;
+    if (np2 >= 64 && np2 != np && np2 != 256) out.push_back(np2);
+    return out;
+}
+
 void build_operand(int prec, int form, int d, int n_phi_, int n_q, const std::vector<double> &phi,
-                   const std::vector<double> &dphi, OperandImage &img) {
+                   const std::vector<double> &dphi, OperandImage &img, int np_pass) {
     const Format F = format_of(prec);
     const int eb = F.elem_bytes;
     const int KCE = 128 / eb;
@@ -565,7 +582,10 @@ void build_operand(int prec, int form, int d, int n_phi_, int n_q, const std::ve
     img.n_qw = (n_q + KCE - 1) / KCE;
     img.n_kchunks = img.n_qw * n_pairs * img.n_blk;
     img.n_cols = n_sym;
-    if (n_sym <= 256) {
+    if (np_pass >= 16 && np_pass <= 256 && np_pass % 16 == 0) {
+        img.NP = np_pass;
+        img.n_pass = (n_sym + np_pass - 1) / np_pass;
+    } else if (n_sym <= 256) {
         img.NP = (n_sym + 15) / 16 * 16;
         img.n_pass = 1;
     } else {

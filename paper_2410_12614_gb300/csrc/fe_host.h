@@ -67,8 +67,13 @@ struct OperandImage {
     int n_kchunks = 0, n_qw = 0, n_pairs = 1, n_pass = 0, NP = 0, n_cols = 0, n_blk = 1;
     double p_inv_scale = 1.0;
 };
+// np_pass: N columns per pass (multiple of 16 in 16..256), or 0 for the
+// default (one pass if n_sym <= 256, else passes of 256).
 void build_operand(int prec, int form, int d, int n_phi, int n_q, const std::vector<double> &phi,
-                   const std::vector<double> &dphi, OperandImage &img);
+                   const std::vector<double> &dphi, OperandImage &img, int np_pass = 0);
+// Candidate pass widths for the autotuner: the default and the narrowest
+// widths that keep the minimal number of passes (least column padding).
+std::vector<int> np_candidates(int n_sym);
 
 unsigned hardware_threads();
 

@@ -42,7 +42,8 @@ struct TcOperand {
     float p_inv_scale = 1.f;       // 2^-e_P
 };
 
-struct TcArgs {
+// One plan's share of a (possibly batched) tensor-core element launch.
+struct TcSeg {
     const double *vertices;
     const int32_t *cells;
     int64_t n_cells;
@@ -52,16 +53,27 @@ struct TcArgs {
     int n_q;
     int n_phi;
     int n_pairs;      // d(d+1)/2
-    int prec;         // fe_precision
-    int elem_bytes;   // storage bytes per operand element
-    uint32_t idesc;   // instruction descriptor without the N field
-    int target_exp;   // per-cell scale target: max|C| * 2^e in [2^(t-1), 2^t)
     int form_mask;    // bit 0 stiffness, bit 1 mass (internal order)
     TcOperand op[MAX_FORMS];
     float *out[MAX_FORMS];
-    const int32_t *sym_kl;     // [n_sym_pad] k | l << 16
+    const int32_t *sym_kl;     // [n_sym] k | l << 16
     const int16_t *full2sym;   // [n_phi * n_phi]
     int staged;                // 1: staged coalesced epilogue (single pass)
+    int64_t tile_begin;        // first global tile of this segment
+};
+
+struct TcArgs {
+    TcSeg seg0;                // the only segment when segs == nullptr
+    const TcSeg *segs;         // device array of n_segs segments (batched launch)
+    int n_segs;
+    int64_t n_tiles;           // total tiles over all segments
+    int prec;                  // fe_precision
+    int elem_bytes;            // storage bytes per operand element
+    uint32_t idesc;            // instruction descriptor without the N field
+    int target_exp;            // per-cell scale target: max|C| * 2^e in [2^(t-1), 2^t)
+    int np_max;                // largest N per pass over the segments
+    int nq_max;                // largest n_q
+    int pitch_max;             // staging pitch (floats) over staged segments, 0 if none
     int *status;
     unsigned long long timeout_ns;
 };
@@ -83,20 +95,27 @@ struct F64Args {
     int *status;
 };
 
-struct AsmArgs {
+// One plan's share of a (possibly batched) assembly launch.
+struct AsmSeg {
     int64_t n_rows;
     const int64_t *row_ptr;
     const int64_t *inc_ptr;    // [n_rows + 1] into inc_elem
     const int32_t *inc_elem;   // element-row ids c * n_phi + k, sorted by (row, c)
-    const uint16_t *inc_slot;  // [n_inc][n_phi] position of dof(c,l) inside the row
     const uint8_t *contrib_cnt;     // [nnz] number of element entries summed into each CSR value
     const int64_t *contrib_base;    // [n_rows + 1] first contribution code of each row
     const uint16_t *contrib_code;   // incidence index | local column << 8, per row in slot order
     int n_phi;
-    int n_forms;
     const void *A[MAX_FORMS];
     void *out[MAX_FORMS];
-    int max_row;
+    int64_t row_begin;         // first global row of this segment
+};
+
+struct AsmArgs {
+    AsmSeg seg0;               // the only segment when segs == nullptr
+    const AsmSeg *segs;        // device array (batched launch)
+    int n_segs;
+    int64_t n_rows;            // total rows over all segments
+    int n_forms;
     int warps_per_block;
 };
 
@@ -122,11 +141,12 @@ struct AdjArgs {
 
 // Kernel launchers (defined in the .cu files).  Return the number of
 // kernel launches made, or a negative cudaError_t on launch failure.
-int launch_tc_elements(const TcArgs &a, size_t smem_bytes, cudaStream_t s);
+int launch_tc_elements(const TcArgs &a, size_t smem_bytes, cudaStream_t s, int grid = 0);
 size_t tc_smem_bytes(const TcArgs &a);
-bool tc_can_stage(const TcArgs &a);
+// Whether a segment can use the staged epilogue under the given global shape.
+bool tc_can_stage(const TcArgs &a, const TcSeg &seg);
 int launch_f64_elements(const F64Args &a, cudaStream_t s);
-int launch_assemble(const AsmArgs &a, bool fp64, cudaStream_t s);
+int launch_assemble(const AsmArgs &a, bool fp64, cudaStream_t s, int warps_per_block = 8);
 // Capacity (in doubles) of the fixed scratch array of the allocation-free
 // adjoint, and the lookup of its device address on the current device.
 constexpr size_t kNoAllocScratchDoubles = size_t(1) << 22;  // 32 MiB

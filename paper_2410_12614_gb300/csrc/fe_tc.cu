@@ -1,5 +1,5 @@
 // Tensor-core element-matrix kernel (sm_103a, tcgen05), persistent and
-// warp-specialised.
+// warp-specialised, over one plan or a batch of plans (segments).
 //
 // Algorithm 1 of the paper for a tile of 128 cells at once, written as one
 // dense contraction per tile with the cells on the MMA M dimension:
@@ -17,7 +17,11 @@
 // strategy of Sec. 4.5.  Only the upper triangle k <= l is computed; the
 // epilogue mirrors it.
 //
-// One CTA per SM walks its tiles; a job is one (tile, form, N pass).  Roles:
+// The cell batching of Sec. 3.1 is generalised to uneven meshes: the global
+// tile sequence is the concatenation of every segment's (plan's) tiles, each
+// tile carrying its segment's shapes (cell type, degree, quadrature size) and
+// buffers.  One CTA per SM walks its tiles; a job is one (tile, form, N pass).
+// Roles:
 //   warps 0-3  builders: FP64 geometry with one thread per cell; the FP32
 //              coefficient window w_q kappa_cq loaded coalesced (one lane per
 //              quadrature point, shared by every (s,t) pair and both forms)
@@ -48,35 +52,25 @@ constexpr int W_MMA = 12;
 constexpr int RING = 2;          // A and B ring stages
 constexpr int ACC_COLS = 256;    // columns per TMEM accumulator (2 of them)
 constexpr int MAX_F2S_IT = 16;   // n_phi^2 <= 512 for the staged epilogue
+constexpr int BAR_BUILDERS = 5;  // named barrier of the 128 builder threads
 
 struct Smem {
     uint8_t *A;        // [RING][128][128 B]
-    uint8_t *B;        // [RING][NPmax][128 B]
-    float *stage;      // [4][32][pitch]
+    uint8_t *B;        // [RING][np_max][128 B]
+    float *stage;      // [4][32][pitch_max]
     float *meta;       // [2][128] unscale per cell for the two accumulators
     float *rowc;       // [128][8] per cell: G pairs * scale (stiffness), |det J| * scale (mass)
-    float *omega;      // [n_q]
-    int16_t *f2s;      // [n_phi^2] full position -> sym column (staged only)
+    float *omega;      // [nq_max] quadrature weights of the current segment
     uint64_t *a_full, *a_empty, *b_full, *b_empty, *acc_full, *acc_empty, *meta_full, *meta_empty, *drain;
     uint32_t *tmem_holder;
     int *flags;        // [0] abort, [1] status bits
 };
 
-__host__ __device__ inline int np_max(const TcArgs &a) {
-    int m = 16;
-    for (int f = 0; f < MAX_FORMS; ++f)
-        if (a.form_mask & (1 << f)) m = (a.op[f].NP > m) ? a.op[f].NP : m;
-    return m;
-}
-
-__host__ __device__ inline int stage_pitch(const TcArgs &a) { return np_max(a) + 1; }
-
 __host__ __device__ inline size_t align1k(size_t x) { return (x + 1023) & ~size_t(1023); }
-
 __host__ __device__ inline size_t bytes_A() { return (size_t)RING * TC_M * TC_CHUNK_BYTES; }
-__host__ __device__ inline size_t bytes_B(const TcArgs &a) { return (size_t)RING * np_max(a) * TC_CHUNK_BYTES; }
+__host__ __device__ inline size_t bytes_B(const TcArgs &a) { return (size_t)RING * a.np_max * TC_CHUNK_BYTES; }
 __host__ __device__ inline size_t bytes_stage(const TcArgs &a) {
-    return a.staged ? align1k((size_t)4 * 32 * stage_pitch(a) * sizeof(float)) : 0;
+    return a.pitch_max > 0 ? align1k((size_t)4 * 32 * a.pitch_max * sizeof(float)) : 0;
 }
 
 __device__ inline Smem carve(uint8_t *raw, const TcArgs &a) {
@@ -89,8 +83,7 @@ __device__ inline Smem carve(uint8_t *raw, const TcArgs &a) {
     s.meta = reinterpret_cast<float *>(q);
     s.rowc = s.meta + 2 * TC_M;
     s.omega = s.rowc + 8 * TC_M;
-    s.f2s = reinterpret_cast<int16_t *>(s.omega + ((a.n_q + 3) & ~3));
-    q = reinterpret_cast<uint8_t *>(s.f2s + (a.staged ? ((a.n_phi * a.n_phi + 3) & ~3) : 0));
+    q = reinterpret_cast<uint8_t *>(s.omega + ((a.nq_max + 3) & ~3));
     q = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(q) + 7) & ~uintptr_t(7));
     uint64_t *b = reinterpret_cast<uint64_t *>(q);
     s.a_full = b;
@@ -106,6 +99,19 @@ __device__ inline Smem carve(uint8_t *raw, const TcArgs &a) {
     s.flags = reinterpret_cast<int *>(s.tmem_holder + 2);
     return s;
 }
+
+// Segment of a global tile (binary search over the segments' first tiles).
+__device__ __forceinline__ const TcSeg &seg_of(const TcArgs &a, int64_t t) {
+    if (a.segs == nullptr) return a.seg0;
+    int lo = 0, hi = a.n_segs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.segs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    }
+    return a.segs[lo];
+}
+
+__device__ __forceinline__ int first_form(const TcSeg &S) { return (S.form_mask & 1) ? 0 : 1; }
 
 // FP64 -> FP32 with round-to-nearest-even (IEEE 754), entirely on the
 // integer units so that the per-quadrature-point path never touches the FP64
@@ -130,46 +136,11 @@ __device__ __forceinline__ float f64_to_f32_rne(double x, int &nonfinite) {
     return __uint_as_float(bits | sign);
 }
 
-template <int PREC, int EP>
-__device__ __forceinline__ uint4 pack_piece(const float *v, int blk) {
-    uint4 r;
-    if constexpr (PREC == FE_PREC_BF16) {
-        r.x = pack_bf16x2(v[0], v[1]);
-        r.y = pack_bf16x2(v[2], v[3]);
-        r.z = pack_bf16x2(v[4], v[5]);
-        r.w = pack_bf16x2(v[6], v[7]);
-    } else if constexpr (PREC == FE_PREC_FP16) {
-        r.x = pack_f16x2(v[0], v[1]);
-        r.y = pack_f16x2(v[2], v[3]);
-        r.z = pack_f16x2(v[4], v[5]);
-        r.w = pack_f16x2(v[6], v[7]);
-    } else if constexpr (PREC == FE_PREC_TF32 || PREC == FE_PREC_TF32X3) {
-        uint32_t w4[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            uint32_t h = round_tf32(v[i]);
-            if (PREC == FE_PREC_TF32X3 && blk == 2) h = round_tf32(v[i] - __uint_as_float(h));
-            w4[i] = h;
-        }
-        r = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-    } else {
-        uint32_t w4[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            w4[i] = pack_e4m3x2(v[4 * i], v[4 * i + 1]) | (pack_e4m3x2(v[4 * i + 2], v[4 * i + 3]) << 16);
-        r = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-    }
-    return r;
-}
-
-__device__ __forceinline__ int first_form(const TcArgs &a) { return (a.form_mask & 1) ? 0 : 1; }
-
 template <int PREC>
 __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_constant__ TcArgs a) {
     constexpr int EB = (PREC == FE_PREC_E4M3) ? 1 : ((PREC == FE_PREC_TF32 || PREC == FE_PREC_TF32X3) ? 4 : 2);
     constexpr int KIND = (PREC == FE_PREC_E4M3) ? 2 : ((EB == 4) ? 1 : 0);
     constexpr int KCE = TC_CHUNK_BYTES / EB;  // quadrature points per chunk
-    constexpr int EP = 16 / EB;               // elements per 16-byte piece
 
     // a CTA that starts after another one gave up does no work at all
     if (*reinterpret_cast<volatile int *>(a.status) & ST_TIMEOUT) return;
@@ -178,9 +149,8 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
     Smem sm = carve(smem_raw, a);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int64_t n_tiles = (a.n_cells + TC_M - 1) / TC_M;
-    const int NPm = np_max(a);
-    const int nph = a.n_phi, nph2 = nph * nph;
+    const int64_t n_tiles = a.n_tiles;
+    const int NPm = a.np_max;
 
     if (tid == 0) {
         for (int s = 0; s < RING; ++s) {
@@ -200,9 +170,6 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         sm.flags[1] = 0;
         fence_mbar_init();
     }
-    for (int i = tid; i < a.n_q; i += V_THREADS) sm.omega[i] = (float)__ldg(a.weights + i);
-    if (a.staged)
-        for (int i = tid; i < nph2; i += V_THREADS) sm.f2s[i] = __ldg(a.full2sym + i);
     if (warp == 0) {
         tmem_alloc(sm.tmem_holder, 2 * ACC_COLS);
         tmem_relinquish();
@@ -229,12 +196,13 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         int ac = 0, jb = 0, nonfinite = 0;
         float win[WIN_REG ? 32 * QL : 1];
         float om[QL];
-        auto load_rows = [&](int64_t tile_cell0, int qw, float *dst) {
+        const TcSeg *cur = nullptr;
+        auto load_rows = [&](const TcSeg &S, int64_t tile_cell0, int qw, float *dst) {
             // dst[r * QL + i] = w_q kappa_{cell r, q}, q = qw * KCE + lane * QL + i
 #pragma unroll
             for (int i = 0; i < QL; ++i) {
                 const int q = qw * KCE + lane * QL + i;
-                om[i] = q < a.n_q ? sm.omega[q] : 0.f;
+                om[i] = q < S.n_q ? sm.omega[q] : 0.f;
             }
 #pragma unroll
             for (int r0 = 0; r0 < 32; r0 += RB) {
@@ -245,7 +213,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
 #pragma unroll
                     for (int i = 0; i < QL; ++i) {
                         const int q = qw * KCE + lane * QL + i;
-                        raw[r * QL + i] = (cell_r < a.n_cells && q < a.n_q) ? __ldg(a.kappa + cell_r * a.n_q + q) : 0.0;
+                        raw[r * QL + i] = (cell_r < S.n_cells && q < S.n_q) ? __ldg(S.kappa + cell_r * S.n_q + q) : 0.0;
                     }
                 }
 #pragma unroll
@@ -256,24 +224,34 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         // next tile's into L2 while this one is built
         auto prefetch_tile = [&](int64_t tt) {
             if (tt >= n_tiles || cl != 0) return;
-            const int64_t c0 = tt * TC_M;
-            const int64_t nc = (a.n_cells - c0) < TC_M ? (a.n_cells - c0) : TC_M;
-            const uint32_t kb = (uint32_t)((nc * a.n_q * 8) & ~int64_t(15));
-            const uint32_t cb = (uint32_t)((nc * (a.d + 1) * 4) & ~int64_t(15));
-            if (kb) prefetch_l2(a.kappa + c0 * a.n_q, kb);
-            if (cb) prefetch_l2(a.cells + c0 * (a.d + 1), cb);
+            const TcSeg &S = seg_of(a, tt);
+            const int64_t c0 = (tt - S.tile_begin) * TC_M;
+            const int64_t nc = (S.n_cells - c0) < TC_M ? (S.n_cells - c0) : TC_M;
+            const uint32_t kb = (uint32_t)((nc * S.n_q * 8) & ~int64_t(15));
+            const uint32_t cb = (uint32_t)((nc * (S.d + 1) * 4) & ~int64_t(15));
+            if (kb && ((reinterpret_cast<uintptr_t>(S.kappa + c0 * S.n_q) & 15) == 0)) prefetch_l2(S.kappa + c0 * S.n_q, kb);
+            if (cb && ((reinterpret_cast<uintptr_t>(S.cells + c0 * (S.d + 1)) & 15) == 0))
+                prefetch_l2(S.cells + c0 * (S.d + 1), cb);
         };
         prefetch_tile(blockIdx.x);
         for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
             prefetch_tile(t + gridDim.x);
-            const int64_t tile_cell0 = t * TC_M;
+            const TcSeg &S = seg_of(a, t);
+            if (&S != cur) {
+                // quadrature weights of the new segment
+                named_bar_sync(BAR_BUILDERS, TC_M);
+                for (int i = cl; i < S.n_q; i += TC_M) sm.omega[i] = (float)__ldg(S.weights + i);
+                named_bar_sync(BAR_BUILDERS, TC_M);
+                cur = &S;
+            }
+            const int64_t tile_cell0 = (t - S.tile_begin) * TC_M;
             const int64_t cell = tile_cell0 + cl;
-            const bool valid = cell < a.n_cells;
+            const bool valid = cell < S.n_cells;
             float g6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, adet = 0.f;
             int st = 0;
             if (valid) {
                 CellGeom geo;
-                st = cell_geometry(a.vertices, a.cells, cell, a.d, geo);
+                st = cell_geometry(S.vertices, S.cells, cell, S.d, geo);
                 if (!st) {
 #pragma unroll
                     for (int j = 0; j < 6; ++j) g6[j] = (float)geo.G[j];
@@ -287,9 +265,9 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 for (int r = 0; r < 32; ++r) {
                     const int64_t cell_r = tile_cell0 + wrow0 + r;
                     float m = 0.f;
-                    if (cell_r < a.n_cells)
-                        for (int q = lane; q < a.n_q; q += 32)
-                            m = fmaxf(m, fabsf(f64_to_f32_rne(__ldg(a.kappa + cell_r * a.n_q + q), nonfinite) * sm.omega[q]));
+                    if (cell_r < S.n_cells)
+                        for (int q = lane; q < S.n_q; q += 32)
+                            m = fmaxf(m, fabsf(f64_to_f32_rne(__ldg(S.kappa + cell_r * S.n_q + q), nonfinite) * sm.omega[q]));
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
                     if (lane == r) wmax = m;
@@ -297,7 +275,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             }
             float unscale_f[MAX_FORMS] = {1.f, 1.f};
             for (int f = 0; f < MAX_FORMS; ++f) {
-                if (!(a.form_mask & (1 << f))) continue;
+                if (!(S.form_mask & (1 << f))) continue;
                 float gmax = 0.f;
                 if (f == 0) {
 #pragma unroll
@@ -315,7 +293,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                     }
                 }
                 const float scale = ldexpf(1.f, e_c);
-                unscale_f[f] = ldexpf(a.op[f].p_inv_scale, -e_c);
+                unscale_f[f] = ldexpf(S.op[f].p_inv_scale, -e_c);
                 if (f == 0) {
 #pragma unroll
                     for (int j = 0; j < 6; ++j) sm.rowc[cl * 8 + j] = g6[j] * scale;
@@ -326,8 +304,8 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             __syncwarp();
             int qw_loaded = -1;
             for (int f = 0; f < MAX_FORMS; ++f) {
-                if (!(a.form_mask & (1 << f))) continue;
-                const TcOperand &op = a.op[f];
+                if (!(S.form_mask & (1 << f))) continue;
+                const TcOperand &op = S.op[f];
                 const int per_qw = op.n_pairs * op.n_blk;
                 for (int n = 0; n < op.n_pass; ++n) {
                     const int b = jb & 1, ub = jb >> 1;
@@ -350,10 +328,10 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         float wtmp[WIN_REG ? 1 : 32 * QL];
                         float *w = WIN_REG ? win : wtmp;
                         if (!WIN_REG) {
-                            load_rows(tile_cell0, qw, w);
+                            load_rows(S, tile_cell0, qw, w);
                         } else if (qw != qw_loaded) {
                             qw_loaded = qw;
-                            load_rows(tile_cell0, qw, w);
+                            load_rows(S, tile_cell0, qw, w);
                         }
                         uint8_t *stA = sm.A + s * (TC_M * TC_CHUNK_BYTES);
                         const int byte = lane * 4;   // this lane's word inside a 128-byte row
@@ -390,26 +368,23 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         if (nonfinite) atomicOr(&sm.flags[1], ST_NONFINITE);
     } else if (warp == W_MMA) {
         // ======================= bulk copies + MMA =======================
-        int64_t my_tiles = 0;
-        if (blockIdx.x < n_tiles) my_tiles = (n_tiles - 1 - blockIdx.x) / gridDim.x + 1;
-        int chunks_per_tile = 0;
-        for (int f = 0; f < MAX_FORMS; ++f)
-            if (a.form_mask & (1 << f)) chunks_per_tile += a.op[f].n_pass * a.op[f].n_kchunks;
-        const int64_t total = my_tiles * chunks_per_tile;
-        // B cursor (the shared operand does not depend on the tile)
-        int bf = first_form(a), bn = 0, bch = 0;
-        int64_t bc = 0;
+        // B cursor: (tile, form, pass, chunk) of the next shared-operand copy;
+        // bc counts the copies issued (the same in every lane).
+        int64_t bt = blockIdx.x, bc = 0;
+        int bf = 0, bn = 0, bch = 0;
+        if (bt < n_tiles) bf = first_form(seg_of(a, bt));
         auto issue_b = [&](int64_t upto) -> bool {
-            while (bc < upto) {
+            while (bc < upto && bt < n_tiles) {
+                const TcSeg &S = seg_of(a, bt);
+                const TcOperand &op = S.op[bf];
+                const uint32_t bytes = (uint32_t)op.NP * TC_CHUNK_BYTES;
                 const int s = (int)(bc % RING);
                 const int64_t ub = bc / RING;
                 if (bc >= RING && !mbar_wait(&sm.b_empty[s], (uint32_t)((ub - 1) & 1), deadline)) return false;
-                const TcOperand &op = a.op[bf];
-                const uint32_t bytes = (uint32_t)op.NP * TC_CHUNK_BYTES;
                 if (lane == 0) {
                     mbar_arrive_expect_tx(&sm.b_full[s], bytes);
-                    bulk_g2s(sm.B + (size_t)s * NPm * TC_CHUNK_BYTES,
-                             op.img + ((size_t)bn * op.n_kchunks + bch) * bytes, bytes, &sm.b_full[s]);
+                    bulk_g2s(sm.B + (size_t)s * NPm * TC_CHUNK_BYTES, op.img + ((size_t)bn * op.n_kchunks + bch) * bytes,
+                             bytes, &sm.b_full[s]);
                 }
                 __syncwarp();
                 ++bc;
@@ -417,7 +392,14 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                     bch = 0;
                     if (++bn == op.n_pass) {
                         bn = 0;
-                        do { bf = (bf + 1) % MAX_FORMS; } while (!(a.form_mask & (1 << bf)));
+                        int nf = bf + 1;
+                        while (nf < MAX_FORMS && !(S.form_mask & (1 << nf))) ++nf;
+                        if (nf < MAX_FORMS) {
+                            bf = nf;
+                        } else {
+                            bt += gridDim.x;
+                            if (bt < n_tiles) bf = first_form(seg_of(a, bt));
+                        }
                     }
                 }
             }
@@ -425,11 +407,12 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         };
         int64_t mc = 0;
         int jb = 0;
-        bool fail = false;
-        for (int64_t t = 0; t < my_tiles && !fail; ++t) {
+        bool fail = !issue_b(RING);
+        for (int64_t t = blockIdx.x; t < n_tiles && !fail; t += gridDim.x) {
+            const TcSeg &S = seg_of(a, t);
             for (int f = 0; f < MAX_FORMS && !fail; ++f) {
-                if (!(a.form_mask & (1 << f))) continue;
-                const TcOperand &op = a.op[f];
+                if (!(S.form_mask & (1 << f))) continue;
+                const TcOperand &op = S.op[f];
                 const uint32_t idesc = a.idesc | ((uint32_t)(op.NP >> 3) << 17);
                 for (int n = 0; n < op.n_pass && !fail; ++n) {
                     const int b = jb & 1, ub = jb >> 1;
@@ -440,10 +423,6 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                     tc_fence_after();
                     const uint32_t dacc = tmem + (uint32_t)(b * ACC_COLS);
                     for (int ch = 0; ch < op.n_kchunks; ++ch) {
-                        if (!issue_b(mc + RING < total ? mc + RING : total)) {
-                            fail = true;
-                            break;
-                        }
                         const int sa = (int)(mc % RING);
                         const uint32_t par = (uint32_t)((mc / RING) & 1);
                         if (!mbar_wait(&sm.a_full[sa], par, deadline) || !mbar_wait(&sm.b_full[sa], par, deadline)) {
@@ -464,6 +443,11 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         }
                         __syncwarp();
                         ++mc;
+                        // refill the stage of chunk mc-1 once its MMAs are done
+                        if (!issue_b(mc + RING)) {
+                            fail = true;
+                            break;
+                        }
                     }
                     ++jb;
                     if (*abort_flag) fail = true;
@@ -484,21 +468,27 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         // 16h..16h+15 of the lane group when writing out.
         const int g = warp & 3;
         const int h = (warp - W_EPI0) >> 2;
-        const int pitch = stage_pitch(a);
+        const int pitch = a.pitch_max;
         float *stg = sm.stage + g * 32 * pitch;
         int f2s_reg[MAX_F2S_IT];
-#pragma unroll
-        for (int it = 0; it < MAX_F2S_IT; ++it) {
-            const int pos = lane + 32 * it;
-            f2s_reg[it] = (a.staged && pos < nph2) ? sm.f2s[pos] : 0;
-        }
-        const int n_it = (nph2 + 31) / 32;
+        const TcSeg *cur = nullptr;
         int jb = 0;
         for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
+            const TcSeg &S = seg_of(a, t);
+            const int nph = S.n_phi, nph2 = nph * nph;
+            const int n_it = (nph2 + 31) / 32;
+            if (&S != cur) {
+#pragma unroll
+                for (int it = 0; it < MAX_F2S_IT; ++it) {
+                    const int pos = lane + 32 * it;
+                    f2s_reg[it] = (S.staged && pos < nph2) ? __ldg(S.full2sym + pos) : 0;
+                }
+                cur = &S;
+            }
             for (int f = 0; f < MAX_FORMS; ++f) {
-                if (!(a.form_mask & (1 << f))) continue;
-                const TcOperand &op = a.op[f];
-                float *out = a.out[f];
+                if (!(S.form_mask & (1 << f))) continue;
+                const TcOperand &op = S.op[f];
+                float *out = S.out[f];
                 for (int n = 0; n < op.n_pass; ++n) {
                     const int b = jb & 1, ub = jb >> 1;
                     if (!mbar_wait(&sm.acc_full[b], ub & 1, deadline) || !mbar_wait(&sm.meta_full[b], ub & 1, deadline)) {
@@ -509,8 +499,8 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                     const float us = sm.meta[b * TC_M + g * 32 + lane];
                     mbar_arrive(&sm.meta_empty[b]);
                     const uint32_t tbase = tmem + (uint32_t)(b * ACC_COLS) + ((uint32_t)(g * 32) << 16);
-                    const int64_t cell0 = t * TC_M + g * 32;
-                    if (a.staged) {
+                    const int64_t cell0 = (t - S.tile_begin) * TC_M + g * 32;
+                    if (S.staged) {
                         float *mine = stg + lane * pitch;
                         for (int c0 = 32 * h; c0 < op.NP; c0 += 64) {
                             uint32_t r[32];
@@ -525,7 +515,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         // whole row-major matrices of 16 consecutive cells (loads first, then stores)
                         if (out) {
                             for (int cc = 16 * h; cc < 16 * h + 16; ++cc) {
-                                if (cell0 + cc >= a.n_cells) break;
+                                if (cell0 + cc >= S.n_cells) break;
                                 float *__restrict__ dst = out + (cell0 + cc) * (int64_t)nph2;
                                 const float *__restrict__ src = stg + cc * pitch;
                                 float vals[MAX_F2S_IT];
@@ -544,13 +534,13 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         for (int c0 = 32 * h; c0 < op.NP; c0 += 64) {
                             uint32_t r[32];
                             tmem_ld32(tbase + (uint32_t)c0, r);
-                            if (mycell < a.n_cells && out) {
+                            if (mycell < S.n_cells && out) {
                                 float *dst = out + mycell * (int64_t)nph2;
 #pragma unroll
                                 for (int i = 0; i < 32; ++i) {
                                     const int col = n * op.NP + c0 + i;
                                     if (c0 + i < op.NP && col < op.n_cols) {
-                                        const int32_t kl = __ldg(a.sym_kl + col);
+                                        const int32_t kl = __ldg(S.sym_kl + col);
                                         const int k = kl & 0xFFFF, l = kl >> 16;
                                         const float v = __uint_as_float(r[i]) * us;
                                         dst[k * nph + l] = v;
@@ -582,21 +572,22 @@ size_t tc_smem_bytes(const TcArgs &a) {
     size_t b = 1024;  // alignment slack
     b += bytes_A() + bytes_B(a) + bytes_stage(a);
     b += 2 * TC_M * sizeof(float) + 8 * TC_M * sizeof(float);
-    b += (size_t)((a.n_q + 3) & ~3) * sizeof(float);
-    b += (size_t)(a.staged ? ((a.n_phi * a.n_phi + 3) & ~3) : 0) * sizeof(int16_t) + 8;
+    b += (size_t)((a.nq_max + 3) & ~3) * sizeof(float) + 8;
     b += (4 * RING + 9) * sizeof(uint64_t) + 8 + 16;
     return b;
 }
 
-// The staged epilogue needs the whole sym row in one accumulator and its
-// staging area within the shared-memory budget.
-bool tc_can_stage(const TcArgs &a) {
-    TcArgs t = a;
-    t.staged = 1;
+bool tc_can_stage(const TcArgs &a, const TcSeg &seg) {
+    int np = 16;
     for (int f = 0; f < MAX_FORMS; ++f)
-        if ((a.form_mask >> f) & 1)
-            if (a.op[f].n_pass != 1) return false;
-    return a.n_phi * a.n_phi <= 32 * MAX_F2S_IT && tc_smem_bytes(t) <= 227 * 1024;
+        if ((seg.form_mask >> f) & 1) {
+            if (seg.op[f].n_pass != 1) return false;
+            np = seg.op[f].NP > np ? seg.op[f].NP : np;
+        }
+    if (seg.n_phi * seg.n_phi > 32 * MAX_F2S_IT) return false;
+    TcArgs t = a;
+    t.pitch_max = (np + 1) > a.pitch_max ? (np + 1) : a.pitch_max;
+    return tc_smem_bytes(t) <= 227 * 1024;
 }
 
 template <int PREC>
@@ -608,13 +599,15 @@ static int launch_prec(const TcArgs &a, size_t smem, cudaStream_t s, int grid) {
     return e == cudaSuccess ? 1 : -(int)e;
 }
 
-int launch_tc_elements(const TcArgs &a, size_t smem, cudaStream_t s) {
-    if (a.n_cells <= 0) return 0;
-    const int64_t n_tiles = (a.n_cells + TC_M - 1) / TC_M;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (int)(n_tiles < sms ? n_tiles : sms);
+int launch_tc_elements(const TcArgs &a, size_t smem, cudaStream_t s, int grid) {
+    if (a.n_tiles <= 0) return 0;
+    if (grid <= 0) {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid = sms;
+    }
+    if (grid > a.n_tiles) grid = (int)a.n_tiles;
     switch (a.prec) {
         case FE_PREC_BF16: return launch_prec<FE_PREC_BF16>(a, smem, s, grid);
         case FE_PREC_FP16: return launch_prec<FE_PREC_FP16>(a, smem, s, grid);
