@@ -101,8 +101,10 @@ __device__ inline Smem carve(uint8_t *raw, const TcArgs &a) {
 }
 
 // Segment of a global tile (binary search over the segments' first tiles).
+// The single-plan instantiation addresses the kernel parameter directly.
+template <bool BATCHED>
 __device__ __forceinline__ const TcSeg &seg_of(const TcArgs &a, int64_t t) {
-    if (a.segs == nullptr) return a.seg0;
+    if (!BATCHED) return a.seg0;
     int lo = 0, hi = a.n_segs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -136,7 +138,7 @@ __device__ __forceinline__ float f64_to_f32_rne(double x, int &nonfinite) {
     return __uint_as_float(bits | sign);
 }
 
-template <int PREC>
+template <int PREC, bool BATCHED>
 __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_constant__ TcArgs a) {
     constexpr int EB = (PREC == FE_PREC_E4M3) ? 1 : ((PREC == FE_PREC_TF32 || PREC == FE_PREC_TF32X3) ? 4 : 2);
     constexpr int KIND = (PREC == FE_PREC_E4M3) ? 2 : ((EB == 4) ? 1 : 0);
@@ -197,12 +199,13 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         float win[WIN_REG ? 32 * QL : 1];
         float om[QL];
         const TcSeg *cur = nullptr;
-        auto load_rows = [&](const TcSeg &S, int64_t tile_cell0, int qw, float *dst) {
+        auto load_rows = [&](const double *__restrict__ kappa, int64_t n_cells, int n_q, int64_t tile_cell0, int qw,
+                             float *dst) {
             // dst[r * QL + i] = w_q kappa_{cell r, q}, q = qw * KCE + lane * QL + i
 #pragma unroll
             for (int i = 0; i < QL; ++i) {
                 const int q = qw * KCE + lane * QL + i;
-                om[i] = q < S.n_q ? sm.omega[q] : 0.f;
+                om[i] = q < n_q ? sm.omega[q] : 0.f;
             }
 #pragma unroll
             for (int r0 = 0; r0 < 32; r0 += RB) {
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
 #pragma unroll
                     for (int i = 0; i < QL; ++i) {
                         const int q = qw * KCE + lane * QL + i;
-                        raw[r * QL + i] = (cell_r < S.n_cells && q < S.n_q) ? __ldg(S.kappa + cell_r * S.n_q + q) : 0.0;
+                        raw[r * QL + i] = (cell_r < n_cells && q < n_q) ? __ldg(kappa + cell_r * n_q + q) : 0.0;
                     }
                 }
 #pragma unroll
@@ -224,7 +227,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         // next tile's into L2 while this one is built
         auto prefetch_tile = [&](int64_t tt) {
             if (tt >= n_tiles || cl != 0) return;
-            const TcSeg &S = seg_of(a, tt);
+            const TcSeg &S = seg_of<BATCHED>(a, tt);
             const int64_t c0 = (tt - S.tile_begin) * TC_M;
             const int64_t nc = (S.n_cells - c0) < TC_M ? (S.n_cells - c0) : TC_M;
             const uint32_t kb = (uint32_t)((nc * S.n_q * 8) & ~int64_t(15));
@@ -236,7 +239,10 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         prefetch_tile(blockIdx.x);
         for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
             prefetch_tile(t + gridDim.x);
-            const TcSeg &S = seg_of(a, t);
+            const TcSeg &S = seg_of<BATCHED>(a, t);
+            const double *__restrict__ s_kappa = S.kappa;
+            const int64_t s_ncells = S.n_cells;
+            const int s_nq = S.n_q;
             if (&S != cur) {
                 // quadrature weights of the new segment
                 named_bar_sync(BAR_BUILDERS, TC_M);
@@ -265,9 +271,9 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 for (int r = 0; r < 32; ++r) {
                     const int64_t cell_r = tile_cell0 + wrow0 + r;
                     float m = 0.f;
-                    if (cell_r < S.n_cells)
-                        for (int q = lane; q < S.n_q; q += 32)
-                            m = fmaxf(m, fabsf(f64_to_f32_rne(__ldg(S.kappa + cell_r * S.n_q + q), nonfinite) * sm.omega[q]));
+                    if (cell_r < s_ncells)
+                        for (int q = lane; q < s_nq; q += 32)
+                            m = fmaxf(m, fabsf(f64_to_f32_rne(__ldg(s_kappa + cell_r * s_nq + q), nonfinite) * sm.omega[q]));
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
                     if (lane == r) wmax = m;
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             int qw_loaded = -1;
             for (int f = 0; f < MAX_FORMS; ++f) {
                 if (!(S.form_mask & (1 << f))) continue;
-                const TcOperand &op = S.op[f];
+                const TcOperand op = S.op[f];
                 const int per_qw = op.n_pairs * op.n_blk;
                 for (int n = 0; n < op.n_pass; ++n) {
                     const int b = jb & 1, ub = jb >> 1;
@@ -328,10 +334,10 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         float wtmp[WIN_REG ? 1 : 32 * QL];
                         float *w = WIN_REG ? win : wtmp;
                         if (!WIN_REG) {
-                            load_rows(S, tile_cell0, qw, w);
+                            load_rows(s_kappa, s_ncells, s_nq, tile_cell0, qw, w);
                         } else if (qw != qw_loaded) {
                             qw_loaded = qw;
-                            load_rows(S, tile_cell0, qw, w);
+                            load_rows(s_kappa, s_ncells, s_nq, tile_cell0, qw, w);
                         }
                         uint8_t *stA = sm.A + s * (TC_M * TC_CHUNK_BYTES);
                         const int byte = lane * 4;   // this lane's word inside a 128-byte row
@@ -372,10 +378,10 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         // bc counts the copies issued (the same in every lane).
         int64_t bt = blockIdx.x, bc = 0;
         int bf = 0, bn = 0, bch = 0;
-        if (bt < n_tiles) bf = first_form(seg_of(a, bt));
+        if (bt < n_tiles) bf = first_form(seg_of<BATCHED>(a, bt));
         auto issue_b = [&](int64_t upto) -> bool {
             while (bc < upto && bt < n_tiles) {
-                const TcSeg &S = seg_of(a, bt);
+                const TcSeg &S = seg_of<BATCHED>(a, bt);
                 const TcOperand &op = S.op[bf];
                 const uint32_t bytes = (uint32_t)op.NP * TC_CHUNK_BYTES;
                 const int s = (int)(bc % RING);
@@ -398,7 +404,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                             bf = nf;
                         } else {
                             bt += gridDim.x;
-                            if (bt < n_tiles) bf = first_form(seg_of(a, bt));
+                            if (bt < n_tiles) bf = first_form(seg_of<BATCHED>(a, bt));
                         }
                     }
                 }
@@ -409,10 +415,10 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         int jb = 0;
         bool fail = !issue_b(RING);
         for (int64_t t = blockIdx.x; t < n_tiles && !fail; t += gridDim.x) {
-            const TcSeg &S = seg_of(a, t);
+            const TcSeg &S = seg_of<BATCHED>(a, t);
             for (int f = 0; f < MAX_FORMS && !fail; ++f) {
                 if (!(S.form_mask & (1 << f))) continue;
-                const TcOperand &op = S.op[f];
+                const TcOperand op = S.op[f];
                 const uint32_t idesc = a.idesc | ((uint32_t)(op.NP >> 3) << 17);
                 for (int n = 0; n < op.n_pass && !fail; ++n) {
                     const int b = jb & 1, ub = jb >> 1;
@@ -474,7 +480,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         const TcSeg *cur = nullptr;
         int jb = 0;
         for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
-            const TcSeg &S = seg_of(a, t);
+            const TcSeg &S = seg_of<BATCHED>(a, t);
             const int nph = S.n_phi, nph2 = nph * nph;
             const int n_it = (nph2 + 31) / 32;
             if (&S != cur) {
@@ -487,8 +493,11 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             }
             for (int f = 0; f < MAX_FORMS; ++f) {
                 if (!(S.form_mask & (1 << f))) continue;
-                const TcOperand &op = S.op[f];
-                float *out = S.out[f];
+                const TcOperand op = S.op[f];
+                float *__restrict__ out = S.out[f];
+                const int64_t s_ncells = S.n_cells;
+                const int s_staged = S.staged;
+                const int32_t *__restrict__ s_symkl = S.sym_kl;
                 for (int n = 0; n < op.n_pass; ++n) {
                     const int b = jb & 1, ub = jb >> 1;
                     if (!mbar_wait(&sm.acc_full[b], ub & 1, deadline) || !mbar_wait(&sm.meta_full[b], ub & 1, deadline)) {
@@ -500,7 +509,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                     mbar_arrive(&sm.meta_empty[b]);
                     const uint32_t tbase = tmem + (uint32_t)(b * ACC_COLS) + ((uint32_t)(g * 32) << 16);
                     const int64_t cell0 = (t - S.tile_begin) * TC_M + g * 32;
-                    if (S.staged) {
+                    if (s_staged) {
                         float *mine = stg + lane * pitch;
                         for (int c0 = 32 * h; c0 < op.NP; c0 += 64) {
                             uint32_t r[32];
@@ -515,7 +524,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         // whole row-major matrices of 16 consecutive cells (loads first, then stores)
                         if (out) {
                             for (int cc = 16 * h; cc < 16 * h + 16; ++cc) {
-                                if (cell0 + cc >= S.n_cells) break;
+                                if (cell0 + cc >= s_ncells) break;
                                 float *__restrict__ dst = out + (cell0 + cc) * (int64_t)nph2;
                                 const float *__restrict__ src = stg + cc * pitch;
                                 float vals[MAX_F2S_IT];
@@ -534,13 +543,13 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         for (int c0 = 32 * h; c0 < op.NP; c0 += 64) {
                             uint32_t r[32];
                             tmem_ld32(tbase + (uint32_t)c0, r);
-                            if (mycell < S.n_cells && out) {
+                            if (mycell < s_ncells && out) {
                                 float *dst = out + mycell * (int64_t)nph2;
 #pragma unroll
                                 for (int i = 0; i < 32; ++i) {
                                     const int col = n * op.NP + c0 + i;
                                     if (c0 + i < op.NP && col < op.n_cols) {
-                                        const int32_t kl = __ldg(S.sym_kl + col);
+                                        const int32_t kl = __ldg(s_symkl + col);
                                         const int k = kl & 0xFFFF, l = kl >> 16;
                                         const float v = __uint_as_float(r[i]) * us;
                                         dst[k * nph + l] = v;
@@ -590,13 +599,19 @@ bool tc_can_stage(const TcArgs &a, const TcSeg &seg) {
     return tc_smem_bytes(t) <= 227 * 1024;
 }
 
-template <int PREC>
-static int launch_prec(const TcArgs &a, size_t smem, cudaStream_t s, int grid) {
-    cudaError_t e = cudaFuncSetAttribute(tc_element_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int PREC, bool BATCHED>
+static int launch_prec2(const TcArgs &a, size_t smem, cudaStream_t s, int grid) {
+    cudaError_t e =
+        cudaFuncSetAttribute(tc_element_kernel<PREC, BATCHED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return -(int)e;
-    tc_element_kernel<PREC><<<(unsigned)grid, V_THREADS, smem, s>>>(a);
+    tc_element_kernel<PREC, BATCHED><<<(unsigned)grid, V_THREADS, smem, s>>>(a);
     e = cudaGetLastError();
     return e == cudaSuccess ? 1 : -(int)e;
+}
+
+template <int PREC>
+static int launch_prec(const TcArgs &a, size_t smem, cudaStream_t s, int grid) {
+    return a.segs ? launch_prec2<PREC, true>(a, smem, s, grid) : launch_prec2<PREC, false>(a, smem, s, grid);
 }
 
 int launch_tc_elements(const TcArgs &a, size_t smem, cudaStream_t s, int grid) {
