@@ -15,6 +15,9 @@
 #include "fe_host.h"
 #include "fe_internal.h"
 
+static_assert(fe::host::kAsmChunkEntries == fe::ASM_CHUNK && fe::host::kAsmChunkIncidences == fe::ASM_CHUNK_INC,
+              "host and device assembly chunk limits differ");
+
 using namespace fe;
 
 namespace {
@@ -79,7 +82,8 @@ struct fe_plan {
     cudaStream_t stream = nullptr;
     int sms = 0;
     DevBuf vertices, cells, weights, cell_dofs, row_ptr, col_idx, inc_ptr, inc_elem, vinc_ptr, vinc;
-    DevBuf contrib_cnt, contrib_base, contrib_code;
+    DevBuf contrib_cnt, contrib_base, contrib_code, contrib_dest, chunk_desc;
+    int64_t n_chunks = 0;                // assembly row chunks
     DevBuf phi, dphi, sym_kl, full2sym, status;
     DevBuf img[6][2];
     TcOperand op[6][2];
@@ -92,7 +96,6 @@ struct fe_plan {
     std::vector<int> host_status;
     std::vector<double> h_phi, h_dphi;   // FP64 tabulation kept for re-packing operands
     int tuned_np[6][2] = {};             // autotuned N-pass width per precision and form
-    int asm_wpb = 8;                     // autotuned assembly block size (warps)
     ~fe_plan() {
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
@@ -242,6 +245,7 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
     P.n_dofs = pat.n_dofs;
     P.nnz = pat.nnz;
     P.max_row = pat.max_row;
+    P.n_chunks = (int64_t)pat.chunk_row.size() - 1;
 
     std::vector<double> phi, dphi;
     host::tabulate(d, degree, rule->points, rule->n_q, phi, dphi);
@@ -261,6 +265,8 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
     FE_CUDA(upload(P.contrib_cnt, pat.contrib_cnt, s), "upload contribution counts");
     FE_CUDA(upload(P.contrib_base, pat.contrib_base, s), "upload contribution bases");
     FE_CUDA(upload(P.contrib_code, pat.contrib_code, s), "upload contribution codes");
+    FE_CUDA(upload(P.contrib_dest, pat.contrib_dest, s), "upload contribution destinations");
+    FE_CUDA(upload(P.chunk_desc, pat.chunk_desc, s), "upload assembly chunks");
     FE_CUDA(upload(P.vinc_ptr, pat.vinc_ptr, s), "upload vinc_ptr");
     FE_CUDA(upload(P.vinc, pat.vinc, s), "upload vinc");
     FE_CUDA(upload(P.phi, phi, s), "upload phi");
@@ -472,6 +478,9 @@ static AsmSeg make_asm_seg(fe_plan *P, unsigned forms, const void *const A[2], v
     g.contrib_cnt = P->contrib_cnt.as<uint8_t>();
     g.contrib_base = P->contrib_base.as<int64_t>();
     g.contrib_code = P->contrib_code.as<uint16_t>();
+    g.contrib_dest = P->contrib_dest.as<uint16_t>();
+    g.chunk_desc = P->chunk_desc.as<int64_t>();
+    g.n_chunks = P->n_chunks;
     g.n_phi = P->n_phi;
     int nf = 0;
     for (int fi = 0; fi < 2; ++fi) {
@@ -482,6 +491,7 @@ static AsmSeg make_asm_seg(fe_plan *P, unsigned forms, const void *const A[2], v
         ++nf;
     }
     g.row_begin = 0;
+    g.chunk_begin = 0;
     return g;
 }
 
@@ -541,9 +551,10 @@ static fe_status run_assembly(fe_plan *P, unsigned forms, bool fp64, const void 
     a.segs = nullptr;
     a.n_segs = 1;
     a.n_rows = P->n_dofs;
+    a.n_chunks = P->n_chunks;
     a.n_forms = n_forms_of(forms);
     mark(P, 1, true);
-    int r = launch_assemble(a, fp64, P->stream, P->asm_wpb);
+    int r = launch_assemble(a, fp64, P->stream);
     if (r < 0) return cuda_fail((cudaError_t)(-r), "assembly kernel launch");
     launches += r;
     mark(P, 1, false);
@@ -873,7 +884,7 @@ static fe_status batch_launch(fe_batch &B, int &launches) {
         launches += r;
     }
     if (B.assemble) {
-        int r = launch_assemble(B.aargs, B.prec == FE_PREC_FP64, B.stream, B.plans[0]->asm_wpb);
+        int r = launch_assemble(B.aargs, B.prec == FE_PREC_FP64, B.stream);
         if (r < 0) return cuda_fail((cudaError_t)(-r), "assembly kernel launch");
         launches += r;
     }
@@ -915,7 +926,7 @@ fe_status fe_batch_create(fe_batch **out, fe_plan *const *plans, int n_plans, un
     const bool fp64 = prec == FE_PREC_FP64;
     std::vector<TcSeg> tsegs;
     std::vector<AsmSeg> asegs;
-    int64_t rows = 0;
+    int64_t rows = 0, chunks = 0;
     for (int i = 0; i < n_plans; ++i) {
         fe_plan *P = plans[i];
         void *A[2] = {A_stiffness ? A_stiffness[i] : nullptr, A_mass ? A_mass[i] : nullptr};
@@ -955,7 +966,9 @@ fe_status fe_batch_create(fe_batch **out, fe_plan *const *plans, int n_plans, un
             const void *Ac[2] = {A[0], A[1]};
             asegs.push_back(make_asm_seg(P, forms, Ac, csr));
             asegs.back().row_begin = rows;
+            asegs.back().chunk_begin = chunks;
             rows += P->n_dofs;
+            chunks += P->n_chunks;
         }
     }
     if (!fp64) {
@@ -972,6 +985,7 @@ fe_status fe_batch_create(fe_batch **out, fe_plan *const *plans, int n_plans, un
         B.aargs.segs = B.asm_segs.as<AsmSeg>();
         B.aargs.n_segs = (int)asegs.size();
         B.aargs.n_rows = rows;
+        B.aargs.n_chunks = chunks;
         B.aargs.n_forms = n_forms_of(forms);
     }
     // one eager run (sets kernel attributes, checks the inputs), then capture

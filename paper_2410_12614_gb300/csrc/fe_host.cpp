@@ -432,12 +432,17 @@ std::string build_pattern(int d, int p, int64_t n_vertices, int64_t n_cells, con
                 const int len = (int)(P.row_ptr[i + 1] - r0);
                 const int ninc = (int)(iptr[i + 1] - iptr[i]);
                 // counts per slot, then offsets, then codes in incidence (= cell) order
+                bool row_over = false;
                 for (int t = 0; t < ninc; ++t)
                     for (int l = 0; l < nph; ++l) {
                         const int sl = P.inc_slot[(size_t)(iptr[i] + t) * nph + l];
-                        if (P.contrib_cnt[r0 + sl] == 255) overflow = 1;
+                        if (P.contrib_cnt[r0 + sl] == 255) row_over = true;
                         else P.contrib_cnt[r0 + sl]++;
                     }
+                if (row_over) {   // the codes would not fit the counts: reported below
+                    overflow = 1;
+                    continue;
+                }
                 fillpos.assign(len + 1, 0);
                 for (int j = 0; j < len; ++j) fillpos[j + 1] = fillpos[j] + P.contrib_cnt[r0 + j];
                 uint16_t *codes = P.contrib_code.data() + P.contrib_base[i];
@@ -449,6 +454,43 @@ std::string build_pattern(int d, int p, int64_t n_vertices, int64_t n_cells, con
             }
         });
         if (overflow) return "a CSR entry has more than 255 contributions";
+        // assembly chunks, and the codes re-counted from each chunk's first incidence
+        P.chunk_row.assign(1, 0);
+        int64_t ent = 0, inc = 0;
+        for (int64_t i = 0; i < nd; ++i) {
+            const int64_t ei = P.contrib_base[i + 1] - P.contrib_base[i], ii = iptr[i + 1] - iptr[i];
+            if (i > P.chunk_row.back() && (ent + ei > kAsmChunkEntries || inc + ii > kAsmChunkIncidences)) {
+                P.chunk_row.push_back((int32_t)i);
+                ent = inc = 0;
+            }
+            ent += ei;
+            inc += ii;
+        }
+        P.chunk_row.push_back((int32_t)nd);
+        const int64_t n_chunks = (int64_t)P.chunk_row.size() - 1;
+        P.chunk_desc.resize((size_t)(n_chunks + 1) * 4);
+        for (int64_t k = 0; k <= n_chunks; ++k) {
+            const int64_t r = P.chunk_row[k];
+            P.chunk_desc[k * 4 + 0] = r;
+            P.chunk_desc[k * 4 + 1] = P.contrib_base[r];
+            P.chunk_desc[k * 4 + 2] = iptr[r];
+            P.chunk_desc[k * 4 + 3] = P.row_ptr[r];
+        }
+        P.contrib_dest.assign(P.contrib_code.size(), 0);
+        parallel_for(n_chunks, [&](int64_t b, int64_t e) {
+            for (int64_t k = b; k < e; ++k) {
+                const int64_t e0 = iptr[P.chunk_row[k]];
+                const int64_t c0 = P.contrib_base[P.chunk_row[k]];
+                for (int64_t i = P.chunk_row[k]; i < P.chunk_row[k + 1]; ++i) {
+                    const unsigned shift = (unsigned)(iptr[i] - e0);
+                    for (int64_t j = P.contrib_base[i]; j < P.contrib_base[i + 1]; ++j) {
+                        const unsigned code = P.contrib_code[j] + shift;
+                        P.contrib_code[j] = (uint16_t)code;
+                        P.contrib_dest[c0 + (int64_t)(code & 0xFFu) * nph + (code >> 8)] = (uint16_t)(j - c0);
+                    }
+                }
+            }
+        });
     }
     // vertex incidence for the adjoint's vertex scatter
     P.vinc_ptr.assign(n_vertices + 1, 0);

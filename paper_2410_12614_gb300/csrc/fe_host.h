@@ -19,6 +19,12 @@ std::vector<int> lattice_nodes(int d, int p);
 // phi [n_phi][n_q] and dphi [d][n_phi][n_q] at the points [n_q][d], FP64.
 void tabulate(int d, int p, const double *pts, int n_q, std::vector<double> &phi, std::vector<double> &dphi);
 
+// Row chunks of the block-wide assembly: consecutive CSR rows holding at most
+// kAsmChunkEntries element entries and kAsmChunkIncidences incidences (a row
+// above the entry limit forms a chunk of its own).
+constexpr int kAsmChunkEntries = 4096;
+constexpr int kAsmChunkIncidences = 256;
+
 struct Pattern {
     int d = 0, p = 0, n_phi = 0;
     int64_t n_vertices = 0, n_cells = 0, n_dofs = 0, nnz = 0;
@@ -31,10 +37,18 @@ struct Pattern {
     std::vector<int32_t> inc_elem;    // c * n_phi + k, sorted by (dof, c)
     std::vector<uint16_t> inc_slot;   // [n_inc][n_phi]
     // per CSR entry, its element-entry contributions in increasing cell order:
-    // code t | l << 8 (t = incidence index inside the row, l = local column)
+    // code t | l << 8 (t = incidence index counted from the first incidence of
+    // the row's chunk, l = local column)
     std::vector<uint8_t> contrib_cnt;   // [nnz]
     std::vector<int64_t> contrib_base;  // [n_dofs + 1] first code of each row
     std::vector<uint16_t> contrib_code; // [n_cells * n_phi * n_phi]
+    std::vector<int32_t> chunk_row;     // [n_chunks + 1] first row of each assembly chunk
+    // [n_chunks + 1][4]: first row, first code, first incidence, first CSR value
+    std::vector<int64_t> chunk_desc;
+    // per chunk, its element entries in incidence order (incidence t of the
+    // chunk, local column l at t * n_phi + l) mapped to their position in the
+    // chunk's code order (the concatenated CSR-value segments)
+    std::vector<uint16_t> contrib_dest; // [n_cells * n_phi * n_phi]
     // vertex -> (cell, local vertex) incidence for the adjoint scatter
     std::vector<int64_t> vinc_ptr;    // [n_vertices+1]
     std::vector<int32_t> vinc;        // c * (d+1) + j, sorted by (vertex, c)

@@ -96,6 +96,10 @@ struct F64Args {
 };
 
 // One plan's share of a (possibly batched) assembly launch.
+// Row chunks of the assembly (fe_host.h kAsmChunkEntries / kAsmChunkIncidences).
+constexpr int ASM_CHUNK = 4096;
+constexpr int ASM_CHUNK_INC = 256;
+
 struct AsmSeg {
     int64_t n_rows;
     const int64_t *row_ptr;
@@ -103,11 +107,15 @@ struct AsmSeg {
     const int32_t *inc_elem;   // element-row ids c * n_phi + k, sorted by (row, c)
     const uint8_t *contrib_cnt;     // [nnz] number of element entries summed into each CSR value
     const int64_t *contrib_base;    // [n_rows + 1] first contribution code of each row
-    const uint16_t *contrib_code;   // incidence index | local column << 8, per row in slot order
+    const uint16_t *contrib_code;   // incidence index in the chunk | local column << 8, per row in slot order
+    const uint16_t *contrib_dest;   // per chunk, entry (t, l) at t * n_phi + l -> its position in code order
+    const int64_t *chunk_desc;      // [n_chunks + 1][4] first row, code, incidence and CSR value of each chunk
+    int64_t n_chunks;
     int n_phi;
     const void *A[MAX_FORMS];
     void *out[MAX_FORMS];
     int64_t row_begin;         // first global row of this segment
+    int64_t chunk_begin;       // first global chunk of this segment
 };
 
 struct AsmArgs {
@@ -115,8 +123,8 @@ struct AsmArgs {
     const AsmSeg *segs;        // device array (batched launch)
     int n_segs;
     int64_t n_rows;            // total rows over all segments
+    int64_t n_chunks;          // total chunks over all segments
     int n_forms;
-    int warps_per_block;
 };
 
 struct AdjArgs {
@@ -146,7 +154,7 @@ size_t tc_smem_bytes(const TcArgs &a);
 // Whether a segment can use the staged epilogue under the given global shape.
 bool tc_can_stage(const TcArgs &a, const TcSeg &seg);
 int launch_f64_elements(const F64Args &a, cudaStream_t s);
-int launch_assemble(const AsmArgs &a, bool fp64, cudaStream_t s, int warps_per_block = 8);
+int launch_assemble(const AsmArgs &a, bool fp64, cudaStream_t s);
 // Capacity (in doubles) of the fixed scratch array of the allocation-free
 // adjoint, and the lookup of its device address on the current device.
 constexpr size_t kNoAllocScratchDoubles = size_t(1) << 22;  // 32 MiB
