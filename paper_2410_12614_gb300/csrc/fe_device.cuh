@@ -118,14 +118,19 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+// A waiting thread is suspended until the phase completes or this many
+// nanoseconds pass (then the caller checks its deadline and waits again), so
+// that waiting warps leave the issue slots to the working ones.
+constexpr uint32_t kWaitSuspendNs = 100000;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kWaitSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -140,6 +145,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
         if (global_ns() > deadline) return false;
     }
     return true;
+}
+
+// The same, with one outcome for the whole warp (every lane waits; a lane that
+// timed out makes the warp give up), for waits followed by warp-collective code.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, unsigned long long deadline) {
+    return __all_sync(0xffffffffu, mbar_wait(bar, parity, deadline)) != 0;
 }
 
 // 1-D bulk copy global -> shared memory, completion counted on an mbarrier.

@@ -156,16 +156,16 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
 
     if (tid == 0) {
         for (int s = 0; s < RING; ++s) {
-            mbar_init(&sm.a_full[s], TC_M);
+            mbar_init(&sm.a_full[s], TC_M / 32);         // one arrival per builder warp
             mbar_init(&sm.a_empty[s], 1);
             mbar_init(&sm.b_full[s], 1);
             mbar_init(&sm.b_empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sm.acc_full[b], 1);
-            mbar_init(&sm.acc_empty[b], 32 * N_EPI);
-            mbar_init(&sm.meta_full[b], TC_M);
-            mbar_init(&sm.meta_empty[b], 32 * N_EPI);
+            mbar_init(&sm.acc_empty[b], N_EPI);          // one per epilogue warp
+            mbar_init(&sm.meta_full[b], TC_M / 32);
+            mbar_init(&sm.meta_empty[b], N_EPI);
         }
         mbar_init(sm.drain, 1);
         sm.flags[0] = 0;
@@ -186,19 +186,39 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
 
     if (warp < 4) {
         // ======================= builders =======================
-        // Geometry with one thread per cell; the operand C with one lane per
-        // QL consecutive quadrature points and a loop over the warp's 32 cells,
-        // so that coefficient loads are coalesced and every lane writes one
-        // 32-bit word of a 128-byte operand row per step.
-        constexpr int QL = KCE / 32;            // points per lane: 2 (bf16/fp16), 1 (tf32), 4 (e4m3)
-        constexpr bool WIN_REG = (QL <= 2);     // keep the coefficient window in registers
-        constexpr int RB = 8 / QL;              // rows per batch of in-flight coefficient loads
+        // Geometry with one thread per cell.  For the 16- and 32-bit formats
+        // the operand C is built with one thread per cell too: the thread keeps
+        // its cell's coefficient window w_q kappa_cq (one 128-byte chunk's worth
+        // of points) in registers and writes its own 128-byte K-major row as
+        // eight swizzled 16-byte stores.  For e4m3 (128 points per chunk) the
+        // window is held one lane per 4 points over the warp's 32 cells, with
+        // coalesced coefficient loads and one 32-bit word per lane and row.
+        constexpr bool CELL_ROWS = (PREC != FE_PREC_E4M3);
+        constexpr int QL = KCE / 32;            // e4m3: points per lane
+        constexpr int RB = 8 / QL;              // e4m3: rows per batch of in-flight coefficient loads
         const int cl = tid;
         const int wrow0 = warp * 32;
         int ac = 0, jb = 0, nonfinite = 0;
-        float win[WIN_REG ? 32 * QL : 1];
+        float win[CELL_ROWS ? KCE : 1];
         float om[QL];
         const TcSeg *cur = nullptr;
+        // win[i] = w_q kappa_{cell, q}, q = qw * KCE + i (this thread's cell)
+        auto load_own = [&](const double *__restrict__ kappa, int n_q, int64_t cell, bool valid, int qw) {
+            constexpr int LB = 16;   // loads in flight
+            const double *row = kappa + cell * n_q + qw * KCE;
+#pragma unroll
+            for (int i0 = 0; i0 < KCE; i0 += LB) {
+                double raw[LB];
+#pragma unroll
+                for (int i = 0; i < LB; ++i)
+                    raw[i] = (valid && qw * KCE + i0 + i < n_q) ? __ldg(row + i0 + i) : 0.0;
+#pragma unroll
+                for (int i = 0; i < LB; ++i) {
+                    const int q = qw * KCE + i0 + i;
+                    win[i0 + i] = (q < n_q) ? f64_to_f32_rne(raw[i], nonfinite) * sm.omega[q] : 0.f;
+                }
+            }
+        };
         auto load_rows = [&](const double *__restrict__ kappa, int64_t n_cells, int n_q, int64_t tile_cell0, int qw,
                              float *dst) {
             // dst[r * QL + i] = w_q kappa_{cell r, q}, q = qw * KCE + lane * QL + i
@@ -265,9 +285,19 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 }
             }
             if (st) atomicOr(&sm.flags[1], st);
-            // per-cell largest |w_q kappa_cq| (for the narrow-exponent formats)
+            // per-cell largest |w_q kappa_cq| (for the narrow-exponent formats); a
+            // tile whose points fit one window loads it here and takes the maximum
+            // from the registers
             float wmax = 0.f;
-            if (a.target_exp > 1) {
+            int qw_loaded = -1;
+            if (CELL_ROWS && s_nq <= KCE) {
+                load_own(s_kappa, s_nq, cell, valid, 0);
+                qw_loaded = 0;
+                if (a.target_exp > 1) {
+#pragma unroll
+                    for (int i = 0; i < KCE; ++i) wmax = fmaxf(wmax, fabsf(win[i]));
+                }
+            } else if (a.target_exp > 1) {
                 for (int r = 0; r < 32; ++r) {
                     const int64_t cell_r = tile_cell0 + wrow0 + r;
                     float m = 0.f;
@@ -308,22 +338,22 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 }
             }
             __syncwarp();
-            int qw_loaded = -1;
             for (int f = 0; f < MAX_FORMS; ++f) {
                 if (!(S.form_mask & (1 << f))) continue;
                 const TcOperand op = S.op[f];
                 const int per_qw = op.n_pairs * op.n_blk;
                 for (int n = 0; n < op.n_pass; ++n) {
                     const int b = jb & 1, ub = jb >> 1;
-                    if (jb >= 2 && !mbar_wait(&sm.meta_empty[b], (ub - 1) & 1, deadline)) {
+                    if (jb >= 2 && !mbar_wait_warp(&sm.meta_empty[b], (ub - 1) & 1, deadline)) {
                         sm.flags[0] = 1;
                         break;
                     }
                     sm.meta[b * TC_M + cl] = unscale_f[f];
-                    mbar_arrive(&sm.meta_full[b]);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm.meta_full[b]);
                     for (int ch = 0; ch < op.n_kchunks; ++ch) {
                         const int s = ac % RING, ua = ac / RING;
-                        if (ac >= RING && !mbar_wait(&sm.a_empty[s], (ua - 1) & 1, deadline)) {
+                        if (ac >= RING && !mbar_wait_warp(&sm.a_empty[s], (ua - 1) & 1, deadline)) {
                             sm.flags[0] = 1;
                             break;
                         }
@@ -331,38 +361,58 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         const int j = (ch / op.n_blk) % op.n_pairs;
                         const int blk = ch % op.n_blk;
                         const int cidx = (f == 0) ? j : 6;
-                        float wtmp[WIN_REG ? 1 : 32 * QL];
-                        float *w = WIN_REG ? win : wtmp;
-                        if (!WIN_REG) {
-                            load_rows(s_kappa, s_ncells, s_nq, tile_cell0, qw, w);
-                        } else if (qw != qw_loaded) {
-                            qw_loaded = qw;
-                            load_rows(s_kappa, s_ncells, s_nq, tile_cell0, qw, w);
-                        }
                         uint8_t *stA = sm.A + s * (TC_M * TC_CHUNK_BYTES);
-                        const int byte = lane * 4;   // this lane's word inside a 128-byte row
-#pragma unroll
-                        for (int r = 0; r < 32; ++r) {
-                            const int R = wrow0 + r;
-                            const float gj = sm.rowc[R * 8 + cidx];
-                            uint32_t word;
-                            if constexpr (PREC == FE_PREC_BF16) {
-                                word = pack_bf16x2(w[r * QL] * gj, w[r * QL + 1] * gj);
-                            } else if constexpr (PREC == FE_PREC_FP16) {
-                                word = pack_f16x2(w[r * QL] * gj, w[r * QL + 1] * gj);
-                            } else if constexpr (EB == 4) {
-                                const float v = w[r * QL] * gj;
-                                word = round_tf32(v);
-                                if (PREC == FE_PREC_TF32X3 && blk == 2) word = round_tf32(v - __uint_as_float(word));
-                            } else {
-                                word = pack_e4m3x2(w[r * QL] * gj, w[r * QL + 1] * gj) |
-                                       (pack_e4m3x2(w[r * QL + 2] * gj, w[r * QL + 3] * gj) << 16);
+                        if constexpr (CELL_ROWS) {
+                            if (qw != qw_loaded) {
+                                qw_loaded = qw;
+                                load_own(s_kappa, s_nq, cell, valid, qw);
                             }
-                            *reinterpret_cast<uint32_t *>(stA + (R >> 3) * 1024 + (R & 7) * 128 +
-                                                          ((((byte >> 4) ^ (R & 7)) & 7) << 4) + (byte & 15)) = word;
+                            const float gj = sm.rowc[cl * 8 + cidx];
+                            uint8_t *rowp = stA + (cl >> 3) * 1024 + (cl & 7) * 128;
+                            constexpr int GE = 16 / EB;   // elements per 16-byte granule
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const float *w = win + k * GE;
+                                uint4 v;
+                                if constexpr (PREC == FE_PREC_BF16) {
+                                    v.x = pack_bf16x2(w[0] * gj, w[1] * gj);
+                                    v.y = pack_bf16x2(w[2] * gj, w[3] * gj);
+                                    v.z = pack_bf16x2(w[4] * gj, w[5] * gj);
+                                    v.w = pack_bf16x2(w[6] * gj, w[7] * gj);
+                                } else if constexpr (PREC == FE_PREC_FP16) {
+                                    v.x = pack_f16x2(w[0] * gj, w[1] * gj);
+                                    v.y = pack_f16x2(w[2] * gj, w[3] * gj);
+                                    v.z = pack_f16x2(w[4] * gj, w[5] * gj);
+                                    v.w = pack_f16x2(w[6] * gj, w[7] * gj);
+                                } else {
+                                    uint32_t u[4];
+#pragma unroll
+                                    for (int e = 0; e < 4; ++e) {
+                                        const float x = w[e] * gj;
+                                        u[e] = round_tf32(x);
+                                        if (PREC == FE_PREC_TF32X3 && blk == 2) u[e] = round_tf32(x - __uint_as_float(u[e]));
+                                    }
+                                    v = make_uint4(u[0], u[1], u[2], u[3]);
+                                }
+                                *reinterpret_cast<uint4 *>(rowp + ((k ^ (cl & 7)) << 4)) = v;
+                            }
+                        } else {
+                            float w[32 * QL];
+                            load_rows(s_kappa, s_ncells, s_nq, tile_cell0, qw, w);
+                            const int byte = lane * 4;   // this lane's word inside a 128-byte row
+#pragma unroll
+                            for (int r = 0; r < 32; ++r) {
+                                const int R = wrow0 + r;
+                                const float gj = sm.rowc[R * 8 + cidx];
+                                const uint32_t word = pack_e4m3x2(w[r * QL] * gj, w[r * QL + 1] * gj) |
+                                                      (pack_e4m3x2(w[r * QL + 2] * gj, w[r * QL + 3] * gj) << 16);
+                                *reinterpret_cast<uint32_t *>(stA + (R >> 3) * 1024 + (R & 7) * 128 +
+                                                              ((((byte >> 4) ^ (R & 7)) & 7) << 4) + (byte & 15)) = word;
+                            }
                         }
                         fence_proxy_async();
-                        mbar_arrive(&sm.a_full[s]);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sm.a_full[s]);
                         ++ac;
                     }
                     ++jb;
@@ -386,7 +436,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 const uint32_t bytes = (uint32_t)op.NP * TC_CHUNK_BYTES;
                 const int s = (int)(bc % RING);
                 const int64_t ub = bc / RING;
-                if (bc >= RING && !mbar_wait(&sm.b_empty[s], (uint32_t)((ub - 1) & 1), deadline)) return false;
+                if (bc >= RING && !mbar_wait_warp(&sm.b_empty[s], (uint32_t)((ub - 1) & 1), deadline)) return false;
                 if (lane == 0) {
                     mbar_arrive_expect_tx(&sm.b_full[s], bytes);
                     bulk_g2s(sm.B + (size_t)s * NPm * TC_CHUNK_BYTES, op.img + ((size_t)bn * op.n_kchunks + bch) * bytes,
@@ -422,7 +472,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 const uint32_t idesc = a.idesc | ((uint32_t)(op.NP >> 3) << 17);
                 for (int n = 0; n < op.n_pass && !fail; ++n) {
                     const int b = jb & 1, ub = jb >> 1;
-                    if (jb >= 2 && !mbar_wait(&sm.acc_empty[b], (ub - 1) & 1, deadline)) {
+                    if (jb >= 2 && !mbar_wait_warp(&sm.acc_empty[b], (ub - 1) & 1, deadline)) {
                         fail = true;
                         break;
                     }
@@ -431,7 +481,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                     for (int ch = 0; ch < op.n_kchunks; ++ch) {
                         const int sa = (int)(mc % RING);
                         const uint32_t par = (uint32_t)((mc / RING) & 1);
-                        if (!mbar_wait(&sm.a_full[sa], par, deadline) || !mbar_wait(&sm.b_full[sa], par, deadline)) {
+                        if (!mbar_wait_warp(&sm.a_full[sa], par, deadline) || !mbar_wait_warp(&sm.b_full[sa], par, deadline)) {
                             fail = true;
                             break;
                         }
@@ -500,13 +550,14 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 const int32_t *__restrict__ s_symkl = S.sym_kl;
                 for (int n = 0; n < op.n_pass; ++n) {
                     const int b = jb & 1, ub = jb >> 1;
-                    if (!mbar_wait(&sm.acc_full[b], ub & 1, deadline) || !mbar_wait(&sm.meta_full[b], ub & 1, deadline)) {
+                    if (!mbar_wait_warp(&sm.acc_full[b], ub & 1, deadline) || !mbar_wait_warp(&sm.meta_full[b], ub & 1, deadline)) {
                         sm.flags[0] = 1;
                         break;
                     }
                     tc_fence_after();
                     const float us = sm.meta[b * TC_M + g * 32 + lane];
-                    mbar_arrive(&sm.meta_empty[b]);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm.meta_empty[b]);
                     const uint32_t tbase = tmem + (uint32_t)(b * ACC_COLS) + ((uint32_t)(g * 32) << 16);
                     const int64_t cell0 = (t - S.tile_begin) * TC_M + g * 32;
                     if (s_staged) {
@@ -519,7 +570,8 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                                 if (c0 + i < op.NP) mine[c0 + i] = __uint_as_float(r[i]) * us;
                         }
                         tc_fence_before();
-                        mbar_arrive(&sm.acc_empty[b]);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sm.acc_empty[b]);
                         named_bar_sync(1 + g, 64);
                         // whole row-major matrices of 16 consecutive cells (loads first, then stores)
                         if (out) {
@@ -533,7 +585,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
 #pragma unroll
                                 for (int it = 0; it < MAX_F2S_IT; ++it) {
                                     const int pos = lane + 32 * it;
-                                    if (it < n_it && pos < nph2) dst[pos] = vals[it];
+                                    if (it < n_it && pos < nph2) __stcs(dst + pos, vals[it]);
                                 }
                             }
                         }
@@ -552,14 +604,15 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                                         const int32_t kl = __ldg(s_symkl + col);
                                         const int k = kl & 0xFFFF, l = kl >> 16;
                                         const float v = __uint_as_float(r[i]) * us;
-                                        dst[k * nph + l] = v;
-                                        dst[l * nph + k] = v;
+                                        __stcs(dst + k * nph + l, v);
+                                        __stcs(dst + l * nph + k, v);
                                     }
                                 }
                             }
                         }
                         tc_fence_before();
-                        mbar_arrive(&sm.acc_empty[b]);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sm.acc_empty[b]);
                     }
                     ++jb;
                 }
