@@ -204,8 +204,28 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         const TcSeg *cur = nullptr;
         // win[i] = w_q kappa_{cell, q}, q = qw * KCE + i (this thread's cell)
         auto load_own = [&](const double *__restrict__ kappa, int n_q, int64_t cell, bool valid, int qw) {
-            constexpr int LB = 16;   // loads in flight
+            constexpr int LB = 16;   // values in flight
             const double *row = kappa + cell * n_q + qw * KCE;
+            // two values per 16-byte load where the rows are 16-byte aligned (window
+            // starts are even since KCE is)
+            if (((n_q & 1) == 0) && ((reinterpret_cast<uintptr_t>(kappa) & 15) == 0)) {
+#pragma unroll
+                for (int i0 = 0; i0 < KCE; i0 += LB) {
+                    double2 raw[LB / 2];
+#pragma unroll
+                    for (int i = 0; i < LB / 2; ++i)
+                        raw[i] = (valid && qw * KCE + i0 + 2 * i < n_q)
+                                     ? __ldg(reinterpret_cast<const double2 *>(row + i0 + 2 * i))
+                                     : make_double2(0.0, 0.0);
+#pragma unroll
+                    for (int i = 0; i < LB / 2; ++i) {
+                        const int q = qw * KCE + i0 + 2 * i;
+                        win[i0 + 2 * i] = (q < n_q) ? f64_to_f32_rne(raw[i].x, nonfinite) * sm.omega[q] : 0.f;
+                        win[i0 + 2 * i + 1] = (q < n_q) ? f64_to_f32_rne(raw[i].y, nonfinite) * sm.omega[q + 1] : 0.f;
+                    }
+                }
+                return;
+            }
 #pragma unroll
             for (int i0 = 0; i0 < KCE; i0 += LB) {
                 double raw[LB];
@@ -533,10 +553,14 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             const TcSeg &S = seg_of<BATCHED>(a, t);
             const int nph = S.n_phi, nph2 = nph * nph;
             const int n_it = (nph2 + 31) / 32;
+            // 16-byte stores when every matrix starts on a 16-byte boundary
+            const bool v4 = (nph2 & 3) == 0;
             if (&S != cur) {
+                // sym index of each output position this lane writes: v4 -> positions
+                // 128 it + 4 lane + e in register 4 it + e; otherwise lane + 32 it
 #pragma unroll
                 for (int it = 0; it < MAX_F2S_IT; ++it) {
-                    const int pos = lane + 32 * it;
+                    const int pos = v4 ? 128 * (it >> 2) + 4 * lane + (it & 3) : lane + 32 * it;
                     f2s_reg[it] = (S.staged && pos < nph2) ? __ldg(S.full2sym + pos) : 0;
                 }
                 cur = &S;
@@ -574,7 +598,30 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         if (lane == 0) mbar_arrive(&sm.acc_empty[b]);
                         named_bar_sync(1 + g, 64);
                         // whole row-major matrices of 16 consecutive cells (loads first, then stores)
-                        if (out) {
+                        if (out && v4) {
+                            // two cells per step, 16-byte coalesced stores
+                            for (int cc = 16 * h; cc < 16 * h + 16; cc += 2) {
+                                float4 vals[2][MAX_F2S_IT / 4];
+#pragma unroll
+                                for (int u = 0; u < 2; ++u) {
+                                    const float *__restrict__ src = stg + (cc + u) * pitch;
+#pragma unroll
+                                    for (int it = 0; it < MAX_F2S_IT / 4; ++it)
+                                        vals[u][it] = make_float4(src[f2s_reg[4 * it]], src[f2s_reg[4 * it + 1]],
+                                                                  src[f2s_reg[4 * it + 2]], src[f2s_reg[4 * it + 3]]);
+                                }
+#pragma unroll
+                                for (int u = 0; u < 2; ++u) {
+                                    if (cell0 + cc + u >= s_ncells) break;
+                                    float *__restrict__ dst = out + (cell0 + cc + u) * (int64_t)nph2;
+#pragma unroll
+                                    for (int it = 0; it < MAX_F2S_IT / 4; ++it) {
+                                        const int pos = 128 * it + 4 * lane;
+                                        if (pos < nph2) __stcs(reinterpret_cast<float4 *>(dst + pos), vals[u][it]);
+                                    }
+                                }
+                            }
+                        } else if (out) {
                             for (int cc = 16 * h; cc < 16 * h + 16; ++cc) {
                                 if (cell0 + cc >= s_ncells) break;
                                 float *__restrict__ dst = out + (cell0 + cc) * (int64_t)nph2;
