@@ -103,12 +103,39 @@ def make_inputs():
 
 
 def algorithmic_bytes(plan, prec):
+    """Bytes each kernel must move through HBM per launch (both forms).
+
+    factor:   kappa (FP64) + connectivity + vertices in; FP32 window (n_q padded
+              to 4) + 64-byte per-cell factor record out.
+    element:  window + the 48 used bytes of the factor record in; element
+              matrices of both forms out (the shared operand P stays in L2).
+    assembly: element matrices of both forms, a 2-byte stage position per
+              element entry, a 1-byte segment length per CSR value and the
+              incidence list in; CSR values of both forms out.
+    """
     eb = 8 if prec == "fp64" else 4
     nc, nph, nq = plan.n_cells, plan.n_phi, plan.n_q
-    elem = nc * nq * 8 + nc * 4 * 4 + plan.n_vertices * 3 * 8 + 2 * nc * nph * nph * eb
-    asm = (2 * nc * nph * nph * eb + 2 * plan.nnz * eb + (plan.n_dofs + 1) * 16 + nc * nph * 4
-           + nc * nph * nph * 2)
-    return elem, asm
+    ldw = (nq + 3) // 4 * 4
+    d = plan.d
+    factor = nc * nq * 8 + nc * (d + 1) * 4 + plan.n_vertices * d * 8 + nc * ldw * 4 + nc * 64
+    elem = nc * ldw * 4 + nc * 48 + 2 * nc * nph * nph * eb
+    asm = 2 * nc * nph * nph * eb + nc * nph * nph * 2 + plan.nnz + nc * nph * 4 + 2 * plan.nnz * eb
+    return factor, elem, asm
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
+    kernel's source is unchanged since the capture (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+        src = os.path.join(ROOT, "paper_2410_12614_gb300", "csrc", rec["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["sha256"]:
+            return None
+        return rec["dram_bytes_per_launch"]
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def run_ours(args, rank, world):
@@ -137,7 +164,7 @@ def run_ours(args, rank, world):
             for _ in range(warmup):
                 plan.assemble(kap, prec=prec, elements=els, out=vals)
             plan.sync()
-            step_ms, el_ms, as_ms = [], [], []
+            step_ms, el_ms, as_ms, fa_ms = [], [], [], []
             launches = 0
             for _ in range(steps):
                 flush.fill_(1.0)
@@ -152,9 +179,10 @@ def run_ours(args, rank, world):
                 st = plan.stage_times()
                 el_ms.append(st[0])
                 as_ms.append(st[1])
+                fa_ms.append(st[3])
             plan.sync()
             plan.enable_timing(False)
-            return step_ms, el_ms, as_ms, launches, els, vals
+            return step_ms, (fa_ms, el_ms, as_ms), launches, els, vals
 
         # headline: BF16
         if world > 1:
@@ -162,7 +190,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         sampler = ClockSampler(dev)
         sampler.start()
-        step_ms, el_ms, as_ms, launches, els, vals = timed("bf16", args.steps, args.warmup)
+        step_ms, (fa_ms, el_ms, as_ms), launches, els, vals = timed("bf16", args.steps, args.warmup)
         clocks = sampler.stop()
         torch.cuda.synchronize()
         if world > 1:
@@ -192,19 +220,20 @@ def run_ours(args, rank, world):
         # other precisions (context lines)
         extra = {}
         for prec, k in (("fp16", max(3, args.steps // 2)), ("fp64", 3)):
-            s2, e2, a2, _, _, _ = timed(prec, k, 1)
-            extra[prec] = {"ms_per_step": statistics.mean(s2), "element_kernel_ms": statistics.mean(e2),
-                           "assembly_kernel_ms": statistics.mean(a2),
+            s2, (f2, e2, a2), _, _, _ = timed(prec, k, 1)
+            extra[prec] = {"ms_per_step": statistics.mean(s2), "factor_kernel_ms": statistics.mean(f2),
+                           "element_kernel_ms": statistics.mean(e2), "assembly_kernel_ms": statistics.mean(a2),
                            "element_matrices_per_s": elems_per_step / (statistics.mean(s2) / 1e3)}
         extra["bf16_speedup_vs_fp64"] = extra["fp64"]["ms_per_step"] / ms_step
 
     hbm, how = _peaks()
-    eb, ab = algorithmic_bytes(plan, "bf16")
-    el_avg, as_avg = statistics.mean(el_ms), statistics.mean(as_ms)
-    if as_avg >= el_avg:
-        dom, dom_ms, dom_bytes = "assembly (segmented row reduction)", as_avg, ab
-    else:
-        dom, dom_ms, dom_bytes = "element matrices (tcgen05 BF16)", el_avg, eb
+    fb, eb, ab = algorithmic_bytes(plan, "bf16")
+    fa_avg, el_avg, as_avg = statistics.mean(fa_ms), statistics.mean(el_ms), statistics.mean(as_ms)
+    kernels = {"factor_kernel": ("factor (geometry + coefficient window)", fa_avg, fb),
+               "tc_element_kernel": ("element matrices (tcgen05 BF16)", el_avg, eb),
+               "assemble_kernel": ("assembly (chunked segmented reduction)", as_avg, ab)}
+    dom_key = max(kernels, key=lambda k: kernels[k][1])
+    dom, dom_ms, dom_bytes = kernels[dom_key]
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9
     result = {
         "metric": METRIC,
@@ -224,9 +253,13 @@ def run_ours(args, rank, world):
                    "l2": "flushed between steps (512 MB write outside the timed events)",
                    "parallelism": f"independent replica per GPU x{world}"},
         "nnz_per_s": nnz_per_s,
-        "stage_ms": {"element_kernel": el_avg, "assembly_kernel": as_avg},
+        "stage_ms": {"factor_kernel": fa_avg, "element_kernel": el_avg, "assembly_kernel": as_avg},
+        "kernels": {k: {"ms": v[1], "algorithmic_bytes": v[2], "achieved_gbs": v[2] / (v[1] / 1e3) / 1e9,
+                        "frac_of_peak": v[2] / (v[1] / 1e3) / 1e9 / hbm, "traffic": _traffic(k)}
+                    for k, v in kernels.items()},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None, "peak_source": f"{how} (MEASURED_PEAKS.json hbm_gbs)",
+                     "frac": achieved / hbm, "traffic": _traffic(dom_key),
+                     "peak_source": f"{how} (MEASURED_PEAKS.json hbm_gbs, copy burst)",
                      "algorithmic_bytes_per_launch": dom_bytes},
         "e2e": {"value": elems_per_step / (e2e_step / 1e3) * world, "unit": "element matrices/s",
                 "h2d_bytes_per_step": int(plan.n_cells * plan.n_q * 8),

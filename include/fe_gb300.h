@@ -271,7 +271,9 @@ fe_status fe_sync_status(fe_plan *plan);
 
 /* Per-stage GPU times (milliseconds) of the most recent call made while
  * timing was enabled: [0] element-matrix kernel(s), [1] assembly kernel,
- * [2] adjoint kernel(s).  Timing uses CUDA events on the plan's stream. */
+ * [2] adjoint kernel(s), [3] factor kernel (geometry, coefficient window and
+ * per-cell scales of the tensor-core paths).  n <= 4 values are written.
+ * Timing uses CUDA events on the plan's stream. */
 fe_status fe_plan_enable_timing(fe_plan *plan, int enable);
 fe_status fe_plan_stage_times(fe_plan *plan, float *ms, int n);
 

@@ -223,8 +223,8 @@ class Plan:
         check(load().fe_plan_enable_timing(self._h, int(on)))
 
     def stage_times(self):
-        ms = (ctypes.c_float * 3)()
-        check(load().fe_plan_stage_times(self._h, ms, 3))
+        ms = (ctypes.c_float * 4)()
+        check(load().fe_plan_stage_times(self._h, ms, 4))
         return list(ms)
 
     def last_launches(self):

@@ -88,9 +88,10 @@ struct fe_plan {
     DevBuf img[6][2];
     TcOperand op[6][2];
     DevBuf ws_elem[2], ws_kappa, ws_csr[2], ws_adj_x, ws_adj_L, ws_Lsum;
+    DevBuf ws_win, ws_cellf;             // factor kernel outputs (window, per-cell factors)
     bool timing = false;
-    cudaEvent_t ev[6] = {};
-    float stage_ms[3] = {0, 0, 0};
+    cudaEvent_t ev[8] = {};
+    float stage_ms[4] = {0, 0, 0, 0};
     int last_launches = 0;
     int stage_marks = 0;
     std::vector<int> host_status;
@@ -358,13 +359,13 @@ fe_status fe_plan_stage_times(fe_plan *plan, float *ms, int n) {
     if (!plan || !ms) return fail(FE_ERR_INVALID_ARG, "NULL argument");
     if (plan->timing && plan->stage_marks) {
         FE_CUDA(cudaStreamSynchronize(plan->stream), "timing sync");
-        for (int i = 0; i < 3; ++i) {
+        for (int i = 0; i < 4; ++i) {
             plan->stage_ms[i] = 0.f;
             if (plan->stage_marks & (1 << i)) cudaEventElapsedTime(&plan->stage_ms[i], plan->ev[2 * i], plan->ev[2 * i + 1]);
         }
         plan->stage_marks = 0;
     }
-    for (int i = 0; i < n && i < 3; ++i) ms[i] = plan->stage_ms[i];
+    for (int i = 0; i < n && i < 4; ++i) ms[i] = plan->stage_ms[i];
     return FE_OK;
 }
 
@@ -410,9 +411,22 @@ static fe_status check_call(fe_plan *plan, unsigned forms, fe_precision prec) {
 // ---------------------------------------------------------------------------
 // segments shared by single-plan calls and batches
 // ---------------------------------------------------------------------------
+static fe_status ensure_ws(DevBuf &b, size_t bytes, const char *what) {
+    cudaError_t e = b.alloc(bytes);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return FE_OK;
+}
+
+// Bytes of the factor kernel's outputs for one plan.
+static size_t win_bytes(const fe_plan *P) { return sizeof(float) * (size_t)P->n_cells * win_ld(P->n_q); }
+static size_t cellf_bytes(const fe_plan *P) { return sizeof(float) * (size_t)P->n_cells * CELLF; }
+
 static TcSeg make_tc_seg(fe_plan *P, unsigned forms, int prec, const double *vertices, const double *kappa,
-                         void *const A[2]) {
+                         void *const A[2], float *win, float *cellf) {
     TcSeg g{};
+    g.win = win;
+    g.cellf = cellf;
+    g.ldw = win_ld(P->n_q);
     g.vertices = vertices ? vertices : P->vertices.as<double>();
     g.cells = P->cells.as<int32_t>();
     g.n_cells = P->n_cells;
@@ -500,8 +514,8 @@ static int n_forms_of(unsigned forms) { return ((forms & FE_FORM_STIFFNESS) ? 1 
 static fe_status run_elements(fe_plan *P, unsigned forms, fe_precision prec, const double *vertices,
                               const double *kappa, void *A[2], int &launches) {
     const double *verts = vertices ? vertices : P->vertices.as<double>();
-    mark(P, 0, true);
     if (prec == FE_PREC_FP64) {
+        mark(P, 0, true);
         for (unsigned form : {(unsigned)FE_FORM_STIFFNESS, (unsigned)FE_FORM_MASS}) {
             if (!(forms & form)) continue;
             F64Args a{};
@@ -523,22 +537,25 @@ static fe_status run_elements(fe_plan *P, unsigned forms, fe_precision prec, con
         }
     } else {
         TcArgs a{};
-        a.seg0 = make_tc_seg(P, forms, prec, verts, kappa, A);
+        fe_status st = ensure_ws(P->ws_win, win_bytes(P), "coefficient window workspace");
+        if (!st) st = ensure_ws(P->ws_cellf, cellf_bytes(P), "cell factor workspace");
+        if (st) return st;
+        a.seg0 = make_tc_seg(P, forms, prec, verts, kappa, A, P->ws_win.as<float>(), P->ws_cellf.as<float>());
         a.segs = nullptr;
         a.n_segs = 1;
         tc_finalize(a, &a.seg0, 1, prec, P->status.as<int>());
         const size_t smem = tc_smem_bytes(a);
-        int r = launch_tc_elements(a, smem, P->stream);
+        mark(P, 3, true);
+        int r = launch_factor(a, P->stream);
+        if (r < 0) return cuda_fail((cudaError_t)(-r), "factor kernel launch");
+        launches += r;
+        mark(P, 3, false);
+        mark(P, 0, true);
+        r = launch_tc_elements(a, smem, P->stream);
         if (r < 0) return cuda_fail((cudaError_t)(-r), "tensor-core element kernel launch");
         launches += r;
     }
     mark(P, 0, false);
-    return FE_OK;
-}
-
-static fe_status ensure_ws(DevBuf &b, size_t bytes, const char *what) {
-    cudaError_t e = b.alloc(bytes);
-    if (e != cudaSuccess) return cuda_fail(e, what);
     return FE_OK;
 }
 
@@ -620,8 +637,10 @@ static fe_status autotune_plan(fe_plan &P) {
                 // sample: at most one tile per SM and at most 256 MB of element output
                 int64_t n = std::min<int64_t>(P.n_cells, (int64_t)sms * TC_M);
                 n = std::min<int64_t>(n, std::max<int64_t>(TC_M, (256ll << 20) / (4ll * P.n_phi * P.n_phi)));
-                DevBuf kap, out;
+                DevBuf kap, out, win, cellf;
                 FE_CUDA(kap.alloc(sizeof(double) * n * P.n_q), "autotune buffer");
+                FE_CUDA(win.alloc(sizeof(float) * n * win_ld(P.n_q)), "autotune buffer");
+                FE_CUDA(cellf.alloc(sizeof(float) * n * CELLF), "autotune buffer");
                 FE_CUDA(out.alloc(sizeof(float) * n * P.n_phi * P.n_phi), "autotune buffer");
                 std::vector<double> ones((size_t)n * P.n_q, 1.0);
                 FE_CUDA(cudaMemcpyAsync(kap.p, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice,
@@ -633,11 +652,16 @@ static fe_status autotune_plan(fe_plan &P) {
                     void *A[2] = {nullptr, nullptr};
                     A[fi] = out.p;
                     TcArgs a{};
-                    a.seg0 = make_tc_seg(&P, form, prec, nullptr, kap.as<double>(), A);
+                    a.seg0 = make_tc_seg(&P, form, prec, nullptr, kap.as<double>(), A, win.as<float>(),
+                                         cellf.as<float>());
                     a.seg0.n_cells = n;
                     a.n_segs = 1;
                     tc_finalize(a, &a.seg0, 1, prec, P.status.as<int>());
                     const size_t smem = tc_smem_bytes(a);
+                    {
+                        const int r = launch_factor(a, P.stream);
+                        if (r < 0) return cuda_fail((cudaError_t)(-r), "autotune factor launch");
+                    }
                     float ms_min = 1e30f;
                     for (int rep = 0; rep < 3; ++rep) {
                         FE_CUDA(cudaEventRecord(P.ev[4], P.stream), "autotune event");
@@ -879,7 +903,10 @@ static fe_status batch_launch(fe_batch &B, int &launches) {
             launches += r;
         }
     } else {
-        int r = launch_tc_elements(B.targs, B.smem, B.stream);
+        int r = launch_factor(B.targs, B.stream);
+        if (r < 0) return cuda_fail((cudaError_t)(-r), "factor kernel launch");
+        launches += r;
+        r = launch_tc_elements(B.targs, B.smem, B.stream);
         if (r < 0) return cuda_fail((cudaError_t)(-r), "tensor-core element kernel launch");
         launches += r;
     }
@@ -959,7 +986,14 @@ fe_status fe_batch_create(fe_batch **out, fe_plan *const *plans, int n_plans, un
                 B.f64.push_back(a);
             }
         } else {
-            tsegs.push_back(make_tc_seg(P, forms, (int)prec, nullptr, kappa[i], A));
+            B.ws.emplace_back(new DevBuf);
+            DevBuf &w = *B.ws.back();
+            B.ws.emplace_back(new DevBuf);
+            DevBuf &cf = *B.ws.back();
+            fe_status st = ensure_ws(w, win_bytes(P), "batch window workspace");
+            if (!st) st = ensure_ws(cf, cellf_bytes(P), "batch cell factor workspace");
+            if (st) return st;
+            tsegs.push_back(make_tc_seg(P, forms, (int)prec, nullptr, kappa[i], A, w.as<float>(), cf.as<float>()));
         }
         if (want_csr) {
             void *csr[2] = {csr_stiffness ? csr_stiffness[i] : nullptr, csr_mass ? csr_mass[i] : nullptr};

@@ -22,8 +22,9 @@ struct CellGeom {
     double G[6];   // symmetric pairs (0,0),(0,1),(0,2),(1,1),(1,2),(2,2) (d=3) or (0,0),(0,1),(1,1)
 };
 
-__device__ __forceinline__ int cell_geometry(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
-                                             int64_t c, int d, CellGeom &g) {
+// J, its cofactor matrix and det J in FP64 (G left out); returns the status bits.
+__device__ __forceinline__ int cell_cofactors(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
+                                              int64_t c, int d, CellGeom &g) {
     double x[4][3];
     const int nv = d + 1;
 #pragma unroll
@@ -65,6 +66,12 @@ __device__ __forceinline__ int cell_geometry(const double *__restrict__ vertices
     int st = 0;
     if (!isfinite(g.det)) st |= ST_NONFINITE;
     else if (g.det == 0.0) st |= ST_DEGENERATE;
+    return st;
+}
+
+__device__ __forceinline__ int cell_geometry(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
+                                             int64_t c, int d, CellGeom &g) {
+    const int st = cell_cofactors(vertices, cells, c, d, g);
     const double inv = (st == 0) ? 1.0 / g.absdet : 0.0;
     if (d == 3) {
         int j = 0;
@@ -82,6 +89,29 @@ __device__ __forceinline__ int cell_geometry(const double *__restrict__ vertices
         g.G[3] = g.G[4] = g.G[5] = 0.0;
     }
     return st;
+}
+
+// FP64 -> FP32 with round-to-nearest-even (IEEE 754), entirely on the
+// integer units so that the per-quadrature-point path never touches the FP64
+// pipe: the exponent is rebiased in place and the 29 dropped mantissa bits are
+// rounded half to even (a carry into the exponent gives the correctly rounded
+// power of two, and infinity past the largest finite value).  Magnitudes below
+// FP32's smallest normal number (2^-126) are flushed to a signed zero;
+// non-finite inputs set the flag and give infinity or NaN.
+__device__ __forceinline__ float f64_to_f32_rne(double x, int &nonfinite) {
+    const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned e = static_cast<unsigned>(u >> 52) & 0x7FFu;
+    const unsigned sign = static_cast<unsigned>(u >> 63) << 31;
+    const unsigned long long mag = (u & 0x7FFFFFFFFFFFFFFFull) - (static_cast<unsigned long long>(1023 - 127) << 52);
+    const unsigned long long r = mag + 0x0FFFFFFFull + ((mag >> 29) & 1ull);
+    unsigned bits = static_cast<unsigned>(r >> 29);
+    bits = (e < 1023u - 126u) ? 0u : bits;
+    bits = (e > 1023u + 127u) ? 0x7F800000u : bits;
+    if (e == 0x7FFu) {
+        nonfinite = 1;
+        bits = (u & 0xFFFFFFFFFFFFFull) ? 0x7FC00000u : 0x7F800000u;
+    }
+    return __uint_as_float(bits | sign);
 }
 
 // --------------------------------------------------------------------------

@@ -1,0 +1,231 @@
+// Factor kernel: the per-cell inputs of the tensor-core contraction.
+//
+// For every tile of 128 cells (the element kernel's tiles, over one plan or a
+// batch of segments) it forms
+//   * the coefficient window w_q kappa_cq in FP32 (kappa rounded once from
+//     FP64 on the integer units, times the FP32 weight), row-major with a
+//     row length padded to a multiple of 4 points and zero past n_q;
+//   * the geometry of Sec. 4.2 / 3.1: J, its cofactors and det J in FP64;
+//     G = |det J| J^-1 J^-T = C^T C / |det J| from the cofactors either in
+//     FP64 and rounded once (TF32x3, whose storage precision is close to
+//     FP32's) or in FP32 from the cofactors and det J rounded once (the
+//     other formats: G then carries a few FP32 roundings, far below their
+//     u_s, and the FP64 pipe -- about two FMAs per clock per SM on this part
+//     -- does a third of the work);
+// C_(st,q) = (w_q kappa_cq) * (G_st 2^e_c) is then one FP32 product per
+// operand element in the element kernel, rounded once to the storage format
+// (the mixed strategy of Sec. 4.5 with u_s on C).
+//
+// Each CTA owns one tile: its four warps stream the tile's kappa block (a
+// contiguous range) with coalesced loads, so the factor work runs at full
+// occupancy instead of on the element kernel's four builder warps.
+#include "fe_device.cuh"
+
+namespace fe {
+
+namespace {
+
+constexpr int F_THREADS = 128;   // one thread per cell of the tile
+constexpr int F_WTS = 1024;   // weights table in shared memory (points)
+
+template <bool BATCHED>
+__device__ __forceinline__ const TcSeg &fseg_of(const TcArgs &a, int64_t t) {
+    if (!BATCHED) return a.seg0;
+    int lo = 0, hi = a.n_segs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.segs[mid].tile_begin <= t) lo = mid; else hi = mid - 1;
+    }
+    return a.segs[lo];
+}
+
+template <bool BATCHED, bool G64>
+__global__ void __launch_bounds__(F_THREADS) factor_kernel(const __grid_constant__ TcArgs a) {
+    __shared__ int rowmax[TC_M];          // max_q |w_q kappa_cq| of each row, as non-negative float bits
+    __shared__ float wts[F_WTS];          // the segment's weights in FP32 (when they fit)
+    __shared__ int flags;
+    const int tid = threadIdx.x;
+    const int64_t t = blockIdx.x;
+    const TcSeg &S = fseg_of<BATCHED>(a, t);
+    const int64_t c0 = (t - S.tile_begin) * TC_M;
+    const int nvalid = (int)((S.n_cells - c0) < TC_M ? (S.n_cells - c0) : TC_M);
+    const int n_q = S.n_q, ldw = S.ldw;
+    const double *__restrict__ kb = S.kappa + c0 * n_q;   // the tile's kappa block
+    const double *__restrict__ weights = S.weights;
+    float *__restrict__ wb = S.win + c0 * ldw;             // the tile's window block
+    const bool wts_smem = ldw <= F_WTS;
+    if (tid < TC_M) rowmax[tid] = 0;
+    if (tid == 0) flags = 0;
+    if (wts_smem)
+        for (int q = tid; q < ldw; q += F_THREADS) wts[q] = q < n_q ? (float)__ldg(weights + q) : 0.f;
+    __syncthreads();
+    // 1. the window, one item of 4 points per thread and step (consecutive
+    //    threads, consecutive items: coalesced loads and 16-byte stores)
+    int nonfinite = 0;
+    const int ipr = ldw >> 2;
+    const int n_items = nvalid * ipr;
+    const bool need_max = a.target_exp > 1;
+    const bool vec = ((n_q & 1) == 0) && ((reinterpret_cast<uintptr_t>(S.kappa) & 15) == 0);
+    constexpr int IU = 4;
+    for (int i0 = tid; i0 < n_items; i0 += F_THREADS * IU) {
+        double raw[IU][4];
+        int rr[IU], qq[IU];
+#pragma unroll
+        for (int u = 0; u < IU; ++u) {
+            const int i = i0 + u * F_THREADS;
+            const int r = i / ipr;
+            const int q = 4 * (i - r * ipr);
+            rr[u] = r;
+            qq[u] = q;
+            const double *src = kb + (int64_t)r * n_q + q;
+            if (i < n_items && vec) {
+                const double2 z = make_double2(0.0, 0.0);
+                const double2 lo = q < n_q ? __ldg(reinterpret_cast<const double2 *>(src)) : z;
+                const double2 hi = q + 2 < n_q ? __ldg(reinterpret_cast<const double2 *>(src + 2)) : z;
+                raw[u][0] = lo.x;
+                raw[u][1] = lo.y;
+                raw[u][2] = hi.x;
+                raw[u][3] = hi.y;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) raw[u][e] = (i < n_items && q + e < n_q) ? __ldg(src + e) : 0.0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < IU; ++u) {
+            const int i = i0 + u * F_THREADS;
+            if (i >= n_items) continue;
+            const int q = qq[u];
+            float v[4];
+            float m = 0.f;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float w = wts_smem ? wts[q + e] : (q + e < n_q ? (float)__ldg(weights + q + e) : 0.f);
+                v[e] = (q + e < n_q) ? f64_to_f32_rne(raw[u][e], nonfinite) * w : 0.f;
+                m = fmaxf(m, fabsf(v[e]));
+            }
+            *reinterpret_cast<float4 *>(wb + (int64_t)rr[u] * ldw + q) = make_float4(v[0], v[1], v[2], v[3]);
+            if (need_max) atomicMax(&rowmax[rr[u]], __float_as_int(m));
+        }
+    }
+    if (nonfinite) atomicOr(&flags, ST_NONFINITE);
+    __syncthreads();
+    // 2. geometry and scales, one thread per cell
+    if (tid < nvalid) {
+        const int64_t c = c0 + tid;
+        float g6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, adet = 0.f;
+        CellGeom geo;
+        int st;
+        if (G64) {
+            st = cell_geometry(S.vertices, S.cells, c, S.d, geo);
+            if (!st) {
+#pragma unroll
+                for (int j = 0; j < 6; ++j) g6[j] = (float)geo.G[j];
+                adet = (float)geo.absdet;
+            }
+        } else {
+            st = cell_cofactors(S.vertices, S.cells, c, S.d, geo);
+            if (!st) {
+                int nf = 0;
+                float C[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) C[i] = f64_to_f32_rne(geo.C[i], nf);
+                adet = f64_to_f32_rne(geo.absdet, nf);
+                const float inv = 1.0f / adet;
+                if (S.d == 3) {
+                    int j = 0;
+#pragma unroll
+                    for (int s = 0; s < 3; ++s)
+#pragma unroll
+                        for (int u = s; u < 3; ++u)
+                            g6[j++] = fmaf(C[s], C[u], fmaf(C[3 + s], C[3 + u], C[6 + s] * C[6 + u])) * inv;
+                } else {
+                    g6[0] = fmaf(C[0], C[0], C[2] * C[2]) * inv;
+                    g6[1] = fmaf(C[0], C[1], C[2] * C[3]) * inv;
+                    g6[2] = fmaf(C[1], C[1], C[3] * C[3]) * inv;
+                }
+                bool fin = nf == 0 && adet > 0.f && isfinite(inv);
+#pragma unroll
+                for (int j = 0; j < 6; ++j) fin = fin && isfinite(g6[j]);
+                if (!fin) {
+                    // cofactors or det J outside FP32's normal range: G in FP64
+                    const double inv64 = 1.0 / geo.absdet;
+                    int j = 0;
+                    if (S.d == 3) {
+#pragma unroll
+                        for (int s = 0; s < 3; ++s)
+#pragma unroll
+                            for (int u = s; u < 3; ++u)
+                                g6[j++] = (float)((geo.C[s] * geo.C[u] + geo.C[3 + s] * geo.C[3 + u] +
+                                                   geo.C[6 + s] * geo.C[6 + u]) * inv64);
+                    } else {
+                        g6[0] = (float)((geo.C[0] * geo.C[0] + geo.C[2] * geo.C[2]) * inv64);
+                        g6[1] = (float)((geo.C[0] * geo.C[1] + geo.C[2] * geo.C[3]) * inv64);
+                        g6[2] = (float)((geo.C[1] * geo.C[1] + geo.C[3] * geo.C[3]) * inv64);
+                    }
+                    adet = (float)geo.absdet;
+                }
+            }
+        }
+        if (st) {
+            atomicOr(&flags, st);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) g6[j] = 0.f;
+            adet = 0.f;
+        }
+        const float wmax = __int_as_float(rowmax[tid]);
+        float rec[CELLF];
+#pragma unroll
+        for (int i = 0; i < CELLF; ++i) rec[i] = 0.f;
+        for (int f = 0; f < MAX_FORMS; ++f) {
+            if (!(S.form_mask & (1 << f))) continue;
+            float gmax = 0.f;
+            if (f == 0) {
+#pragma unroll
+                for (int j = 0; j < 6; ++j) gmax = fmaxf(gmax, fabsf(g6[j]));
+            } else {
+                gmax = adet;
+            }
+            int e_c = 0;
+            if (need_max && !st) {
+                const float cmax = wmax * gmax;
+                if (cmax > 0.f && isfinite(cmax)) {
+                    int e;
+                    frexpf(cmax, &e);
+                    e_c = a.target_exp - e;
+                }
+            }
+            const float scale = ldexpf(1.f, e_c);
+            rec[CELLF_UNSCALE + f] = ldexpf(S.op[f].p_inv_scale, -e_c);
+            if (f == 0) {
+#pragma unroll
+                for (int j = 0; j < 6; ++j) rec[CELLF_G + j] = g6[j] * scale;
+            } else {
+                rec[CELLF_DET] = adet * scale;
+            }
+        }
+        float4 *dst = reinterpret_cast<float4 *>(S.cellf + c * CELLF);
+#pragma unroll
+        for (int i = 0; i < CELLF / 4; ++i) dst[i] = make_float4(rec[4 * i], rec[4 * i + 1], rec[4 * i + 2], rec[4 * i + 3]);
+    }
+    __syncthreads();
+    if (tid == 0 && flags) atomicOr(a.status, flags);
+}
+
+}  // namespace
+
+int launch_factor(const TcArgs &a, cudaStream_t s) {
+    if (a.n_tiles <= 0) return 0;
+    const bool g64 = a.prec == FE_PREC_TF32X3;
+    if (a.segs) {
+        if (g64) factor_kernel<true, true><<<(unsigned)a.n_tiles, F_THREADS, 0, s>>>(a);
+        else factor_kernel<true, false><<<(unsigned)a.n_tiles, F_THREADS, 0, s>>>(a);
+    } else {
+        if (g64) factor_kernel<false, true><<<(unsigned)a.n_tiles, F_THREADS, 0, s>>>(a);
+        else factor_kernel<false, false><<<(unsigned)a.n_tiles, F_THREADS, 0, s>>>(a);
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 1 : -(int)e;
+}
+
+}  // namespace fe

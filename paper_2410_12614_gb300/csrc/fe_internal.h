@@ -60,7 +60,19 @@ struct TcSeg {
     const int16_t *full2sym;   // [n_phi * n_phi]
     int staged;                // 1: staged coalesced epilogue (single pass)
     int64_t tile_begin;        // first global tile of this segment
+    // written by the factor kernel, read by the element kernel
+    float *win;                // [n_cells][ldw] w_q kappa_cq in FP32 (zero past n_q)
+    float *cellf;              // [n_cells][CELLF] per-cell factors (CELLF_* slots)
+    int ldw;                   // n_q rounded up to a multiple of 4
 };
+
+// Per-cell factor record (floats): the scaled geometry of each pair, the
+// scaled |det J| for the mass form, and the unscale of each form's accumulator.
+constexpr int CELLF = 16;
+constexpr int CELLF_G = 0;         // [0, 6): G_st * 2^e_stiffness
+constexpr int CELLF_DET = 6;       // |det J| * 2^e_mass
+constexpr int CELLF_UNSCALE = 8;   // [8, 10): unscale of form 0 / form 1
+inline int win_ld(int n_q) { return (n_q + 3) & ~3; }
 
 struct TcArgs {
     TcSeg seg0;                // the only segment when segs == nullptr
@@ -150,6 +162,9 @@ struct AdjArgs {
 // Kernel launchers (defined in the .cu files).  Return the number of
 // kernel launches made, or a negative cudaError_t on launch failure.
 int launch_tc_elements(const TcArgs &a, size_t smem_bytes, cudaStream_t s, int grid = 0);
+// Geometry, coefficient window and per-cell scales of every tile (the factor
+// kernel; run before launch_tc_elements on the same arguments).
+int launch_factor(const TcArgs &a, cudaStream_t s);
 size_t tc_smem_bytes(const TcArgs &a);
 // Whether a segment can use the staged epilogue under the given global shape.
 bool tc_can_stage(const TcArgs &a, const TcSeg &seg);

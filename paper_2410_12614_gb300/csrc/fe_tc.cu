@@ -7,7 +7,9 @@
 //   A^c_{kl} = sum_{(s<=t), q} C^c_{(st,q)} P_{(st,q),(kl)}          (k <= l)
 //
 // where C^c_{(st,q)} = w_q kappa_cq G^c_st (Sec. 3.1, C_st = diag_q(w_q z(X_q)
-// G_st)) is formed per cell from the FP64 geometry, and
+// G_st)) is formed per cell from the factor kernel's outputs (FP32 window
+// w_q kappa_cq and the FP64 geometry rounded to FP32, with the per-cell
+// scale of the narrow formats), and
 // P_{(st,q),(kl)} = B_skq B_tlq + [s != t] B_tkq B_slq is the product of the
 // tabulated reference derivatives (the triple products B_s C_st B_t^T of
 // Sec. 3.1 folded over the symmetric pairs), precomputed in FP64 at plan time
@@ -22,11 +24,10 @@
 // tile carrying its segment's shapes (cell type, degree, quadrature size) and
 // buffers.  One CTA per SM walks its tiles; a job is one (tile, form, N pass).
 // Roles:
-//   warps 0-3  builders: FP64 geometry with one thread per cell; the FP32
-//              coefficient window w_q kappa_cq loaded coalesced (one lane per
-//              quadrature point, shared by every (s,t) pair and both forms)
-//              and the 128-byte swizzled K-major rows of C written one row
-//              per warp instruction into a 2-stage ring (arrive a_full).
+//   warps 0-3  builders, one thread per cell: its factors and its window
+//              (shared by every (s,t) pair and both forms) in registers, its
+//              128-byte swizzled K-major row of C written into a 2-stage ring
+//              (one a_full arrival per warp).
 //   warps 4-11 epilogue, two warps per TMEM lane group: drain a finished
 //              accumulator into a conflict-free sym-packed staging area,
 //              release it, and write whole row-major element matrices with
@@ -52,7 +53,6 @@ constexpr int W_MMA = 12;
 constexpr int RING = 2;          // A and B ring stages
 constexpr int ACC_COLS = 256;    // columns per TMEM accumulator (2 of them)
 constexpr int MAX_F2S_IT = 16;   // n_phi^2 <= 512 for the staged epilogue
-constexpr int BAR_BUILDERS = 5;  // named barrier of the 128 builder threads
 
 struct Smem {
     uint8_t *A;        // [RING][128][128 B]
@@ -60,7 +60,6 @@ struct Smem {
     float *stage;      // [4][32][pitch_max]
     float *meta;       // [2][128] unscale per cell for the two accumulators
     float *rowc;       // [128][8] per cell: G pairs * scale (stiffness), |det J| * scale (mass)
-    float *omega;      // [nq_max] quadrature weights of the current segment
     uint64_t *a_full, *a_empty, *b_full, *b_empty, *acc_full, *acc_empty, *meta_full, *meta_empty, *drain;
     uint32_t *tmem_holder;
     int *flags;        // [0] abort, [1] status bits
@@ -82,8 +81,7 @@ __device__ inline Smem carve(uint8_t *raw, const TcArgs &a) {
     uint8_t *q = reinterpret_cast<uint8_t *>(s.stage) + bytes_stage(a);
     s.meta = reinterpret_cast<float *>(q);
     s.rowc = s.meta + 2 * TC_M;
-    s.omega = s.rowc + 8 * TC_M;
-    q = reinterpret_cast<uint8_t *>(s.omega + ((a.nq_max + 3) & ~3));
+    q = reinterpret_cast<uint8_t *>(s.rowc + 8 * TC_M);
     q = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(q) + 7) & ~uintptr_t(7));
     uint64_t *b = reinterpret_cast<uint64_t *>(q);
     s.a_full = b;
@@ -114,29 +112,6 @@ __device__ __forceinline__ const TcSeg &seg_of(const TcArgs &a, int64_t t) {
 }
 
 __device__ __forceinline__ int first_form(const TcSeg &S) { return (S.form_mask & 1) ? 0 : 1; }
-
-// FP64 -> FP32 with round-to-nearest-even (IEEE 754), entirely on the
-// integer units so that the per-quadrature-point path never touches the FP64
-// pipe: the exponent is rebiased in place and the 29 dropped mantissa bits are
-// rounded half to even (a carry into the exponent gives the correctly rounded
-// power of two, and infinity past the largest finite value).  Magnitudes below
-// FP32's smallest normal number (2^-126) are flushed to a signed zero;
-// non-finite inputs set the flag and give infinity or NaN.
-__device__ __forceinline__ float f64_to_f32_rne(double x, int &nonfinite) {
-    const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(x));
-    const unsigned e = static_cast<unsigned>(u >> 52) & 0x7FFu;
-    const unsigned sign = static_cast<unsigned>(u >> 63) << 31;
-    const unsigned long long mag = (u & 0x7FFFFFFFFFFFFFFFull) - (static_cast<unsigned long long>(1023 - 127) << 52);
-    const unsigned long long r = mag + 0x0FFFFFFFull + ((mag >> 29) & 1ull);
-    unsigned bits = static_cast<unsigned>(r >> 29);
-    bits = (e < 1023u - 126u) ? 0u : bits;
-    bits = (e > 1023u + 127u) ? 0x7F800000u : bits;
-    if (e == 0x7FFu) {
-        nonfinite = 1;
-        bits = (u & 0xFFFFFFFFFFFFFull) ? 0x7FC00000u : 0x7F800000u;
-    }
-    return __uint_as_float(bits | sign);
-}
 
 template <int PREC, bool BATCHED>
 __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_constant__ TcArgs a) {
@@ -186,176 +161,94 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
 
     if (warp < 4) {
         // ======================= builders =======================
-        // Geometry with one thread per cell.  For the 16- and 32-bit formats
-        // the operand C is built with one thread per cell too: the thread keeps
-        // its cell's coefficient window w_q kappa_cq (one 128-byte chunk's worth
-        // of points) in registers and writes its own 128-byte K-major row as
-        // eight swizzled 16-byte stores.  For e4m3 (128 points per chunk) the
-        // window is held one lane per 4 points over the warp's 32 cells, with
-        // coalesced coefficient loads and one 32-bit word per lane and row.
+        // The factor kernel has left, per cell, the FP32 coefficient window
+        // w_q kappa_cq and the scaled geometry factors.  For the 16- and 32-bit
+        // formats the operand C is built with one thread per cell: the thread
+        // keeps its cell's window (one 128-byte chunk's worth of points) in
+        // registers and writes its own 128-byte K-major row as eight swizzled
+        // 16-byte stores.  For e4m3 (128 points per chunk) the window is held
+        // one lane per 4 points over the warp's 32 cells, with coalesced loads
+        // and one 32-bit word per lane and row.
         constexpr bool CELL_ROWS = (PREC != FE_PREC_E4M3);
         constexpr int QL = KCE / 32;            // e4m3: points per lane
-        constexpr int RB = 8 / QL;              // e4m3: rows per batch of in-flight coefficient loads
         const int cl = tid;
         const int wrow0 = warp * 32;
-        int ac = 0, jb = 0, nonfinite = 0;
+        int ac = 0, jb = 0;
         float win[CELL_ROWS ? KCE : 1];
-        float om[QL];
-        const TcSeg *cur = nullptr;
         // win[i] = w_q kappa_{cell, q}, q = qw * KCE + i (this thread's cell)
-        auto load_own = [&](const double *__restrict__ kappa, int n_q, int64_t cell, bool valid, int qw) {
-            constexpr int LB = 16;   // values in flight
-            const double *row = kappa + cell * n_q + qw * KCE;
-            // two values per 16-byte load where the rows are 16-byte aligned (window
-            // starts are even since KCE is)
-            if (((n_q & 1) == 0) && ((reinterpret_cast<uintptr_t>(kappa) & 15) == 0)) {
+        auto load_own = [&](const float *__restrict__ W, int ldw, int64_t cell, bool valid, int qw) {
+            const float *row = W + cell * ldw + qw * KCE;
 #pragma unroll
-                for (int i0 = 0; i0 < KCE; i0 += LB) {
-                    double2 raw[LB / 2];
-#pragma unroll
-                    for (int i = 0; i < LB / 2; ++i)
-                        raw[i] = (valid && qw * KCE + i0 + 2 * i < n_q)
-                                     ? __ldg(reinterpret_cast<const double2 *>(row + i0 + 2 * i))
-                                     : make_double2(0.0, 0.0);
-#pragma unroll
-                    for (int i = 0; i < LB / 2; ++i) {
-                        const int q = qw * KCE + i0 + 2 * i;
-                        win[i0 + 2 * i] = (q < n_q) ? f64_to_f32_rne(raw[i].x, nonfinite) * sm.omega[q] : 0.f;
-                        win[i0 + 2 * i + 1] = (q < n_q) ? f64_to_f32_rne(raw[i].y, nonfinite) * sm.omega[q + 1] : 0.f;
-                    }
-                }
-                return;
-            }
-#pragma unroll
-            for (int i0 = 0; i0 < KCE; i0 += LB) {
-                double raw[LB];
-#pragma unroll
-                for (int i = 0; i < LB; ++i)
-                    raw[i] = (valid && qw * KCE + i0 + i < n_q) ? __ldg(row + i0 + i) : 0.0;
-#pragma unroll
-                for (int i = 0; i < LB; ++i) {
-                    const int q = qw * KCE + i0 + i;
-                    win[i0 + i] = (q < n_q) ? f64_to_f32_rne(raw[i], nonfinite) * sm.omega[q] : 0.f;
-                }
+            for (int i = 0; i < KCE; i += 4) {
+                const float4 v = (valid && qw * KCE + i < ldw) ? __ldg(reinterpret_cast<const float4 *>(row + i))
+                                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                win[i] = v.x;
+                win[i + 1] = v.y;
+                win[i + 2] = v.z;
+                win[i + 3] = v.w;
             }
         };
-        auto load_rows = [&](const double *__restrict__ kappa, int64_t n_cells, int n_q, int64_t tile_cell0, int qw,
+        // dst[r * QL + i] = w_q kappa_{cell r, q}, q = qw * KCE + lane * QL + i (e4m3)
+        auto load_rows = [&](const float *__restrict__ W, int ldw, int64_t n_cells, int64_t tile_cell0, int qw,
                              float *dst) {
-            // dst[r * QL + i] = w_q kappa_{cell r, q}, q = qw * KCE + lane * QL + i
+            const int q = qw * KCE + lane * QL;
 #pragma unroll
-            for (int i = 0; i < QL; ++i) {
-                const int q = qw * KCE + lane * QL + i;
-                om[i] = q < n_q ? sm.omega[q] : 0.f;
-            }
-#pragma unroll
-            for (int r0 = 0; r0 < 32; r0 += RB) {
-                double raw[RB * QL];
-#pragma unroll
-                for (int r = 0; r < RB; ++r) {
-                    const int64_t cell_r = tile_cell0 + wrow0 + r0 + r;
-#pragma unroll
-                    for (int i = 0; i < QL; ++i) {
-                        const int q = qw * KCE + lane * QL + i;
-                        raw[r * QL + i] = (cell_r < n_cells && q < n_q) ? __ldg(kappa + cell_r * n_q + q) : 0.0;
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < RB * QL; ++k) dst[r0 * QL + k] = f64_to_f32_rne(raw[k], nonfinite) * om[k % QL];
+            for (int r = 0; r < 32; ++r) {
+                const int64_t cell_r = tile_cell0 + wrow0 + r;
+                const float4 v = (cell_r < n_cells && q < ldw) ? __ldg(reinterpret_cast<const float4 *>(W + cell_r * ldw + q))
+                                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                dst[r * QL] = v.x;
+                dst[r * QL + 1] = v.y;
+                dst[r * QL + 2] = v.z;
+                dst[r * QL + 3] = v.w;
             }
         };
-        // the coefficient and connectivity blocks of a tile are contiguous: pull the
-        // next tile's into L2 while this one is built
+        // the window and factor blocks of a tile are contiguous: pull the next
+        // tile's into L2 while this one is built
         auto prefetch_tile = [&](int64_t tt) {
             if (tt >= n_tiles || cl != 0) return;
             const TcSeg &S = seg_of<BATCHED>(a, tt);
             const int64_t c0 = (tt - S.tile_begin) * TC_M;
             const int64_t nc = (S.n_cells - c0) < TC_M ? (S.n_cells - c0) : TC_M;
-            const uint32_t kb = (uint32_t)((nc * S.n_q * 8) & ~int64_t(15));
-            const uint32_t cb = (uint32_t)((nc * (S.d + 1) * 4) & ~int64_t(15));
-            if (kb && ((reinterpret_cast<uintptr_t>(S.kappa + c0 * S.n_q) & 15) == 0)) prefetch_l2(S.kappa + c0 * S.n_q, kb);
-            if (cb && ((reinterpret_cast<uintptr_t>(S.cells + c0 * (S.d + 1)) & 15) == 0))
-                prefetch_l2(S.cells + c0 * (S.d + 1), cb);
+            prefetch_l2(S.win + c0 * S.ldw, (uint32_t)(nc * S.ldw * sizeof(float)));
+            prefetch_l2(S.cellf + c0 * CELLF, (uint32_t)(nc * CELLF * sizeof(float)));
         };
         prefetch_tile(blockIdx.x);
         for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
             prefetch_tile(t + gridDim.x);
             const TcSeg &S = seg_of<BATCHED>(a, t);
-            const double *__restrict__ s_kappa = S.kappa;
+            const float *__restrict__ s_win = S.win;
+            const int s_ldw = S.ldw;
             const int64_t s_ncells = S.n_cells;
             const int s_nq = S.n_q;
-            if (&S != cur) {
-                // quadrature weights of the new segment
-                named_bar_sync(BAR_BUILDERS, TC_M);
-                for (int i = cl; i < S.n_q; i += TC_M) sm.omega[i] = (float)__ldg(S.weights + i);
-                named_bar_sync(BAR_BUILDERS, TC_M);
-                cur = &S;
-            }
             const int64_t tile_cell0 = (t - S.tile_begin) * TC_M;
             const int64_t cell = tile_cell0 + cl;
-            const bool valid = cell < S.n_cells;
-            float g6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, adet = 0.f;
-            int st = 0;
-            if (valid) {
-                CellGeom geo;
-                st = cell_geometry(S.vertices, S.cells, cell, S.d, geo);
-                if (!st) {
+            const bool valid = cell < s_ncells;
+            // this cell's factors: scaled geometry to the shared row table, unscales
+            float unscale_f[MAX_FORMS] = {1.f, 1.f};
+            {
+                float rec[12];
 #pragma unroll
-                    for (int j = 0; j < 6; ++j) g6[j] = (float)geo.G[j];
-                    adet = (float)geo.absdet;
+                for (int i = 0; i < 3; ++i) {
+                    const float4 v = valid ? __ldg(reinterpret_cast<const float4 *>(S.cellf + cell * CELLF) + i)
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                    rec[4 * i] = v.x;
+                    rec[4 * i + 1] = v.y;
+                    rec[4 * i + 2] = v.z;
+                    rec[4 * i + 3] = v.w;
+                }
+#pragma unroll
+                for (int j = 0; j < 7; ++j) sm.rowc[cl * 8 + j] = rec[CELLF_G + j];
+                if (valid) {
+                    unscale_f[0] = rec[CELLF_UNSCALE];
+                    unscale_f[1] = rec[CELLF_UNSCALE + 1];
                 }
             }
-            if (st) atomicOr(&sm.flags[1], st);
-            // per-cell largest |w_q kappa_cq| (for the narrow-exponent formats); a
-            // tile whose points fit one window loads it here and takes the maximum
-            // from the registers
-            float wmax = 0.f;
+            // a tile whose points fit one window loads it once, here
             int qw_loaded = -1;
             if (CELL_ROWS && s_nq <= KCE) {
-                load_own(s_kappa, s_nq, cell, valid, 0);
+                load_own(s_win, s_ldw, cell, valid, 0);
                 qw_loaded = 0;
-                if (a.target_exp > 1) {
-#pragma unroll
-                    for (int i = 0; i < KCE; ++i) wmax = fmaxf(wmax, fabsf(win[i]));
-                }
-            } else if (a.target_exp > 1) {
-                for (int r = 0; r < 32; ++r) {
-                    const int64_t cell_r = tile_cell0 + wrow0 + r;
-                    float m = 0.f;
-                    if (cell_r < s_ncells)
-                        for (int q = lane; q < s_nq; q += 32)
-                            m = fmaxf(m, fabsf(f64_to_f32_rne(__ldg(s_kappa + cell_r * s_nq + q), nonfinite) * sm.omega[q]));
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                    if (lane == r) wmax = m;
-                }
-            }
-            float unscale_f[MAX_FORMS] = {1.f, 1.f};
-            for (int f = 0; f < MAX_FORMS; ++f) {
-                if (!(S.form_mask & (1 << f))) continue;
-                float gmax = 0.f;
-                if (f == 0) {
-#pragma unroll
-                    for (int j = 0; j < 6; ++j) gmax = fmaxf(gmax, fabsf(g6[j]));
-                } else {
-                    gmax = adet;
-                }
-                int e_c = 0;
-                if (a.target_exp > 1 && valid && !st) {
-                    const float cmax = wmax * gmax;
-                    if (cmax > 0.f && isfinite(cmax)) {
-                        int e;
-                        frexpf(cmax, &e);
-                        e_c = a.target_exp - e;
-                    }
-                }
-                const float scale = ldexpf(1.f, e_c);
-                unscale_f[f] = ldexpf(S.op[f].p_inv_scale, -e_c);
-                if (f == 0) {
-#pragma unroll
-                    for (int j = 0; j < 6; ++j) sm.rowc[cl * 8 + j] = g6[j] * scale;
-                } else {
-                    sm.rowc[cl * 8 + 6] = adet * scale;
-                }
             }
             __syncwarp();
             for (int f = 0; f < MAX_FORMS; ++f) {
@@ -385,7 +278,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         if constexpr (CELL_ROWS) {
                             if (qw != qw_loaded) {
                                 qw_loaded = qw;
-                                load_own(s_kappa, s_nq, cell, valid, qw);
+                                load_own(s_win, s_ldw, cell, valid, qw);
                             }
                             const float gj = sm.rowc[cl * 8 + cidx];
                             uint8_t *rowp = stA + (cl >> 3) * 1024 + (cl & 7) * 128;
@@ -418,7 +311,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                             }
                         } else {
                             float w[32 * QL];
-                            load_rows(s_kappa, s_ncells, s_nq, tile_cell0, qw, w);
+                            load_rows(s_win, s_ldw, s_ncells, tile_cell0, qw, w);
                             const int byte = lane * 4;   // this lane's word inside a 128-byte row
 #pragma unroll
                             for (int r = 0; r < 32; ++r) {
@@ -441,7 +334,6 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 if (*abort_flag) break;
             }
         }
-        if (nonfinite) atomicOr(&sm.flags[1], ST_NONFINITE);
     } else if (warp == W_MMA) {
         // ======================= bulk copies + MMA =======================
         // B cursor: (tile, form, pass, chunk) of the next shared-operand copy;
@@ -681,7 +573,7 @@ size_t tc_smem_bytes(const TcArgs &a) {
     size_t b = 1024;  // alignment slack
     b += bytes_A() + bytes_B(a) + bytes_stage(a);
     b += 2 * TC_M * sizeof(float) + 8 * TC_M * sizeof(float);
-    b += (size_t)((a.nq_max + 3) & ~3) * sizeof(float) + 8;
+    b += 8;
     b += (4 * RING + 9) * sizeof(uint64_t) + 8 + 16;
     return b;
 }
