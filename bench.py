@@ -124,14 +124,16 @@ def algorithmic_bytes(plan, prec):
 
 
 def _traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
-    kernel's source is unchanged since the capture (else None)."""
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.json), if the kernel's sources are unchanged since the
+    capture (else None)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(path))[kernel]
-        src = os.path.join(ROOT, "paper_2410_12614_gb300", "csrc", rec["source"])
-        if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["sha256"]:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_2410_12614_gb300", "csrc", f), "rb").read())
+        if h.hexdigest() != rec["sha256"]:
             return None
         return rec["dram_bytes_per_launch"]
     except (OSError, KeyError, ValueError):

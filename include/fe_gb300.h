@@ -172,7 +172,13 @@ fe_status fe_cell_dofs(const fe_plan *plan, int32_t *cell_dofs);
  * vertices: device [n_vertices][d] FP64, or NULL for the plan's copy.
  * kappa: device [n_cells][n_q] FP64, the coefficient at the quadrature points.
  * A_stiffness / A_mass: device [n_cells][n_phi][n_phi], double for
- * FE_PREC_FP64 else float; the pointer of a form not in `forms` is ignored. */
+ * FE_PREC_FP64 else float; the pointer of a form not in `forms` is ignored.
+ * The reduced-precision paths run two kernels: a factor kernel (geometry,
+ * the coefficient window w_q kappa_cq in FP32 and the per-cell scales, into
+ * a plan workspace of 4 * (n_q rounded up to 4) + 64 bytes per cell, allocated
+ * on first use) and the tensor-core kernel.  Asynchronous on the plan's
+ * stream; device status (degenerate or non-finite cells, timeouts) is read
+ * by fe_sync_status. */
 fe_status fe_element_matrices(fe_plan *plan, unsigned forms, fe_precision prec, const double *vertices,
                               const double *kappa, void *A_stiffness, void *A_mass);
 
@@ -239,10 +245,10 @@ fe_status fe_adjoint_noalloc(fe_plan *plan, const double *vertices, const double
 /* Batches                                                                 */
 /* ---------------------------------------------------------------------- */
 
-/* A batch of plans run as one persistent tensor-core launch (the cell
- * batching of Sec. 3.1, generalised to meshes of uneven size,
- * cell type and degree) followed by one assembly launch over the rows of
- * every plan, captured once in a CUDA graph and replayed by fe_batch_run.
+/* A batch of plans run as one factor launch and one persistent tensor-core
+ * launch (the cell batching of Sec. 3.1, generalised to meshes of uneven
+ * size, cell type and degree) followed by one assembly launch over the rows
+ * of every plan, captured once in a CUDA graph and replayed by fe_batch_run.
  * Each plan's tile shape (N-pass width) is the one its autotuner chose.
  * plans: n_plans plans on the current device, each serving `forms` and
  * `prec` (FE_PREC_FP64 runs the FP64 kernels, one per plan and form, inside

@@ -16,16 +16,18 @@
 // operand element in the element kernel, rounded once to the storage format
 // (the mixed strategy of Sec. 4.5 with u_s on C).
 //
-// Each CTA owns one tile: its four warps stream the tile's kappa block (a
-// contiguous range) with coalesced loads, so the factor work runs at full
-// occupancy instead of on the element kernel's four builder warps.
+// Each CTA owns half a tile (64 cells): its four warps stream that part of
+// the kappa block (a contiguous range) with coalesced loads, so the factor
+// work runs at full occupancy instead of on the element kernel's four
+// builder warps.
 #include "fe_device.cuh"
 
 namespace fe {
 
 namespace {
 
-constexpr int F_THREADS = 128;   // one thread per cell of the tile
+constexpr int F_THREADS = 128;
+constexpr int F_CELLS = 64;      // cells per CTA (half a tile): enough CTAs to hide the load latency
 constexpr int F_WTS = 1024;   // weights table in shared memory (points)
 
 template <bool BATCHED>
@@ -40,21 +42,22 @@ __device__ __forceinline__ const TcSeg &fseg_of(const TcArgs &a, int64_t t) {
 }
 
 template <bool BATCHED, bool G64>
-__global__ void __launch_bounds__(F_THREADS) factor_kernel(const __grid_constant__ TcArgs a) {
-    __shared__ int rowmax[TC_M];          // max_q |w_q kappa_cq| of each row, as non-negative float bits
+__global__ void __launch_bounds__(F_THREADS, 8) factor_kernel(const __grid_constant__ TcArgs a) {
+    __shared__ int rowmax[F_CELLS];       // max_q |w_q kappa_cq| of each row, as non-negative float bits
     __shared__ float wts[F_WTS];          // the segment's weights in FP32 (when they fit)
     __shared__ int flags;
     const int tid = threadIdx.x;
-    const int64_t t = blockIdx.x;
+    const int64_t t = blockIdx.x / (TC_M / F_CELLS);
     const TcSeg &S = fseg_of<BATCHED>(a, t);
-    const int64_t c0 = (t - S.tile_begin) * TC_M;
-    const int nvalid = (int)((S.n_cells - c0) < TC_M ? (S.n_cells - c0) : TC_M);
+    const int64_t c0 = (t - S.tile_begin) * TC_M + (blockIdx.x % (TC_M / F_CELLS)) * F_CELLS;
+    const int64_t left = S.n_cells - c0;
+    const int nvalid = (int)(left < F_CELLS ? (left > 0 ? left : 0) : F_CELLS);
     const int n_q = S.n_q, ldw = S.ldw;
     const double *__restrict__ kb = S.kappa + c0 * n_q;   // the tile's kappa block
     const double *__restrict__ weights = S.weights;
     float *__restrict__ wb = S.win + c0 * ldw;             // the tile's window block
     const bool wts_smem = ldw <= F_WTS;
-    if (tid < TC_M) rowmax[tid] = 0;
+    if (tid < F_CELLS) rowmax[tid] = 0;
     if (tid == 0) flags = 0;
     if (wts_smem)
         for (int q = tid; q < ldw; q += F_THREADS) wts[q] = q < n_q ? (float)__ldg(weights + q) : 0.f;
@@ -217,12 +220,13 @@ __global__ void __launch_bounds__(F_THREADS) factor_kernel(const __grid_constant
 int launch_factor(const TcArgs &a, cudaStream_t s) {
     if (a.n_tiles <= 0) return 0;
     const bool g64 = a.prec == FE_PREC_TF32X3;
+    const unsigned grid = (unsigned)(a.n_tiles * (TC_M / F_CELLS));
     if (a.segs) {
-        if (g64) factor_kernel<true, true><<<(unsigned)a.n_tiles, F_THREADS, 0, s>>>(a);
-        else factor_kernel<true, false><<<(unsigned)a.n_tiles, F_THREADS, 0, s>>>(a);
+        if (g64) factor_kernel<true, true><<<grid, F_THREADS, 0, s>>>(a);
+        else factor_kernel<true, false><<<grid, F_THREADS, 0, s>>>(a);
     } else {
-        if (g64) factor_kernel<false, true><<<(unsigned)a.n_tiles, F_THREADS, 0, s>>>(a);
-        else factor_kernel<false, false><<<(unsigned)a.n_tiles, F_THREADS, 0, s>>>(a);
+        if (g64) factor_kernel<false, true><<<grid, F_THREADS, 0, s>>>(a);
+        else factor_kernel<false, false><<<grid, F_THREADS, 0, s>>>(a);
     }
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? 1 : -(int)e;

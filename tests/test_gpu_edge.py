@@ -1,0 +1,89 @@
+"""GPU edge cases of the assembly chunking and of the factor kernel's geometry.
+
+* A fan of 200 P5 triangles around one vertex: that vertex's CSR row sums
+  200 * 21 = 4200 element entries, above the 4096-entry assembly chunk, so it
+  is summed on the per-row fallback path; its neighbours' rows exercise the
+  256-incidence chunk limit.
+* Tetrahedra so small (or so large) that det J leaves FP32's normal range:
+  the factor kernel must fall back to forming G in FP64.
+The oracle decides in every case (FP64 to 1e-12; reduced precision within the
+per-cell bound of Corollary 4.10 and the CSR bound of Corollary 4.11).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_12614_gb300 import api, inputs
+
+from gpu_util import FP64_TOL, cell_bounds, cell_errors, csr_bound, cuda, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def fan_mesh(n_tri, radius=1.0):
+    ang = 2 * np.pi * np.arange(n_tri) / n_tri
+    v = np.vstack([[0.0, 0.0], np.c_[radius * np.cos(ang), radius * np.sin(ang)]])
+    c = np.array([[0, 1 + i, 1 + (i + 1) % n_tri] for i in range(n_tri)], dtype=np.int32)
+    return v, c
+
+
+def _plan_and_ref(cell, v, c, p, precisions):
+    pts, w = api.quadrature_rule(cell, p + 1)
+    plan = api.Plan(cell, v, c, p, pts, w, precisions=precisions)
+    ref = oracle.Problem(v, c, p, *oracle.rule_for_degree(cell, p))
+    return plan, ref
+
+
+def test_fan_row_above_chunk_limit():
+    v, c = fan_mesh(200)
+    p = 5
+    plan, ref = _plan_and_ref("triangle", v, c, p, ("bf16",))
+    dofs, _ = ref.cell_dofs()
+    # the centre vertex's row really is above the chunk limit
+    assert 200 * ref.n_phi > 4096 and np.bincount(dofs.reshape(-1)).max() == 200
+    kap = inputs.lognormal_kappa(plan.n_cells, plan.n_q, 5)
+    kd = cuda(kap)
+    rp, ci = plan.csr_pattern()
+    orp, oci = ref.csr_pattern()
+    assert np.array_equal(rp.cpu().numpy(), orp) and np.array_equal(ci.cpu().numpy(), oci)
+    for form in ("stiffness", "mass"):
+        A = ref.element_matrices(kap, form)
+        g_exact = ref.assemble(A)
+        for prec in ("fp64", "bf16"):
+            els = plan.element_matrices(kd, forms=(form,), prec=prec)
+            vals = plan.assemble(kd, forms=(form,), prec=prec)
+            plan.sync()
+            got, gv = to_np(els[form]), to_np(vals[form])
+            if prec == "fp64":
+                assert cell_errors(got, A).max() <= FP64_TOL
+                assert np.abs(gv - g_exact).max() <= FP64_TOL * np.abs(g_exact).max()
+            else:
+                bnd = cell_bounds(ref, kap, form, prec, A)
+                assert np.all(cell_errors(got, A) <= bnd)
+                assert np.all(np.abs(gv - g_exact) <= csr_bound(ref, A, bnd))
+            # the GPU's assembly of its own element matrices, entry by entry, in
+            # particular on the long row
+            own = ref.assemble(got)
+            centre = slice(int(orp[0]), int(orp[1]))
+            assert np.abs(gv - own).max() <= (1e-13 if prec == "fp64" else 1e-5) * np.abs(g_exact).max()
+            assert np.abs(gv[centre] - own[centre]).max() <= (1e-13 if prec == "fp64" else 1e-5) * np.abs(own).max()
+
+
+@pytest.mark.parametrize("scale", [1e-13, 1e13])
+def test_geometry_outside_fp32_range(scale):
+    # |det J| ~ (scale/2)^3: below FP32's smallest normal number (1e-13) or
+    # above its largest (1e13); the stiffness matrices scale like h and stay
+    # representable, the mass matrices (~h^3) do not and are not checked.
+    v, c = inputs.structured_mesh("tetrahedron", 2, 0.15, 21)
+    v = v * scale
+    p = 2
+    plan, ref = _plan_and_ref("tetrahedron", v, c, p, ("bf16", "fp16", "tf32x3"))
+    kap = inputs.lognormal_kappa(plan.n_cells, plan.n_q, 22)
+    kd = cuda(kap)
+    A = ref.element_matrices(kap, "stiffness")
+    for prec in ("bf16", "fp16", "tf32x3"):
+        got = to_np(plan.element_matrices(kd, forms=("stiffness",), prec=prec)["stiffness"])
+        plan.sync()
+        bnd = cell_bounds(ref, kap, "stiffness", prec, A)
+        err = cell_errors(got, A)
+        assert np.all(err <= bnd), (prec, float(err.max()))
