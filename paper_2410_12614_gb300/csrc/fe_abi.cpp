@@ -96,6 +96,7 @@ struct fe_plan {
     int stage_marks = 0;
     std::vector<int> host_status;
     std::vector<double> h_phi, h_dphi;   // FP64 tabulation kept for re-packing operands
+    std::vector<int> col_of_sym;         // operand column of each pair (k <= l)
     int tuned_np[6][2] = {};             // autotuned N-pass width per precision and form
     ~fe_plan() {
         for (auto &e : ev)
@@ -272,13 +273,20 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
     FE_CUDA(upload(P.vinc, pat.vinc, s), "upload vinc");
     FE_CUDA(upload(P.phi, phi, s), "upload phi");
     FE_CUDA(upload(P.dphi, dphi, s), "upload dphi");
-    std::vector<int32_t> symkl;
+    // operand column of every pair (k <= l): a bank-conflict-free order for the
+    // staged epilogue's gathers; sym_kl maps a column back to its pair (-1: padding)
+    P.col_of_sym = host::stage_columns(P.n_phi, (P.n_phi * P.n_phi) % 4 == 0);
+    std::vector<int32_t> symkl((size_t)(P.n_sym + 15) / 16 * 16, -1);
     std::vector<int16_t> f2s((size_t)P.n_phi * P.n_phi);
-    for (int k = 0; k < P.n_phi; ++k)
-        for (int l = k; l < P.n_phi; ++l) {
-            f2s[(size_t)k * P.n_phi + l] = f2s[(size_t)l * P.n_phi + k] = (int16_t)symkl.size();
-            symkl.push_back(k | (l << 16));
-        }
+    {
+        int pr = 0;
+        for (int k = 0; k < P.n_phi; ++k)
+            for (int l = k; l < P.n_phi; ++l, ++pr) {
+                const int col = P.col_of_sym[pr];
+                f2s[(size_t)k * P.n_phi + l] = f2s[(size_t)l * P.n_phi + k] = (int16_t)col;
+                symkl[col] = k | (l << 16);
+            }
+    }
     if (P.n_sym > 32767) f2s.assign(f2s.size(), 0);  // only used by single-pass shapes (n_sym <= 256)
     FE_CUDA(upload(P.sym_kl, symkl, s), "upload sym table");
     FE_CUDA(upload(P.full2sym, f2s, s), "upload sym map");
@@ -584,7 +592,7 @@ static fe_status run_assembly(fe_plan *P, unsigned forms, bool fp64, const void 
 static fe_status pack_operand(fe_plan &P, int prec, int fi, int np_pass) {
     host::OperandImage img;
     const unsigned form = fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS;
-    host::build_operand(prec, (int)form, P.d, P.n_phi, P.n_q, P.h_phi, P.h_dphi, img, np_pass);
+    host::build_operand(prec, (int)form, P.d, P.n_phi, P.n_q, P.h_phi, P.h_dphi, img, np_pass, P.col_of_sym);
     FE_CUDA(upload(P.img[prec][fi], img.bytes, P.stream), "upload operand image");
     TcOperand &o = P.op[prec][fi];
     o.img = P.img[prec][fi].as<uint8_t>();

@@ -19,6 +19,7 @@
 #include "fe_host.h"
 
 #include <algorithm>
+#include <climits>
 #include <array>
 #include <atomic>
 #include <cmath>
@@ -576,8 +577,95 @@ std::vector<int> np_candidates(int n_sym) {
     return out;
 }
 
+std::vector<int> stage_columns(int n_phi_, bool v4, int *conflicts) {
+    const int n_sym = n_phi_ * (n_phi_ + 1) / 2;
+    std::vector<int> col(n_sym);
+    for (int i = 0; i < n_sym; ++i) col[i] = i;
+    if (conflicts) *conflicts = -1;
+    if (n_sym > 256) return col;
+    const int ncol = (n_sym + 15) / 16 * 16;
+    // pair index of (k, l), k <= l, in row order
+    auto pair_of = [&](int k, int l) {
+        if (k > l) std::swap(k, l);
+        return k * n_phi_ - k * (k - 1) / 2 + (l - k);
+    };
+    // groups of each pair (one or two output positions)
+    const int npos = n_phi_ * n_phi_;
+    const int ngroups = v4 ? ((npos + 127) / 128) * 4 : (npos + 31) / 32;
+    std::vector<std::vector<int>> members(ngroups);
+    std::vector<std::array<int, 2>> groups_of(n_sym, {-1, -1});
+    for (int pos = 0; pos < npos; ++pos) {
+        const int g = v4 ? (pos / 128) * 4 + (pos & 3) : pos / 32;
+        const int pr = pair_of(pos / n_phi_, pos % n_phi_);
+        bool seen = false;
+        for (int m : members[g]) seen = seen || (m == pr);
+        if (!seen) members[g].push_back(pr);
+        if (groups_of[pr][0] < 0) groups_of[pr][0] = g;
+        else if (groups_of[pr][0] != g) groups_of[pr][1] = g;
+    }
+    std::vector<int> cap(32);
+    for (int r = 0; r < 32; ++r) cap[r] = (ncol - r + 31) / 32;
+    std::vector<int> best_colour(n_sym, 0);
+    int best = INT32_MAX;
+    uint64_t rng = 0x9E3779B97F4A7C15ull;
+    auto next = [&]() {
+        rng ^= rng << 13;
+        rng ^= rng >> 7;
+        rng ^= rng << 17;
+        return rng;
+    };
+    std::vector<int> order(n_sym), colour(n_sym), left(32);
+    std::vector<std::array<int, 32>> used(ngroups);
+    for (int attempt = 0; attempt < 400 && best > 0; ++attempt) {
+        for (int i = 0; i < n_sym; ++i) order[i] = i;
+        // pairs in two groups first, random order within
+        for (int i = n_sym - 1; i > 0; --i) std::swap(order[i], order[next() % (uint64_t)(i + 1)]);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return (groups_of[a][1] >= 0) > (groups_of[b][1] >= 0); });
+        for (auto &u : used) u.fill(0);
+        left = cap;
+        for (int pr : order) {
+            int pick = -1, pick_cost = INT32_MAX, pick_left = -1;
+            const int r0 = (int)(next() & 31);
+            for (int t = 0; t < 32; ++t) {
+                const int r = (r0 + t) & 31;
+                if (left[r] == 0) continue;
+                int cost = 0;
+                for (int g : groups_of[pr])
+                    if (g >= 0) cost += used[g][r];
+                if (cost < pick_cost || (cost == pick_cost && left[r] > pick_left)) {
+                    pick = r;
+                    pick_cost = cost;
+                    pick_left = left[r];
+                }
+            }
+            colour[pr] = pick;
+            --left[pick];
+            for (int g : groups_of[pr])
+                if (g >= 0) ++used[g][pick];
+        }
+        int excess = 0;
+        for (int g = 0; g < ngroups; ++g)
+            for (int r = 0; r < 32; ++r) excess += std::max(0, used[g][r] - 1);
+        if (excess < best) {
+            best = excess;
+            best_colour = colour;
+        }
+    }
+    // the pairs of colour r take columns r, r + 32, r + 64, ... in pair order
+    std::vector<int> next_slot(32);
+    for (int r = 0; r < 32; ++r) next_slot[r] = r;
+    for (int pr = 0; pr < n_sym; ++pr) {
+        col[pr] = next_slot[best_colour[pr]];
+        next_slot[best_colour[pr]] += 32;
+    }
+    if (conflicts) *conflicts = best;
+    return col;
+}
+
 void build_operand(int prec, int form, int d, int n_phi_, int n_q, const std::vector<double> &phi,
-                   const std::vector<double> &dphi, OperandImage &img, int np_pass) {
+                   const std::vector<double> &dphi, OperandImage &img, int np_pass,
+                   const std::vector<int> &col_of_sym) {
     const Format F = format_of(prec);
     const int eb = F.elem_bytes;
     const int KCE = 128 / eb;
@@ -642,6 +730,13 @@ void build_operand(int prec, int form, int d, int n_phi_, int n_q, const std::ve
         for (size_t i = 0; i < Pv.size(); ++i) lo[i] = round_to_format(std::ldexp(Pv[i], eP) - hi[i], F.mbits, F.emin, F.maxfinite);
     }
     (void)K_true;
+    // pair at each operand column (-1: padding)
+    std::vector<int> pair_at((size_t)img.n_pass * img.NP, -1);
+    for (int c = 0; c < n_sym; ++c) {
+        const int colc = col_of_sym.empty() ? c : col_of_sym[c];
+        if (colc >= 0 && colc < (int)pair_at.size()) pair_at[colc] = c;
+    }
+    if (!col_of_sym.empty()) img.n_cols = std::min<int>((int)pair_at.size(), (n_sym + 15) / 16 * 16);
     const size_t block = (size_t)img.NP * 128;
     img.bytes.assign(block * img.n_kchunks * img.n_pass, 0);
     for (int n = 0; n < img.n_pass; ++n)
@@ -651,13 +746,14 @@ void build_operand(int prec, int form, int d, int n_phi_, int n_q, const std::ve
             const int blk = ch % img.n_blk;
             uint8_t *base = img.bytes.data() + ((size_t)n * img.n_kchunks + ch) * block;
             for (int r = 0; r < img.NP; ++r) {
-                int col = n * img.NP + r;
+                const int col = n * img.NP + r;
+                const int pr = pair_at[col];
                 for (int e = 0; e < KCE; ++e) {
                     const int q = qw * KCE + e;
                     double v = 0.0;
-                    if (col < n_sym && q < n_q) {
+                    if (pr >= 0 && q < n_q) {
                         const std::vector<double> &src = (blk == 1) ? lo : hi;  // C_hi P_hi, C_hi P_lo, C_lo P_hi
-                        v = src[(size_t)(q * n_pairs + j) * n_sym + col];
+                        v = src[(size_t)(q * n_pairs + j) * n_sym + pr];
                     }
                     uint32_t bits = encode(prec, v);
                     int byte = e * eb;

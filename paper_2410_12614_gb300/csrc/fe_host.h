@@ -82,9 +82,22 @@ struct OperandImage {
     double p_inv_scale = 1.0;
 };
 // np_pass: N columns per pass (multiple of 16 in 16..256), or 0 for the
-// default (one pass if n_sym <= 256, else passes of 256).
+// default (one pass if n_sym <= 256, else passes of 256).  col_of_sym: the
+// operand column of each symmetric pair (k <= l) in [0, n_pass * NP), or
+// empty for column = pair index.
 void build_operand(int prec, int form, int d, int n_phi, int n_q, const std::vector<double> &phi,
-                   const std::vector<double> &dphi, OperandImage &img, int np_pass = 0);
+                   const std::vector<double> &dphi, OperandImage &img, int np_pass = 0,
+                   const std::vector<int> &col_of_sym = {});
+
+// Operand columns of the symmetric pairs (k <= l, in row order) for the staged
+// epilogue: a column's staged value sits in shared-memory bank (column mod 32),
+// and one gather instruction of the epilogue reads the 32 output positions of a
+// group (v4: positions 128 it + 4 j + e, j = 0..31, for fixed it and e; else 32
+// consecutive positions).  The pairs of a group get distinct banks where the
+// greedy colouring (with restarts) finds it; columns stay below
+// 16 * ceil(n_sym / 16).  Identity for n_sym > 256 (multi-pass shapes).
+// conflicts (optional): the remaining excess over one per bank, summed over groups.
+std::vector<int> stage_columns(int n_phi, bool v4, int *conflicts = nullptr);
 // Candidate pass widths for the autotuner: the default and the narrowest
 // widths that keep the minimal number of passes (least column padding).
 std::vector<int> np_candidates(int n_sym);

@@ -37,7 +37,7 @@ struct TcOperand {
     int n_pairs = 1;               // symmetric (s,t) pairs (stiffness) or 1 (mass)
     int n_pass = 0;                // N passes
     int NP = 0;                    // N per pass (multiple of 16, <= 256)
-    int n_cols = 0;                // valid sym columns (n_sym)
+    int n_cols = 0;                // operand columns that may carry a pair (sym_kl entries)
     int n_blk = 1;                 // 1, or 3 for split TF32 (head, head, tail)
     float p_inv_scale = 1.f;       // 2^-e_P
 };
@@ -56,8 +56,8 @@ struct TcSeg {
     int form_mask;    // bit 0 stiffness, bit 1 mass (internal order)
     TcOperand op[MAX_FORMS];
     float *out[MAX_FORMS];
-    const int32_t *sym_kl;     // [n_sym] k | l << 16
-    const int16_t *full2sym;   // [n_phi * n_phi]
+    const int32_t *sym_kl;     // [operand column] k | l << 16, -1 for padding columns
+    const int16_t *full2sym;   // [n_phi * n_phi] operand column of entry (k, l)
     int staged;                // 1: staged coalesced epilogue (single pass)
     int64_t tile_begin;        // first global tile of this segment
     // written by the factor kernel, read by the element kernel

@@ -539,8 +539,8 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
 #pragma unroll
                                 for (int i = 0; i < 32; ++i) {
                                     const int col = n * op.NP + c0 + i;
-                                    if (c0 + i < op.NP && col < op.n_cols) {
-                                        const int32_t kl = __ldg(s_symkl + col);
+                                    const int32_t kl = (c0 + i < op.NP && col < op.n_cols) ? __ldg(s_symkl + col) : -1;
+                                    if (kl >= 0) {   // (padding columns carry no pair)
                                         const int k = kl & 0xFFFF, l = kl >> 16;
                                         const float v = __uint_as_float(r[i]) * us;
                                         __stcs(dst + k * nph + l, v);
