@@ -290,6 +290,8 @@ def run_ours(args, rank, world):
     }
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args, plan, kap_h, els, v, c)
+    if rank == 0 and args.with_batch:
+        result["batched_256_meshes"] = run_batch(args)
     return result
 
 
@@ -355,6 +357,63 @@ def cpu_baseline(args, plan=None, kap=None, gpu_els=None, v=None, c=None, budget
                        "bound_at_worst_cell": float(bnd[np.argmax(e)]), "within_bound": bool(np.all(e <= bnd))}
         out["bf16_accuracy_on_sample"] = errs
     return out
+
+
+def run_batch(args):
+    """The 256-mesh uneven batch (triangles p = 1..6, tetrahedra p = 1..5, cell
+    counts log-uniform in 1e3..2e5, seed 6): one graph replay of fe_batch_run =
+    factor + persistent element launch over every mesh's tiles + one assembly
+    launch over every mesh's rows, BF16.  Reports element matrices/s (both
+    forms), nnz/s and the achieved fraction of the per-mesh roofline
+    sum_m max(bytes_m / HBM, flops_m / BF16 peak)."""
+    import torch
+    from paper_2410_12614_gb300 import api, inputs
+    stream = torch.cuda.Stream()
+    plans, kaps = [], []
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i, x in enumerate(inputs.batched_workload()):
+            v, c = inputs.structured_mesh(x["cell_type"], x["n"], x["alpha"], x["seed"])
+            pts, w = api.quadrature_rule(x["cell_type"], x["degree"] + 1)
+            plan = api.Plan(x["cell_type"], v, c, x["degree"], pts, w, precisions=("bf16",), stream=stream)
+            plans.append(plan)
+            kaps.append(torch.from_numpy(inputs.lognormal_kappa(plan.n_cells, plan.n_q, 500 + i)).cuda())
+        setup_s = time.perf_counter() - t0
+        batch = api.Batch(plans, kaps, prec="bf16", stream=stream)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        sink = torch.empty((), dtype=torch.float32, device="cuda")
+        for _ in range(2):
+            batch.run()
+        batch.sync()
+        times = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.fill_(1.0)
+            sink.copy_(flush.sum())
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.run()
+            e1.record(stream)
+            stream.synchronize()
+            times.append(e0.elapsed_time(e1))
+        batch.sync()
+    ms = statistics.median(times)
+    hbm, _ = _peaks()
+    peak_tf = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+    ideal = 0.0
+    n_cells = nnz = 0
+    for p in plans:
+        fb, eb, ab = algorithmic_bytes(p, "bf16")
+        n_sym = p.n_phi * (p.n_phi + 1) // 2
+        pairs = p.d * (p.d + 1) // 2
+        flops = 2.0 * p.n_cells * p.n_q * (pairs + 1) * n_sym
+        ideal += max((fb + eb + ab) / (hbm * 1e9), flops / (peak_tf * 1e12))
+        n_cells += p.n_cells
+        nnz += p.nnz
+    return {"meshes": len(plans), "cells": n_cells, "nnz_per_matrix": nnz, "ms_per_run": ms,
+            "element_matrices_per_s": 2 * n_cells / (ms / 1e3), "nnz_per_s": 2 * nnz / (ms / 1e3),
+            "ideal_ms": ideal * 1e3, "frac_of_roofline": ideal * 1e3 / ms, "launches": batch.launches,
+            "plan_setup_s": setup_s}
 
 
 _POOL_STATE = {}
@@ -436,6 +495,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--with-batch", action="store_true",
+                    help="also time the 256-mesh uneven batch (adds about a minute of plan set-up)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -603,8 +603,9 @@ static fe_status pack_operand(fe_plan &P, int prec, int fi, int np_pass) {
     o.NP = img.NP;
     o.n_cols = img.n_cols;
     o.n_blk = img.n_blk;
+    o.rows_per_pass = img.rows_per_pass;
     o.p_inv_scale = (float)img.p_inv_scale;
-    P.tuned_np[prec][fi] = img.NP;
+    P.tuned_np[prec][fi] = img.rows_per_pass > 0 ? -img.rows_per_pass : img.NP;
     return FE_OK;
 }
 
@@ -631,7 +632,7 @@ static fe_status autotune_plan(fe_plan &P) {
         for (int fi = 0; fi < 2; ++fi) {
             const unsigned form = fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS;
             if (!(P.form_mask & form)) continue;
-            std::vector<int> cand = host::np_candidates(P.n_sym);
+            std::vector<int> cand = host::np_candidates(P.n_phi);
             if (cand.size() < 2) continue;
             char key[96];
             snprintf(key, sizeof(key), "%d,%d,%d,%d,%d", P.d, P.p, P.n_q, prec, fi);
@@ -695,7 +696,7 @@ static fe_status autotune_plan(fe_plan &P) {
                 std::lock_guard<std::mutex> lock(g_tune_mutex);
                 g_tune_cache[key] = best;
             }
-            if (P.op[prec][fi].NP != best) {
+            if (P.tuned_np[prec][fi] != best) {
                 fe_status st = pack_operand(P, prec, fi, best);
                 if (st) return st;
             }

@@ -560,12 +560,23 @@ uint32_t encode(int prec, double r) {
     return (sign << 7) | ((uint32_t)(E + 7) << 3) | mant;
 }
 
-std::vector<int> np_candidates(int n_sym) {
+int row_block_rows(int n_phi_) { return std::max(1, 240 / n_phi_); }
+
+bool row_block_default(int n_phi_) {
+    const int n_sym = n_phi_ * (n_phi_ + 1) / 2;
+    if (n_sym <= 256) return false;
+    const int R = row_block_rows(n_phi_);
+    return (n_phi_ + R - 1) / R <= 2 * ((n_sym + 255) / 256);
+}
+
+std::vector<int> np_candidates(int n_phi_) {
+    const int n_sym = n_phi_ * (n_phi_ + 1) / 2;
     std::vector<int> out;
     if (n_sym <= 256) {
         out.push_back((n_sym + 15) / 16 * 16);
         return out;
     }
+    out.push_back(-row_block_rows(n_phi_));
     const int passes = (n_sym + 255) / 256;
     out.push_back(256);
     // the narrowest multiple of 16 with the same number of passes
@@ -712,7 +723,14 @@ void build_operand(int prec, int form, int d, int n_phi_, int n_q, const std::ve
     img.n_qw = (n_q + KCE - 1) / KCE;
     img.n_kchunks = img.n_qw * n_pairs * img.n_blk;
     img.n_cols = n_sym;
-    if (np_pass >= 16 && np_pass <= 256 && np_pass % 16 == 0) {
+    if (np_pass == 0 && row_block_default(n_phi_)) np_pass = -row_block_rows(n_phi_);
+    if (np_pass < 0) {
+        const int R = std::min(-np_pass, n_phi_);
+        img.rows_per_pass = R;
+        img.NP = (R * n_phi_ + 15) / 16 * 16;
+        img.n_pass = (n_phi_ + R - 1) / R;
+        img.n_cols = img.n_pass * img.NP;
+    } else if (np_pass >= 16 && np_pass <= 256 && np_pass % 16 == 0) {
         img.NP = np_pass;
         img.n_pass = (n_sym + np_pass - 1) / np_pass;
     } else if (n_sym <= 256) {
@@ -732,11 +750,23 @@ void build_operand(int prec, int form, int d, int n_phi_, int n_q, const std::ve
     (void)K_true;
     // pair at each operand column (-1: padding)
     std::vector<int> pair_at((size_t)img.n_pass * img.NP, -1);
-    for (int c = 0; c < n_sym; ++c) {
-        const int colc = col_of_sym.empty() ? c : col_of_sym[c];
-        if (colc >= 0 && colc < (int)pair_at.size()) pair_at[colc] = c;
+    if (img.rows_per_pass > 0) {
+        // pass n: rows k = n R .. n R + R - 1, column (k - n R) n_phi + l
+        const int R = img.rows_per_pass;
+        for (int n = 0; n < img.n_pass; ++n)
+            for (int r = 0; r < R * n_phi_; ++r) {
+                const int k = n * R + r / n_phi_, l = r % n_phi_;
+                if (k >= n_phi_) continue;
+                const int a = std::min(k, l), b = std::max(k, l);
+                pair_at[(size_t)n * img.NP + r] = a * n_phi_ - a * (a - 1) / 2 + (b - a);
+            }
+    } else {
+        for (int c = 0; c < n_sym; ++c) {
+            const int colc = col_of_sym.empty() ? c : col_of_sym[c];
+            if (colc >= 0 && colc < (int)pair_at.size()) pair_at[colc] = c;
+        }
+        if (!col_of_sym.empty()) img.n_cols = std::min<int>((int)pair_at.size(), (n_sym + 15) / 16 * 16);
     }
-    if (!col_of_sym.empty()) img.n_cols = std::min<int>((int)pair_at.size(), (n_sym + 15) / 16 * 16);
     const size_t block = (size_t)img.NP * 128;
     img.bytes.assign(block * img.n_kchunks * img.n_pass, 0);
     for (int n = 0; n < img.n_pass; ++n)

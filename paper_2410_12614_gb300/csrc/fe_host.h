@@ -79,12 +79,15 @@ uint32_t encode(int prec, double r);
 struct OperandImage {
     std::vector<uint8_t> bytes;
     int n_kchunks = 0, n_qw = 0, n_pairs = 1, n_pass = 0, NP = 0, n_cols = 0, n_blk = 1;
+    int rows_per_pass = 0;   // 0: symmetric-pair columns; R > 0: each pass holds R full rows (k, every l)
     double p_inv_scale = 1.0;
 };
-// np_pass: N columns per pass (multiple of 16 in 16..256), or 0 for the
-// default (one pass if n_sym <= 256, else passes of 256).  col_of_sym: the
-// operand column of each symmetric pair (k <= l) in [0, n_pass * NP), or
-// empty for column = pair index.
+// np_pass: N columns per pass (multiple of 16 in 16..256) of the symmetric-
+// pair layout, 0 for the default layout (pairs in one pass if n_sym <= 256;
+// else full-row passes when row_block_default says so, pair passes of 256
+// otherwise), or -R for the full-row layout with R rows per pass.
+// col_of_sym: the operand column of each symmetric pair (k <= l) in the pair
+// layout, or empty for column = pair index.
 void build_operand(int prec, int form, int d, int n_phi, int n_q, const std::vector<double> &phi,
                    const std::vector<double> &dphi, OperandImage &img, int np_pass = 0,
                    const std::vector<int> &col_of_sym = {});
@@ -98,9 +101,15 @@ void build_operand(int prec, int form, int d, int n_phi, int n_q, const std::vec
 // 16 * ceil(n_sym / 16).  Identity for n_sym > 256 (multi-pass shapes).
 // conflicts (optional): the remaining excess over one per bank, summed over groups.
 std::vector<int> stage_columns(int n_phi, bool v4, int *conflicts = nullptr);
-// Candidate pass widths for the autotuner: the default and the narrowest
-// widths that keep the minimal number of passes (least column padding).
-std::vector<int> np_candidates(int n_sym);
+// Candidate layouts for the autotuner (np_pass values as above): the pair
+// layout's default width and the narrowest widths that keep the minimal number
+// of passes, and for n_sym > 256 the full-row layout.
+std::vector<int> np_candidates(int n_phi);
+// Rows per pass of the full-row layout (R * n_phi <= 240 columns), and whether
+// it is the default for shapes whose pairs need several passes (at most twice
+// the passes of the pair layout).
+int row_block_rows(int n_phi);
+bool row_block_default(int n_phi);
 
 unsigned hardware_threads();
 

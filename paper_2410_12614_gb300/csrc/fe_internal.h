@@ -39,6 +39,7 @@ struct TcOperand {
     int NP = 0;                    // N per pass (multiple of 16, <= 256)
     int n_cols = 0;                // operand columns that may carry a pair (sym_kl entries)
     int n_blk = 1;                 // 1, or 3 for split TF32 (head, head, tail)
+    int rows_per_pass = 0;         // 0: columns are symmetric pairs; R: pass n holds rows nR..nR+R-1 (all l)
     float p_inv_scale = 1.f;       // 2^-e_P
 };
 

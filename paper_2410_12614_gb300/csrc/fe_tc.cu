@@ -29,9 +29,12 @@
 //              128-byte swizzled K-major row of C written into a 2-stage ring
 //              (one a_full arrival per warp).
 //   warps 4-11 epilogue, two warps per TMEM lane group: drain a finished
-//              accumulator into a conflict-free sym-packed staging area,
-//              release it, and write whole row-major element matrices with
-//              coalesced stores (mirroring k <= l to k > l).
+//              accumulator into a conflict-free staging area, release it, and
+//              write row-major element matrices with coalesced stores: whole
+//              matrices gathered from the pair columns (mirroring k <= l to
+//              k > l; the columns are ordered so that these gathers hit
+//              distinct banks), or, for the full-row layout of large
+//              elements, each pass's rows as one contiguous run.
 //   warp 12    bulk copies of the pre-swizzled P chunks into a 2-stage ring
 //              (one 1-D copy per chunk, no multicast) and tcgen05.mma into
 //              one of two 256-column FP32 TMEM accumulators (lane 0 issues).
@@ -490,7 +493,29 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         if (lane == 0) mbar_arrive(&sm.acc_empty[b]);
                         named_bar_sync(1 + g, 64);
                         // whole row-major matrices of 16 consecutive cells (loads first, then stores)
-                        if (out && v4) {
+                        if (out && op.rows_per_pass > 0) {
+                            // full-row pass: rows [k0, k0 + R) of each cell are one contiguous run
+                            const int k0 = n * op.rows_per_pass;
+                            const int len = (nph - k0 < op.rows_per_pass ? nph - k0 : op.rows_per_pass) * nph;
+                            for (int cc = 16 * h; cc < 16 * h + 16; ++cc) {
+                                if (cell0 + cc >= s_ncells) break;
+                                float *__restrict__ dst = out + (cell0 + cc) * (int64_t)nph2 + (int64_t)k0 * nph;
+                                const float *__restrict__ src = stg + cc * pitch;
+                                for (int i0 = 0; i0 < len; i0 += 128) {
+                                    float x[4];
+#pragma unroll
+                                    for (int u = 0; u < 4; ++u) {
+                                        const int i = i0 + u * 32 + lane;
+                                        x[u] = i < len ? src[i] : 0.f;
+                                    }
+#pragma unroll
+                                    for (int u = 0; u < 4; ++u) {
+                                        const int i = i0 + u * 32 + lane;
+                                        if (i < len) __stcs(dst + i, x[u]);
+                                    }
+                                }
+                            }
+                        } else if (out && v4) {
                             // two cells per step, 16-byte coalesced stores
                             for (int cc = 16 * h; cc < 16 * h + 16; cc += 2) {
                                 float4 vals[2][MAX_F2S_IT / 4];
@@ -539,6 +564,14 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
 #pragma unroll
                                 for (int i = 0; i < 32; ++i) {
                                     const int col = n * op.NP + c0 + i;
+                                    if (op.rows_per_pass > 0) {
+                                        // full-row layout: column c of pass n is entry (nR + c / n_phi, c % n_phi)
+                                        const int cc = c0 + i;
+                                        const int k = n * op.rows_per_pass + cc / nph;
+                                        if (cc < op.NP && cc < op.rows_per_pass * nph && k < nph)
+                                            __stcs(dst + k * nph + cc % nph, __uint_as_float(r[i]) * us);
+                                        continue;
+                                    }
                                     const int32_t kl = (c0 + i < op.NP && col < op.n_cols) ? __ldg(s_symkl + col) : -1;
                                     if (kl >= 0) {   // (padding columns carry no pair)
                                         const int k = kl & 0xFFFF, l = kl >> 16;
@@ -580,12 +613,17 @@ size_t tc_smem_bytes(const TcArgs &a) {
 
 bool tc_can_stage(const TcArgs &a, const TcSeg &seg) {
     int np = 16;
+    bool pairs = false;
     for (int f = 0; f < MAX_FORMS; ++f)
         if ((seg.form_mask >> f) & 1) {
-            if (seg.op[f].n_pass != 1) return false;
+            // the pair layout is staged in one pass; the full-row layout in any number
+            if (seg.op[f].rows_per_pass == 0) {
+                if (seg.op[f].n_pass != 1) return false;
+                pairs = true;
+            }
             np = seg.op[f].NP > np ? seg.op[f].NP : np;
         }
-    if (seg.n_phi * seg.n_phi > 32 * MAX_F2S_IT) return false;
+    if (pairs && seg.n_phi * seg.n_phi > 32 * MAX_F2S_IT) return false;
     TcArgs t = a;
     t.pitch_max = (np + 1) > a.pitch_max ? (np + 1) : a.pitch_max;
     return tc_smem_bytes(t) <= 227 * 1024;
