@@ -22,19 +22,21 @@ struct CellGeom {
     double G[6];   // symmetric pairs (0,0),(0,1),(0,2),(1,1),(1,2),(2,2) (d=3) or (0,0),(0,1),(1,1)
 };
 
-// J, its cofactor matrix and det J in FP64 (G left out); returns the status bits.
-__device__ __forceinline__ int cell_cofactors(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
-                                              int64_t c, int d, CellGeom &g) {
-    double x[4][3];
+// The d+1 vertex coordinates of cell c (unused entries zero).
+__device__ __forceinline__ void cell_vertices(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
+                                              int64_t c, int d, double (&x)[4][3]) {
     const int nv = d + 1;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        if (k < nv) {
-            int64_t v = __ldg(cells + c * nv + k);
+        const int64_t v = (k < nv) ? __ldg(cells + c * nv + k) : 0;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) x[k][i] = (i < d) ? __ldg(vertices + v * d + i) : 0.0;
-        }
+        for (int i = 0; i < 3; ++i) x[k][i] = (k < nv && i < d) ? __ldg(vertices + v * d + i) : 0.0;
     }
+}
+
+// J, its cofactor matrix and det J in FP64 (G left out) from the vertex
+// coordinates; returns the status bits.
+__device__ __forceinline__ int cell_cofactors_x(const double (&x)[4][3], int d, CellGeom &g) {
     double J[3][3];
     if (d == 3) {
 #pragma unroll
@@ -69,9 +71,15 @@ __device__ __forceinline__ int cell_cofactors(const double *__restrict__ vertice
     return st;
 }
 
-__device__ __forceinline__ int cell_geometry(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
-                                             int64_t c, int d, CellGeom &g) {
-    const int st = cell_cofactors(vertices, cells, c, d, g);
+__device__ __forceinline__ int cell_cofactors(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
+                                              int64_t c, int d, CellGeom &g) {
+    double x[4][3];
+    cell_vertices(vertices, cells, c, d, x);
+    return cell_cofactors_x(x, d, g);
+}
+
+__device__ __forceinline__ int cell_geometry_x(const double (&x)[4][3], int d, CellGeom &g) {
+    const int st = cell_cofactors_x(x, d, g);
     const double inv = (st == 0) ? 1.0 / g.absdet : 0.0;
     if (d == 3) {
         int j = 0;
@@ -89,6 +97,13 @@ __device__ __forceinline__ int cell_geometry(const double *__restrict__ vertices
         g.G[3] = g.G[4] = g.G[5] = 0.0;
     }
     return st;
+}
+
+__device__ __forceinline__ int cell_geometry(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
+                                             int64_t c, int d, CellGeom &g) {
+    double x[4][3];
+    cell_vertices(vertices, cells, c, d, x);
+    return cell_geometry_x(x, d, g);
 }
 
 // FP64 -> FP32 with round-to-nearest-even (IEEE 754), entirely on the
