@@ -203,6 +203,23 @@ fe_status fe_assemble_host(fe_plan *plan, unsigned forms, fe_precision prec, con
 fe_status fe_assemble_elements(fe_plan *plan, unsigned forms, fe_precision prec, const void *A_stiffness,
                                const void *A_mass, void *csr_stiffness, void *csr_mass);
 
+/* Linear forms (Algorithm 2; Sec. 3.1 v_j = a_K(w, phi_j)): the action of
+ * the mass and/or Poisson form on the FE function with global coefficients w,
+ *   b^c = sum_s B_s r_s,  r_s = vstack_q(w_q z(X_q) (G grad w(X_q))_s)
+ * (mass: r = vstack_q(w_q z(X_q) |det J| w(X_q))), and the vector assembly
+ * v^g = L b (Sec. 3.3), each entry summed over its cells in increasing cell
+ * order (bitwise reproducible).
+ * prec: FE_PREC_FP64 (FP64 throughout), or FE_PREC_TF32 / BF16 / FP16: the
+ * tabulated B and each cell's coefficients rounded once to the storage
+ * format, everything else in FP32 (Sec. 4.5).  Others: FE_ERR_UNSUPPORTED.
+ * kappa: device [n_cells][n_q] FP64.  w: device [n_dofs] FP64.
+ * b_stiffness / b_mass: device [n_cells][n_phi] cell vectors (double for FP64
+ * else float) or NULL; v_stiffness / v_mass: device [n_dofs] (same type) or
+ * NULL; a requested form needs at least one of its two outputs (cell vectors
+ * then live in a plan workspace).  Asynchronous on the plan's stream. */
+fe_status fe_action(fe_plan *plan, unsigned forms, fe_precision prec, const double *vertices, const double *kappa,
+                    const double *w, void *b_stiffness, void *b_mass, void *v_stiffness, void *v_mass);
+
 /* Adjoint of L = v^T A^g u for the stiffness form (not in the paper):
  *   g_kappa[c][q] = dL/dkappa_cq = w_q |det J| (J^{-T} grad u_h(X_q)).(J^{-T} grad v_h(X_q))
  *   g_vertices[v][i] = dL/dx_{v,i}, kappa at the quadrature points held fixed,

@@ -20,6 +20,8 @@ element kernels and assembly"):
 * C routines in ``fe_oracle.c``: geometry by LU (Sec. 4.2), element matrices
   by the literal quadrature sum (Sec. 3.1), canonical dof map, CSR pattern,
   assembly A^g = L D L^T (Sec. 3.3), kappa_q^A (Corollary 4.10), adjoint.
+* ``Problem.action`` / ``assemble_vector`` -- Algorithm 2 (the action of a
+  form on a known FE function, b = sum_s B_s r_s) and v^g = L b (Sec. 3.3).
 * ``error_bound`` -- the per-cell bound of Theorem 4.8 / Corollary 4.10 in
   the form used by the tests (see its docstring).
 
@@ -406,6 +408,43 @@ class Problem:
                                             gk.ctypes.data if want_kappa else None,
                                             gx.ctypes.data if want_x else None, ctypes.byref(L)), "adjoint")
         return float(L.value), gk, gx
+
+    # linear forms: the action of a form on a known FE function (Algorithm 2) --
+    def action(self, kappa, w, form: str, with_magnitude: bool = False):
+        """Per-cell vectors b [n_cells, n_phi] of v_j = a_K(w, phi_j) (Sec. 3.1) for
+        the FE function with global coefficients w, by Algorithm 2 in FP64:
+        r_s = vstack_q(w_q z(X_q) (G grad w)_s(X_q)) (Poisson; mass: w_q z |det J| w(X_q)),
+        b = sum_s B_s r_s, with grad w(X_q) = sum_k w_k B_skq the reference gradient.
+        with_magnitude: also sum_{s,q} |B_skq| sum_t |w_q z G_st| sum_j |B_tjq| |w_j|,
+        the magnitude a componentwise rounding bound scales with."""
+        dofs, nd = self.cell_dofs()
+        kappa = np.asarray(kappa, np.float64).reshape(self.n_cells, self.n_q)
+        wc = np.asarray(w, np.float64)[dofs]                                 # [nc, n_phi]
+        det, G = mesh_geometry(self.vertices, self.cells)                    # G = |det J| J^-1 J^-T
+        wk = self.weights[None, :] * kappa                                   # w_q z(X_q)
+        if form == "mass":
+            val = np.einsum("ck,kq->cq", wc, self.phi)                      # w(X_q)
+            r = wk * np.abs(det)[:, None] * val
+            b = np.einsum("kq,cq->ck", self.phi, r)
+            if not with_magnitude:
+                return b
+            mr = wk * np.abs(det)[:, None] * np.einsum("ck,kq->cq", np.abs(wc), np.abs(self.phi))
+            return b, np.einsum("kq,cq->ck", np.abs(self.phi), mr)
+        gw = np.einsum("ck,skq->csq", wc, self.dphi)                        # reference gradient of w
+        r = wk[:, None, :] * np.einsum("cst,ctq->csq", G, gw)
+        b = np.einsum("skq,csq->ck", self.dphi, r)
+        if not with_magnitude:
+            return b
+        agw = np.einsum("ck,skq->csq", np.abs(wc), np.abs(self.dphi))
+        mr = wk[:, None, :] * np.einsum("cst,ctq->csq", np.abs(G), agw)
+        return b, np.einsum("skq,csq->ck", np.abs(self.dphi), mr)
+
+    def assemble_vector(self, b):
+        """v^g = L b (Sec. 3.3): each cell vector added into its dofs."""
+        dofs, nd = self.cell_dofs()
+        v = np.zeros(nd)
+        np.add.at(v, dofs.reshape(-1), np.asarray(b, np.float64).reshape(-1))
+        return v
 
     def with_vertices(self, vertices):
         other = Problem.__new__(Problem)

@@ -191,6 +191,23 @@ class Plan:
                                       _ptr(out.get("stiffness")), _ptr(out.get("mass"))), "fe_assemble_host")
         return out
 
+    def action(self, kappa, w, forms=("stiffness", "mass"), prec="fp64", vertices=None, cell_vectors=False,
+               out=None):
+        """Algorithm 2: v^g = L b with b^c_j = a_K(w, phi_j) for the FE function with
+        coefficients w (fe_action).  Returns {form: v [n_dofs]} (and, with
+        cell_vectors, {form: b [n_cells, n_phi]} as a second value)."""
+        self._check_dev(kappa, torch.float64, (self.n_cells, self.n_q), "kappa")
+        self._check_dev(w, torch.float64, (self.n_dofs,), "w")
+        self._check_dev(vertices, torch.float64, (self.n_vertices, self.d), "vertices")
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        v = out if out is not None else {f: torch.empty(self.n_dofs, dtype=dt, device=self.device) for f in forms}
+        b = {f: torch.empty((self.n_cells, self.n_phi), dtype=dt, device=self.device) for f in forms} \
+            if cell_vectors else {}
+        check(load().fe_action(self._h, self._forms_mask(forms), PRECISIONS[prec], _ptr(vertices), _ptr(kappa),
+                               _ptr(w), _ptr(b.get("stiffness")), _ptr(b.get("mass")), _ptr(v.get("stiffness")),
+                               _ptr(v.get("mass"))), "fe_action")
+        return (v, b) if cell_vectors else v
+
     def adjoint(self, kappa, u, v, vertices=None, want_kappa=True, want_vertices=True, want_L=True):
         """(L, dL/dkappa, dL/dvertices) for L = v^T A_stiffness u, computed in FP64."""
         self._check_dev(kappa, torch.float64, (self.n_cells, self.n_q), "kappa")

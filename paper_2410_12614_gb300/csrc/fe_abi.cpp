@@ -89,6 +89,8 @@ struct fe_plan {
     TcOperand op[6][2];
     DevBuf ws_elem[2], ws_kappa, ws_csr[2], ws_adj_x, ws_adj_L, ws_Lsum;
     DevBuf ws_win, ws_cellf;             // factor kernel outputs (window, per-cell factors)
+    DevBuf act_tab[6][2], act_tab_t[6][2];  // action tables per precision and form (B, transposed B)
+    DevBuf ws_act_b[2];                  // action cell vectors when the caller keeps none
     bool timing = false;
     cudaEvent_t ev[8] = {};
     float stage_ms[4] = {0, 0, 0, 0};
@@ -830,6 +832,91 @@ fe_status fe_adjoint(fe_plan *plan, const double *vertices, const double *kappa,
     if (r < 0) return cuda_fail((cudaError_t)(-r), "adjoint kernel launch");
     mark(plan, 2, false);
     plan->last_launches = r;
+    return FE_OK;
+}
+
+// Tables of the action kernel for one precision and form: B [n_d][n_phi][n_q]
+// and its transpose [n_d][n_q][n_phi], in FP64 or rounded once to the storage
+// format (kept as FP32 values).
+static fe_status action_tables(fe_plan *P, int prec, int fi) {
+    if (P->act_tab[prec][fi].p) return FE_OK;
+    const bool stiff = fi == 0;
+    const int nd = stiff ? P->d : 1, nph = P->n_phi, nq = P->n_q;
+    const std::vector<double> &src = stiff ? P->h_dphi : P->h_phi;
+    std::vector<double> t((size_t)nd * nph * nq), tt(t.size());
+    const host::Format F = host::format_of(prec);
+    for (int s = 0; s < nd; ++s)
+        for (int k = 0; k < nph; ++k)
+            for (int q = 0; q < nq; ++q) {
+                double v = src[((size_t)s * nph + k) * nq + q];
+                if (prec != FE_PREC_FP64) v = host::round_to_format(v, F.mbits, F.emin, F.maxfinite);
+                t[((size_t)s * nph + k) * nq + q] = v;
+                tt[((size_t)s * nq + q) * nph + k] = v;
+            }
+    if (prec == FE_PREC_FP64) {
+        FE_CUDA(upload(P->act_tab[prec][fi], t, P->stream), "upload action table");
+        FE_CUDA(upload(P->act_tab_t[prec][fi], tt, P->stream), "upload action table");
+    } else {
+        std::vector<float> f(t.begin(), t.end()), ft(tt.begin(), tt.end());
+        FE_CUDA(upload(P->act_tab[prec][fi], f, P->stream), "upload action table");
+        FE_CUDA(upload(P->act_tab_t[prec][fi], ft, P->stream), "upload action table");
+    }
+    return FE_OK;
+}
+
+fe_status fe_action(fe_plan *plan, unsigned forms, fe_precision prec, const double *vertices, const double *kappa,
+                    const double *w, void *b_stiffness, void *b_mass, void *v_stiffness, void *v_mass) {
+    g_err.clear();
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (forms == 0 || (forms & ~plan->form_mask)) return fail(FE_ERR_INVALID_ARG, "forms not served by the plan");
+    if (prec != FE_PREC_FP64 && prec != FE_PREC_TF32 && prec != FE_PREC_BF16 && prec != FE_PREC_FP16)
+        return fail(FE_ERR_UNSUPPORTED, "fe_action supports FP64, TF32, BF16 and FP16");
+    if (!kappa || !w) return fail(FE_ERR_INVALID_ARG, "NULL kappa or w");
+    const bool fp64 = prec == FE_PREC_FP64;
+    void *bs[2] = {b_stiffness, b_mass}, *vs[2] = {v_stiffness, v_mass};
+    int launches = 0;
+    for (int fi = 0; fi < 2; ++fi) {
+        const unsigned form = fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS;
+        if (!(forms & form)) continue;
+        if (!bs[fi] && !vs[fi]) return fail(FE_ERR_INVALID_ARG, "no output for a requested form");
+        fe_status st = action_tables(plan, (int)prec, fi);
+        if (st) return st;
+        void *b = bs[fi];
+        if (!b) {
+            st = ensure_ws(plan->ws_act_b[fi], (fp64 ? 8 : 4) * (size_t)plan->n_cells * plan->n_phi,
+                           "action workspace");
+            if (st) return st;
+            b = plan->ws_act_b[fi].p;
+        }
+        ActArgs a{};
+        a.vertices = vertices ? vertices : plan->vertices.as<double>();
+        a.cells = plan->cells.as<int32_t>();
+        a.cell_dofs = plan->cell_dofs.as<int32_t>();
+        a.n_cells = plan->n_cells;
+        a.d = plan->d;
+        a.n_phi = plan->n_phi;
+        a.n_q = plan->n_q;
+        a.form = (int)form;
+        a.prec = (int)prec;
+        a.kappa = kappa;
+        a.weights = plan->weights.as<double>();
+        a.w = w;
+        a.tab = plan->act_tab[prec][fi].p;
+        a.tab_t = plan->act_tab_t[prec][fi].p;
+        a.b = b;
+        a.status = plan->status.as<int>();
+        if (action_smem_bytes(a, fp64) > 200 * 1024) return fail(FE_ERR_UNSUPPORTED, "element too large for fe_action");
+        int r = launch_action(a, fp64, plan->stream);
+        if (r < 0) return cuda_fail((cudaError_t)(-r), "action kernel launch");
+        launches += r;
+        if (vs[fi]) {
+            r = launch_vector_assemble(plan->n_dofs, plan->inc_ptr.as<int64_t>(), plan->inc_elem.as<int32_t>(), b,
+                                       vs[fi], fp64, plan->stream);
+            if (r < 0) return cuda_fail((cudaError_t)(-r), "vector assembly launch");
+            launches += r;
+        }
+    }
+    plan->last_launches = launches;
     return FE_OK;
 }
 

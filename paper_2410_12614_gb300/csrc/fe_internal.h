@@ -160,6 +160,24 @@ struct AdjArgs {
     int *status;
 };
 
+// One form's action on a FE function (Algorithm 2) over one plan.
+struct ActArgs {
+    const double *vertices;
+    const int32_t *cells;
+    const int32_t *cell_dofs;  // [n_cells][n_phi]
+    int64_t n_cells;
+    int d, n_phi, n_q;
+    int form;                  // FE_FORM_MASS or FE_FORM_STIFFNESS
+    int prec;                  // FE_PREC_FP64 or a storage format
+    const double *kappa;       // [n_cells][n_q]
+    const double *weights;     // [n_q]
+    const double *w;           // [n_dofs] global coefficients
+    const void *tab;           // [n_d][n_phi][n_q] (double, or float rounded to the storage format)
+    const void *tab_t;         // [n_d][n_q][n_phi] the same, transposed
+    void *b;                   // [n_cells][n_phi] cell vectors (double or float)
+    int *status;
+};
+
 // Kernel launchers (defined in the .cu files).  Return the number of
 // kernel launches made, or a negative cudaError_t on launch failure.
 int launch_tc_elements(const TcArgs &a, size_t smem_bytes, cudaStream_t s, int grid = 0);
@@ -167,6 +185,10 @@ int launch_tc_elements(const TcArgs &a, size_t smem_bytes, cudaStream_t s, int g
 // kernel; run before launch_tc_elements on the same arguments).
 int launch_factor(const TcArgs &a, cudaStream_t s);
 size_t tc_smem_bytes(const TcArgs &a);
+int launch_action(const ActArgs &a, bool fp64, cudaStream_t s);
+size_t action_smem_bytes(const ActArgs &a, bool fp64);
+int launch_vector_assemble(int64_t n_dofs, const int64_t *inc_ptr, const int32_t *inc_elem, const void *b, void *v,
+                           bool fp64, cudaStream_t s);
 // Whether a segment can use the staged epilogue under the given global shape.
 bool tc_can_stage(const TcArgs &a, const TcSeg &seg);
 int launch_f64_elements(const F64Args &a, cudaStream_t s);
