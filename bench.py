@@ -125,6 +125,22 @@ def algorithmic_bytes(plan, prec):
     return factor, elem, asm
 
 
+def action_cost(plan):
+    """Algorithmic HBM bytes and FP32 flops of one action step (both forms in
+    one pass): kappa (FP64), connectivity, vertices and the cells' dof lists in
+    once; each global coefficient read once (later gathers hit L2); per form,
+    the cell vectors written and read back by the vector assembly, and the
+    assembled vector out; the incidence lists read once.  Flops: grad w (or w)
+    at the points, r, and b."""
+    nc, nq, nph, d, nd_ = plan.n_cells, plan.n_q, plan.n_phi, plan.d, plan.n_dofs
+    shared = (8 * nq * nc + 4 * (d + 1) * nc + 8 * d * plan.n_vertices + 4 * nph * nc + 8 * nd_
+              + 8 * (nd_ + 1) + 4 * nph * nc)
+    per_form = 2 * 4 * nph * nc + 4 * nd_
+    flops = nc * nq * (2 * d * nph + (2 * d * d + d) + 2 * d * nph)   # Poisson
+    flops += nc * nq * (2 * nph + 2 + 2 * nph)                         # mass
+    return shared + 2 * per_form, flops
+
+
 def _traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary
     (profiles/traffic.json), if the kernel's sources are unchanged since the
@@ -265,6 +281,22 @@ def run_ours(args, rank, world):
                 ts.append(e0.elapsed_time(e1))
             ms = statistics.median(ts)
             action[prec] = {"ms_per_step": ms, "cell_vectors_per_s": 2 * plan.n_cells / (ms / 1e3)}
+        # the mixed action's roofline: max(bytes / HBM peak, flops / FP32 CUDA-core peak), the
+        # latter from the unit counts: SMs x 128 FP32 lanes x 2 flops x the maximum SM clock
+        hbm_peak, _ = _peaks()
+        a_bytes, a_flops = action_cost(plan)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        fp32_tflops = sms * 128 * 2 * (clocks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+        t_bytes = a_bytes / (hbm_peak * 1e9) * 1e3
+        t_flops = a_flops / (fp32_tflops * 1e12) * 1e3
+        action["bf16"].update({
+            "algorithmic_bytes": a_bytes, "fp32_flops": a_flops,
+            "achieved_gbs": a_bytes / (action["bf16"]["ms_per_step"] / 1e3) / 1e9,
+            "achieved_fp32_tflops": a_flops / (action["bf16"]["ms_per_step"] / 1e3) / 1e12,
+            "fp32_peak_tflops": fp32_tflops, "hbm_peak_gbs": hbm_peak,
+            "bound": "alu" if t_flops > t_bytes else "hbm",
+            "roofline_ms": max(t_bytes, t_flops),
+            "frac_of_roofline": max(t_bytes, t_flops) / action["bf16"]["ms_per_step"]})
         extra["action_algorithm2"] = action
 
     hbm, how = _peaks()

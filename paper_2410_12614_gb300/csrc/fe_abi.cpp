@@ -89,7 +89,8 @@ struct fe_plan {
     TcOperand op[6][2];
     DevBuf ws_elem[2], ws_kappa, ws_csr[2], ws_adj_x, ws_adj_L, ws_Lsum;
     DevBuf ws_win, ws_cellf;             // factor kernel outputs (window, per-cell factors)
-    DevBuf act_tab[6][2], act_tab_t[6][2];  // action tables per precision and form (B, transposed B)
+    DevBuf act_tab[6][2], act_tab_t[6][2];  // warp-per-cell action tables per precision and form (B, transposed B)
+    DevBuf act_packed[6][3];                // thread-per-cell action tables per precision and forms mask - 1
     DevBuf ws_act_b[2];                  // action cell vectors when the caller keeps none
     bool timing = false;
     cudaEvent_t ev[8] = {};
@@ -835,9 +836,9 @@ fe_status fe_adjoint(fe_plan *plan, const double *vertices, const double *kappa,
     return FE_OK;
 }
 
-// Tables of the action kernel for one precision and form: B [n_d][n_phi][n_q]
-// and its transpose [n_d][n_q][n_phi], in FP64 or rounded once to the storage
-// format (kept as FP32 values).
+// Tables of the warp-per-cell action kernel for one precision and form: B
+// [n_d][n_phi][n_q] and its transpose [n_d][n_q][n_phi], in FP64 or rounded once
+// to the storage format (kept as FP32 values).
 static fe_status action_tables(fe_plan *P, int prec, int fi) {
     if (P->act_tab[prec][fi].p) return FE_OK;
     const bool stiff = fi == 0;
@@ -864,6 +865,33 @@ static fe_status action_tables(fe_plan *P, int prec, int fi) {
     return FE_OK;
 }
 
+// Packed table of the thread-per-cell action kernel for one storage format and
+// forms mask (bit 0 Poisson, bit 1 mass): per quadrature point the Poisson
+// segments B_skq (s = 0 .. d-1) then the mass segment B_kq, each over k and
+// zero-padded to act_seg_floats, rounded once to the storage format.
+static fe_status action_packed(fe_plan *P, int prec, int forms) {
+    DevBuf &dst = P->act_packed[prec][forms - 1];
+    if (dst.p) return FE_OK;
+    const int nph = P->n_phi, nq = P->n_q, d = P->d;
+    const int seg = act_seg_floats(nph), row = act_row_floats(d, nph, forms);
+    const host::Format F = host::format_of(prec);
+    std::vector<float> packed((size_t)nq * row, 0.f);
+    for (int q = 0; q < nq; ++q) {
+        int off = 0;
+        if (forms & 1)
+            for (int s = 0; s < d; ++s, off += seg)
+                for (int k = 0; k < nph; ++k)
+                    packed[(size_t)q * row + off + k] = (float)host::round_to_format(
+                        P->h_dphi[((size_t)s * nph + k) * nq + q], F.mbits, F.emin, F.maxfinite);
+        if (forms & 2)
+            for (int k = 0; k < nph; ++k)
+                packed[(size_t)q * row + off + k] =
+                    (float)host::round_to_format(P->h_phi[(size_t)k * nq + q], F.mbits, F.emin, F.maxfinite);
+    }
+    FE_CUDA(upload(dst, packed, P->stream), "upload action table");
+    return FE_OK;
+}
+
 fe_status fe_action(fe_plan *plan, unsigned forms, fe_precision prec, const double *vertices, const double *kappa,
                     const double *w, void *b_stiffness, void *b_mass, void *v_stiffness, void *v_mass) {
     g_err.clear();
@@ -874,47 +902,76 @@ fe_status fe_action(fe_plan *plan, unsigned forms, fe_precision prec, const doub
     if (!kappa || !w) return fail(FE_ERR_INVALID_ARG, "NULL kappa or w");
     const bool fp64 = prec == FE_PREC_FP64;
     void *bs[2] = {b_stiffness, b_mass}, *vs[2] = {v_stiffness, v_mass};
-    int launches = 0;
+    const unsigned form_bit[2] = {FE_FORM_STIFFNESS, FE_FORM_MASS};
+    int mask = 0;   // bit 0 Poisson, bit 1 mass
     for (int fi = 0; fi < 2; ++fi) {
-        const unsigned form = fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS;
-        if (!(forms & form)) continue;
+        if (!(forms & form_bit[fi])) continue;
         if (!bs[fi] && !vs[fi]) return fail(FE_ERR_INVALID_ARG, "no output for a requested form");
-        fe_status st = action_tables(plan, (int)prec, fi);
-        if (st) return st;
-        void *b = bs[fi];
-        if (!b) {
-            st = ensure_ws(plan->ws_act_b[fi], (fp64 ? 8 : 4) * (size_t)plan->n_cells * plan->n_phi,
-                           "action workspace");
+        mask |= 1 << fi;
+        if (!bs[fi]) {
+            fe_status st = ensure_ws(plan->ws_act_b[fi], (fp64 ? 8 : 4) * (size_t)plan->n_cells * plan->n_phi,
+                                     "action workspace");
             if (st) return st;
-            b = plan->ws_act_b[fi].p;
+            bs[fi] = plan->ws_act_b[fi].p;
         }
-        ActArgs a{};
-        a.vertices = vertices ? vertices : plan->vertices.as<double>();
-        a.cells = plan->cells.as<int32_t>();
-        a.cell_dofs = plan->cell_dofs.as<int32_t>();
-        a.n_cells = plan->n_cells;
-        a.d = plan->d;
-        a.n_phi = plan->n_phi;
-        a.n_q = plan->n_q;
-        a.form = (int)form;
-        a.prec = (int)prec;
-        a.kappa = kappa;
-        a.weights = plan->weights.as<double>();
-        a.w = w;
-        a.tab = plan->act_tab[prec][fi].p;
-        a.tab_t = plan->act_tab_t[prec][fi].p;
-        a.b = b;
-        a.status = plan->status.as<int>();
+    }
+    ActArgs a{};
+    a.vertices = vertices ? vertices : plan->vertices.as<double>();
+    a.cells = plan->cells.as<int32_t>();
+    a.cell_dofs = plan->cell_dofs.as<int32_t>();
+    a.n_cells = plan->n_cells;
+    a.d = plan->d;
+    a.n_phi = plan->n_phi;
+    a.n_q = plan->n_q;
+    a.prec = (int)prec;
+    a.kappa = kappa;
+    a.weights = plan->weights.as<double>();
+    a.w = w;
+    a.status = plan->status.as<int>();
+    int launches = 0;
+    if (action_per_cell(plan->d, plan->n_phi, fp64)) {
+        // every requested form in one launch
+        fe_status st = action_packed(plan, (int)prec, mask);
+        if (st) return st;
+        a.forms = mask;
+        a.tab = plan->act_packed[prec][mask - 1].p;
+        a.b = bs[0];
+        a.b_mass = bs[1];
+        a.qw = action_window(plan->d, plan->n_phi, plan->n_q, mask);
         if (action_smem_bytes(a, fp64) > 200 * 1024) return fail(FE_ERR_UNSUPPORTED, "element too large for fe_action");
-        int r = launch_action(a, fp64, plan->stream);
+        const int r = launch_action(a, fp64, plan->stream);
         if (r < 0) return cuda_fail((cudaError_t)(-r), "action kernel launch");
         launches += r;
-        if (vs[fi]) {
-            r = launch_vector_assemble(plan->n_dofs, plan->inc_ptr.as<int64_t>(), plan->inc_elem.as<int32_t>(), b,
-                                       vs[fi], fp64, plan->stream);
-            if (r < 0) return cuda_fail((cudaError_t)(-r), "vector assembly launch");
+    } else {
+        for (int fi = 0; fi < 2; ++fi) {
+            if (!(mask & (1 << fi))) continue;
+            fe_status st = action_tables(plan, (int)prec, fi);
+            if (st) return st;
+            a.form = (int)form_bit[fi];
+            a.tab = plan->act_tab[prec][fi].p;
+            a.tab_t = plan->act_tab_t[prec][fi].p;
+            a.b = bs[fi];
+            if (action_smem_bytes(a, fp64) > 200 * 1024)
+                return fail(FE_ERR_UNSUPPORTED, "element too large for fe_action");
+            const int r = launch_action(a, fp64, plan->stream);
+            if (r < 0) return cuda_fail((cudaError_t)(-r), "action kernel launch");
             launches += r;
         }
+    }
+    // vector assembly of the forms whose assembled vector was asked for (one launch)
+    const void *vb[2] = {nullptr, nullptr};
+    void *vv[2] = {nullptr, nullptr};
+    int nv = 0;
+    for (int fi = 0; fi < 2; ++fi)
+        if ((mask & (1 << fi)) && vs[fi]) {
+            vb[nv] = bs[fi];
+            vv[nv++] = vs[fi];
+        }
+    if (nv > 0) {
+        const int r = launch_vector_assemble(plan->n_dofs, plan->inc_ptr.as<int64_t>(), plan->inc_elem.as<int32_t>(),
+                                             vb[0], vb[1], vv[0], vv[1], fp64, plan->stream);
+        if (r < 0) return cuda_fail((cudaError_t)(-r), "vector assembly launch");
+        launches += r;
     }
     plan->last_launches = launches;
     return FE_OK;

@@ -47,12 +47,6 @@ __device__ __forceinline__ const AsmSeg &aseg_of(const AsmArgs &a, int64_t chunk
     return a.segs[lo];
 }
 
-template <int BYTES>
-__device__ __forceinline__ void cp_async_small(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // One row with more entries than a chunk holds, summed by one warp from
 // global memory: lane j of each 32-value group owns CSR value j and walks its
 // segment in order.  e0 is the chunk's first incidence.

@@ -129,12 +129,77 @@ __device__ __forceinline__ float f64_to_f32_rne(double x, int &nonfinite) {
     return __uint_as_float(bits | sign);
 }
 
+// G = |det J| J^-1 J^-T = C^T C / |det J| (upper triangle: G00 G01 G02 G11
+// G12 G22; d = 2: G00 G01 G11) and |det J| in FP32, formed from the FP64
+// cofactors and determinant rounded once each; a cell whose cofactors or
+// determinant leave FP32's normal range gets G computed in FP64 and rounded
+// once.  Returns the geometry status; on a nonzero status g6 and adet are
+// left as they were.
+__device__ __forceinline__ int cell_g32(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
+                                        int64_t c, int d, float (&g6)[6], float &adet) {
+    CellGeom geo;
+    const int st = cell_cofactors(vertices, cells, c, d, geo);
+    if (st) return st;
+    int nf = 0;
+    float C[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) C[i] = f64_to_f32_rne(geo.C[i], nf);
+    adet = f64_to_f32_rne(geo.absdet, nf);
+    const float inv = 1.0f / adet;
+    if (d == 3) {
+        int j = 0;
+#pragma unroll
+        for (int s = 0; s < 3; ++s)
+#pragma unroll
+            for (int u = s; u < 3; ++u)
+                g6[j++] = fmaf(C[s], C[u], fmaf(C[3 + s], C[3 + u], C[6 + s] * C[6 + u])) * inv;
+    } else {
+        g6[0] = fmaf(C[0], C[0], C[2] * C[2]) * inv;
+        g6[1] = fmaf(C[0], C[1], C[2] * C[3]) * inv;
+        g6[2] = fmaf(C[1], C[1], C[3] * C[3]) * inv;
+    }
+    bool fin = nf == 0 && adet > 0.f && isfinite(inv);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) fin = fin && isfinite(g6[j]);
+    if (!fin) {
+        const double inv64 = 1.0 / geo.absdet;
+        int j = 0;
+        if (d == 3) {
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+#pragma unroll
+                for (int u = s; u < 3; ++u)
+                    g6[j++] = (float)((geo.C[s] * geo.C[u] + geo.C[3 + s] * geo.C[3 + u] + geo.C[6 + s] * geo.C[6 + u]) *
+                                      inv64);
+        } else {
+            g6[0] = (float)((geo.C[0] * geo.C[0] + geo.C[2] * geo.C[2]) * inv64);
+            g6[1] = (float)((geo.C[0] * geo.C[1] + geo.C[2] * geo.C[3]) * inv64);
+            g6[2] = (float)((geo.C[1] * geo.C[1] + geo.C[3] * geo.C[3]) * inv64);
+        }
+        adet = (float)geo.absdet;
+    }
+    return 0;
+}
+
 // --------------------------------------------------------------------------
 // PTX wrappers
 // --------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+// Asynchronous global -> shared copy of 4, 8 or 16 bytes (both addresses
+// aligned to the size); cp_async_wait_all waits for the thread's copies.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Groups of asynchronous copies: close the thread's current group; wait until
+// at most N of its groups are still in flight.
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;

@@ -117,9 +117,9 @@ __global__ void __launch_bounds__(F_THREADS, 8) factor_kernel(const __grid_const
     if (tid < nvalid) {
         const int64_t c = c0 + tid;
         float g6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, adet = 0.f;
-        CellGeom geo;
         int st;
         if (G64) {
+            CellGeom geo;
             st = cell_geometry(S.vertices, S.cells, c, S.d, geo);
             if (!st) {
 #pragma unroll
@@ -127,48 +127,7 @@ __global__ void __launch_bounds__(F_THREADS, 8) factor_kernel(const __grid_const
                 adet = (float)geo.absdet;
             }
         } else {
-            st = cell_cofactors(S.vertices, S.cells, c, S.d, geo);
-            if (!st) {
-                int nf = 0;
-                float C[9];
-#pragma unroll
-                for (int i = 0; i < 9; ++i) C[i] = f64_to_f32_rne(geo.C[i], nf);
-                adet = f64_to_f32_rne(geo.absdet, nf);
-                const float inv = 1.0f / adet;
-                if (S.d == 3) {
-                    int j = 0;
-#pragma unroll
-                    for (int s = 0; s < 3; ++s)
-#pragma unroll
-                        for (int u = s; u < 3; ++u)
-                            g6[j++] = fmaf(C[s], C[u], fmaf(C[3 + s], C[3 + u], C[6 + s] * C[6 + u])) * inv;
-                } else {
-                    g6[0] = fmaf(C[0], C[0], C[2] * C[2]) * inv;
-                    g6[1] = fmaf(C[0], C[1], C[2] * C[3]) * inv;
-                    g6[2] = fmaf(C[1], C[1], C[3] * C[3]) * inv;
-                }
-                bool fin = nf == 0 && adet > 0.f && isfinite(inv);
-#pragma unroll
-                for (int j = 0; j < 6; ++j) fin = fin && isfinite(g6[j]);
-                if (!fin) {
-                    // cofactors or det J outside FP32's normal range: G in FP64
-                    const double inv64 = 1.0 / geo.absdet;
-                    int j = 0;
-                    if (S.d == 3) {
-#pragma unroll
-                        for (int s = 0; s < 3; ++s)
-#pragma unroll
-                            for (int u = s; u < 3; ++u)
-                                g6[j++] = (float)((geo.C[s] * geo.C[u] + geo.C[3 + s] * geo.C[3 + u] +
-                                                   geo.C[6 + s] * geo.C[6 + u]) * inv64);
-                    } else {
-                        g6[0] = (float)((geo.C[0] * geo.C[0] + geo.C[2] * geo.C[2]) * inv64);
-                        g6[1] = (float)((geo.C[0] * geo.C[1] + geo.C[2] * geo.C[3]) * inv64);
-                        g6[2] = (float)((geo.C[1] * geo.C[1] + geo.C[3] * geo.C[3]) * inv64);
-                    }
-                    adet = (float)geo.absdet;
-                }
-            }
+            st = cell_g32(S.vertices, S.cells, c, S.d, g6, adet);
         }
         if (st) {
             atomicOr(&flags, st);

@@ -167,16 +167,41 @@ struct ActArgs {
     const int32_t *cell_dofs;  // [n_cells][n_phi]
     int64_t n_cells;
     int d, n_phi, n_q;
-    int form;                  // FE_FORM_MASS or FE_FORM_STIFFNESS
+    int form;                  // warp-per-cell kernel: FE_FORM_MASS or FE_FORM_STIFFNESS
+    int forms;                 // thread-per-cell kernel: bit 0 Poisson, bit 1 mass
     int prec;                  // FE_PREC_FP64 or a storage format
     const double *kappa;       // [n_cells][n_q]
     const double *weights;     // [n_q]
     const double *w;           // [n_dofs] global coefficients
-    const void *tab;           // [n_d][n_phi][n_q] (double, or float rounded to the storage format)
-    const void *tab_t;         // [n_d][n_q][n_phi] the same, transposed
-    void *b;                   // [n_cells][n_phi] cell vectors (double or float)
+    // Tables: the thread-per-cell kernel (action_per_cell) reads tab only, packed
+    // [n_q][act_row_floats]: per point, the Poisson segments s = 0 .. d-1 (if
+    // requested) then the mass segment (if requested), each act_seg_floats long
+    // (entries k = 0 .. n_phi-1, zero-padded).  The warp-per-cell kernel reads tab
+    // [n_d][n_phi][n_q] and tab_t [n_d][n_q][n_phi].  Double for FP64, else float
+    // values rounded to the storage format.
+    const void *tab;
+    const void *tab_t;
+    void *b;                   // [n_cells][n_phi] cell vectors (double or float): the form, or Poisson
+    void *b_mass;              // thread-per-cell kernel: the mass form's cell vectors
     int *status;
+    int qw;                    // quadrature points per shared-memory window (thread-per-cell kernel)
 };
+
+// Packed action table: floats per segment (one derivative direction, or the
+// basis values, over the local dofs, padded to a multiple of 4) and per
+// quadrature point for the requested forms (bit 0 Poisson: d segments; bit 1
+// mass: one segment).
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int act_seg_floats(int n_phi) { return (n_phi + 3) / 4 * 4; }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int act_row_floats(int d, int n_phi, int forms) {
+    return act_seg_floats(n_phi) * (((forms & 1) ? d : 0) + ((forms & 2) ? 1 : 0));
+}
+constexpr int kActSmemTarget = 48 * 1024;   // shared memory per CTA the quadrature window is sized for
 
 // Kernel launchers (defined in the .cu files).  Return the number of
 // kernel launches made, or a negative cudaError_t on launch failure.
@@ -187,8 +212,13 @@ int launch_factor(const TcArgs &a, cudaStream_t s);
 size_t tc_smem_bytes(const TcArgs &a);
 int launch_action(const ActArgs &a, bool fp64, cudaStream_t s);
 size_t action_smem_bytes(const ActArgs &a, bool fp64);
-int launch_vector_assemble(int64_t n_dofs, const int64_t *inc_ptr, const int32_t *inc_elem, const void *b, void *v,
-                           bool fp64, cudaStream_t s);
+// Whether the thread-per-cell action kernel serves (d, n_phi, precision), and
+// its quadrature window for the requested forms.
+bool action_per_cell(int d, int n_phi, bool fp64);
+int action_window(int d, int n_phi, int n_q, int forms);
+// v0 = L b0 (and v1 = L b1 when b1 is not NULL) in one launch.
+int launch_vector_assemble(int64_t n_dofs, const int64_t *inc_ptr, const int32_t *inc_elem, const void *b0,
+                           const void *b1, void *v0, void *v1, bool fp64, cudaStream_t s);
 // Whether a segment can use the staged epilogue under the given global shape.
 bool tc_can_stage(const TcArgs &a, const TcSeg &seg);
 int launch_f64_elements(const F64Args &a, cudaStream_t s);
