@@ -210,8 +210,11 @@ fe_status fe_assemble_elements(fe_plan *plan, unsigned forms, fe_precision prec,
  * v^g = L b (Sec. 3.3), each entry summed over its cells in increasing cell
  * order (bitwise reproducible).
  * prec: FE_PREC_FP64 (FP64 throughout), or FE_PREC_TF32 / BF16 / FP16: the
- * tabulated B and each cell's coefficients rounded once to the storage
- * format, everything else in FP32 (Sec. 4.5).  Others: FE_ERR_UNSUPPORTED.
+ * tabulated B and each cell's coefficients rounded once to the storage format
+ * (the casting remark of Sec. 4.5), r_s computed in FP32 and rounded once to
+ * the storage format (the theorem on r_s, Sec. 4.5), both contractions
+ * accumulated in FP32.  Others: FE_ERR_UNSUPPORTED.  Both forms requested
+ * together are computed in one pass over kappa and the geometry.
  * kappa: device [n_cells][n_q] FP64.  w: device [n_dofs] FP64.
  * b_stiffness / b_mass: device [n_cells][n_phi] cell vectors (double for FP64
  * else float) or NULL; v_stiffness / v_mass: device [n_dofs] (same type) or
