@@ -20,8 +20,10 @@
 //   3. a block-wide scan of the counts gives each CSR value's segment in the
 //      stage; one thread per value sums it in order, starting from zero, and
 //      the values leave in coalesced stores.
-// A row with more than ASM_CHUNK entries is a chunk of its own and is summed
-// by one warp straight from global memory in the same order.  Every value is
+// Chunks are taken from the last one down (the element matrices written last
+// by the element kernel are still in L2).  A row with more than ASM_CHUNK
+// entries is a chunk of its own and is summed by one warp straight from global
+// memory in the same order.  Every value is
 // bitwise reproducible and independent of the launch shape.  Accumulation is
 // in the element precision (FP32 for the reduced-precision paths, FP64 for
 // the FP64 path), as in the u_q of Corollary 4.11.
@@ -93,7 +95,11 @@ __global__ void __launch_bounds__(ASM_THREADS) assemble_kernel(const __grid_cons
     uint8_t *cnt_s = reinterpret_cast<uint8_t *>(start_s + ASM_CHUNK);        // [ASM_CHUNK] segment lengths
     __shared__ int warp_tot[ASM_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int64_t g = blockIdx.x; g < a.n_chunks; g += gridDim.x) {
+    // chunks from the last row down: the element kernel that ran just before
+    // wrote the highest cells last, so their element matrices are the ones
+    // still in L2 and are read first
+    for (int64_t gi = blockIdx.x; gi < a.n_chunks; gi += gridDim.x) {
+        const int64_t g = a.n_chunks - 1 - gi;
         const AsmSeg &S = aseg_of<BATCHED>(a, g);
         const int64_t ch = g - S.chunk_begin;
         const T *__restrict__ A0 = static_cast<const T *>(S.A[0]);
