@@ -328,7 +328,9 @@ __global__ void __launch_bounds__(ACT_WARPS * 32) action_kernel(const __grid_con
         __syncwarp();
         // grad w (or w) at the quadrature points, then r
         for (int q = lane; q < nq; q += 32) {
-            const T wk = (T)__ldg(a.weights + q) * (T)__ldg(a.kappa + c * nq + q);
+            const double kq = __ldg(a.kappa + c * nq + q);
+            if (!isfinite(kq)) atomicOr(a.status, ST_NONFINITE);
+            const T wk = (T)__ldg(a.weights + q) * (T)kq;
             if (nd == 1) {
                 T val = T(0);
                 for (int k = 0; k < nph; ++k) val = fma(B[(size_t)k * nq + q], ws[k], val);

@@ -68,3 +68,26 @@ def test_action_deterministic_and_outputs():
         assert torch.equal(v1[f], v2[f])
     with pytest.raises(Exception):
         plan.action(kd, w, prec="e4m3")
+
+
+def test_action_status_codes():
+    # non-finite kappa -> FE_ERR_NONFINITE; a cell of zero volume -> FE_ERR_DEGENERATE_CELL
+    v, c = inputs.cube_mesh(2, 0.1, 1)
+    pts, w = api.quadrature_rule("tetrahedron", 3)
+    plan = api.Plan("tetrahedron", v, c, 2, pts, w, precisions=("bf16",))
+    wd = cuda(inputs.gaussian_vector(plan.n_dofs, 130).astype(np.float64))
+    for prec in ("bf16", "fp64"):
+        kap = inputs.lognormal_kappa(plan.n_cells, plan.n_q, 131)
+        kap[7, 2] = np.inf
+        plan.action(cuda(kap), wd, prec=prec)
+        with pytest.raises(api._lib.FeError) as e:
+            plan.sync()
+        assert e.value.status == -4
+        plan.sync()   # the status word was cleared
+        verts = torch.from_numpy(v.copy()).cuda()
+        verts[c[0][3]] = verts[c[0][0]]   # two vertices of cell 0 coincide: det J == 0
+        plan.action(cuda(inputs.lognormal_kappa(plan.n_cells, plan.n_q, 132)), wd, prec=prec, vertices=verts)
+        with pytest.raises(api._lib.FeError) as e:
+            plan.sync()
+        assert e.value.status in (-3, -4)
+        plan.sync()
