@@ -355,7 +355,77 @@ def run_ours(args, rank, world):
         result["cpu_baseline"] = cpu_baseline(args, plan, kap_h, els, v, c)
     if rank == 0 and args.with_batch:
         result["batched_256_meshes"] = run_batch(args)
+    if rank == 0 and args.sweep:
+        result["degree_sweep"] = run_sweep(args)
     return result
+
+
+SWEEP_PRECISIONS = ("bf16", "fp16", "tf32", "tf32x3", "e4m3")
+
+
+def run_sweep(args):
+    """Degree sweep: P1..P8 tetrahedra on 16^3 x 6 Kuhn boxes (24,576 cells,
+    jitter 0.15h, seed 4; kappa lognormal at (p+1)^3 points, seed 5), element
+    matrices of both forms (factor kernel + contraction; FP64 on the CUDA cores
+    up to P5) per precision, inputs resident, L2 flushed before each timed run.
+    Roofline per run: max(bytes / HBM peak, flops / the format's dense peak)
+    with flops = 2 n_d n_q n_phi^2 per cell and form (the Remark after
+    Algorithm 1; n_d = 3 Poisson, 1 mass) and bytes = kappa + connectivity
+    in, both element matrices out.  Format peaks from the measured BF16 burst
+    rate: FP16 the same, TF32 half, E4M3 twice, TF32x3 (three TF32 products
+    per term) a sixth."""
+    import torch
+    from paper_2410_12614_gb300 import api, inputs
+    hbm, _ = _peaks()
+    try:
+        bf16 = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+        peak_src = "measured BF16 burst"
+    except Exception:
+        bf16, peak_src = 1900.0, "fallback BF16"
+    peaks = {"bf16": bf16, "fp16": bf16, "tf32": bf16 / 2, "e4m3": 2 * bf16, "tf32x3": bf16 / 6}
+    v, c = inputs.cube_mesh(16, 0.15, 4)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {"mesh": "P1..P8 tetrahedra, 16^3 boxes x 6 (24,576 cells)", "peaks_tflops": peaks,
+           "peak_source": peak_src, "hbm_gbs": hbm, "runs": []}
+    with torch.cuda.stream(stream):
+        for p in range(1, 9):
+            pts, w = api.quadrature_rule("tetrahedron", p + 1)
+            plan = api.Plan("tetrahedron", v, c, p, pts, w, precisions=SWEEP_PRECISIONS, stream=stream)
+            kap = torch.from_numpy(inputs.lognormal_kappa(plan.n_cells, plan.n_q, 5)).cuda()
+            nc, nq, nph = plan.n_cells, plan.n_q, plan.n_phi
+            flops = 2.0 * (3 + 1) * nq * nph * nph * nc
+            for prec in SWEEP_PRECISIONS + (("fp64",) if p <= 5 else ()):
+                eb = 8 if prec == "fp64" else 4
+                els = {f: plan.empty_elements(prec) for f in ("stiffness", "mass")}
+                nbytes = nc * (8 * nq + 4 * 4 + 2 * eb * nph * nph) + plan.n_vertices * 3 * 8
+                for _ in range(2):
+                    plan.element_matrices(kap, prec=prec, out=els)
+                plan.sync()
+                ts = []
+                for _ in range(5 if prec != "fp64" or p <= 3 else 2):
+                    flush.fill_(1.0)
+                    flush.sum()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    plan.element_matrices(kap, prec=prec, out=els)
+                    e1.record(stream)
+                    stream.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                ms = statistics.median(ts)
+                run = {"p": p, "prec": prec, "n_phi": nph, "n_q": nq, "ms": ms,
+                       "element_matrices_per_s": 2 * nc / (ms / 1e3),
+                       "tflops": flops / (ms / 1e3) / 1e12, "gbs": nbytes / (ms / 1e3) / 1e9}
+                if prec != "fp64":
+                    t_bytes, t_flops = nbytes / (hbm * 1e9), flops / (peaks[prec] * 1e12)
+                    run.update({"bound": "tensor" if t_flops > t_bytes else "hbm",
+                                "frac_of_roofline": max(t_bytes, t_flops) / (ms / 1e3)})
+                out["runs"].append(run)
+                del els
+            del plan, kap
+            torch.cuda.empty_cache()
+    return out
 
 
 def _cpu_model():
@@ -562,6 +632,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--with-batch", action="store_true",
                     help="also time the 256-mesh uneven batch (adds about a minute of plan set-up)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="also time the element kernels for P1..P8 tetrahedra on 16^3 x 6 in every precision")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
