@@ -388,14 +388,17 @@ def run_sweep(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     out = {"mesh": "P1..P8 tetrahedra, 16^3 boxes x 6 (24,576 cells)", "peaks_tflops": peaks,
            "peak_source": peak_src, "hbm_gbs": hbm, "runs": []}
+    degrees = [int(x) for x in args.sweep_degrees.split(",")]
+    precs = tuple(x for x in args.sweep_precisions.split(",") if x in SWEEP_PRECISIONS)
     with torch.cuda.stream(stream):
-        for p in range(1, 9):
+        for p in degrees:
             pts, w = api.quadrature_rule("tetrahedron", p + 1)
-            plan = api.Plan("tetrahedron", v, c, p, pts, w, precisions=SWEEP_PRECISIONS, stream=stream)
+            plan = api.Plan("tetrahedron", v, c, p, pts, w, precisions=precs, stream=stream)
             kap = torch.from_numpy(inputs.lognormal_kappa(plan.n_cells, plan.n_q, 5)).cuda()
             nc, nq, nph = plan.n_cells, plan.n_q, plan.n_phi
             flops = 2.0 * (3 + 1) * nq * nph * nph * nc
-            for prec in SWEEP_PRECISIONS + (("fp64",) if p <= 5 else ()):
+            with_fp64 = p <= 5 and "fp64" in args.sweep_precisions.split(",")
+            for prec in precs + (("fp64",) if with_fp64 else ()):
                 eb = 8 if prec == "fp64" else 4
                 els = {f: plan.empty_elements(prec) for f in ("stiffness", "mass")}
                 nbytes = nc * (8 * nq + 4 * 4 + 2 * eb * nph * nph) + plan.n_vertices * 3 * 8
@@ -634,6 +637,10 @@ def main():
                     help="also time the 256-mesh uneven batch (adds about a minute of plan set-up)")
     ap.add_argument("--sweep", action="store_true",
                     help="also time the element kernels for P1..P8 tetrahedra on 16^3 x 6 in every precision")
+    ap.add_argument("--sweep-only", action="store_true",
+                    help="time only the degree sweep and print it as the JSON line (a profiling entry point)")
+    ap.add_argument("--sweep-degrees", default="1,2,3,4,5,6,7,8")
+    ap.add_argument("--sweep-precisions", default="bf16,fp16,tf32,tf32x3,e4m3,fp64")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -649,6 +656,12 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
+    if args.sweep_only:
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            print(json.dumps({"degree_sweep": run_sweep(args)}))
+        return
     res = run_ours(args, rank, world)
     if rank == 0:
         print(json.dumps(res))

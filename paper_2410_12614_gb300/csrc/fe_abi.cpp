@@ -647,10 +647,18 @@ static fe_status autotune_plan(fe_plan &P) {
             }
             if (best < 0) {
                 // sample: at most one tile per SM and at most 256 MB of element output
-                int64_t n = std::min<int64_t>(P.n_cells, (int64_t)sms * TC_M);
-                n = std::min<int64_t>(n, std::max<int64_t>(TC_M, (256ll << 20) / (4ll * P.n_phi * P.n_phi)));
-                DevBuf kap, out, win, cellf;
+                // two full waves of tiles (every SM busy, as in a production launch;
+                // a partial wave would time one tile's latency instead), at most 2 GB
+                // of sample output
+                int64_t n = std::min<int64_t>(P.n_cells, 2ll * sms * TC_M);
+                n = std::min<int64_t>(n, std::max<int64_t>(TC_M, (2048ll << 20) / (4ll * P.n_phi * P.n_phi)));
+                DevBuf kap, out, win, cellf, flush;
                 FE_CUDA(kap.alloc(sizeof(double) * n * P.n_q), "autotune buffer");
+                // written before every timed run so that each candidate starts with
+                // the sample's output out of L2, as a production launch does: the
+                // layouts differ in how many partially written sectors they leave
+                const size_t flush_bytes = (size_t)256 << 20;
+                FE_CUDA(flush.alloc(flush_bytes), "autotune buffer");
                 FE_CUDA(win.alloc(sizeof(float) * n * win_ld(P.n_q)), "autotune buffer");
                 FE_CUDA(cellf.alloc(sizeof(float) * n * CELLF), "autotune buffer");
                 FE_CUDA(out.alloc(sizeof(float) * n * P.n_phi * P.n_phi), "autotune buffer");
@@ -676,6 +684,7 @@ static fe_status autotune_plan(fe_plan &P) {
                     }
                     float ms_min = 1e30f;
                     for (int rep = 0; rep < 3; ++rep) {
+                        FE_CUDA(cudaMemsetAsync(flush.p, rep, flush_bytes, P.stream), "autotune flush");
                         FE_CUDA(cudaEventRecord(P.ev[4], P.stream), "autotune event");
                         int r = launch_tc_elements(a, smem, P.stream);
                         if (r < 0) return cuda_fail((cudaError_t)(-r), "autotune launch");
