@@ -38,6 +38,24 @@ WORKLOAD = ("P3 stiffness + mass, unit cube 24^3 boxes x 6 Kuhn tetrahedra (82,9
 METRIC = "element matrices/s and assembled nnz/s, mixed vs FP64 GPU, at stated max rel error"
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest value of x over all ranks (a job's time is its slowest
+    rank's); x itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step, ms_per_step, world):
+    """Whole-job units per second: every rank processes its own units in the
+    (max-over-ranks) step time."""
+    return world * units_per_rank_step / (ms_per_step / 1e3)
+
+
 def workload_config(world):
     """The `config` of both arms: the workload and how steps are timed."""
     return {"workload": WORKLOAD,
@@ -236,15 +254,11 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        total_ms = sum(step_ms)
-        if world > 1:
-            t = torch.tensor([total_ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(step_ms), world)
         ms_step = total_ms / args.steps
         elems_per_step = 2 * plan.n_cells
-        value = world * elems_per_step / (ms_step / 1e3)
-        nnz_per_s = world * 2 * plan.nnz / (ms_step / 1e3)
+        value = job_throughput(elems_per_step, ms_step, world)
+        nnz_per_s = job_throughput(2 * plan.nnz, ms_step, world)
 
         # end to end through the public API with host buffers
         kap_pinned = torch.from_numpy(kap_h).pin_memory()
@@ -256,7 +270,7 @@ def run_ours(args, rank, world):
             t0 = time.perf_counter()
             plan.assemble_host(kap_pinned, prec="bf16", out=host_out)
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        e2e_step = statistics.median(e2e_ms)
+        e2e_step = max_over_ranks(statistics.median(e2e_ms), world)
 
         # other precisions (context lines)
         extra = {}
@@ -343,7 +357,7 @@ def run_ours(args, rank, world):
                      "frac": achieved / hbm, "traffic": _traffic(dom_key),
                      "peak_source": f"{how} (MEASURED_PEAKS.json hbm_gbs, copy burst)",
                      "algorithmic_bytes_per_launch": dom_bytes},
-        "e2e": {"value": elems_per_step / (e2e_step / 1e3) * world, "unit": "element matrices/s",
+        "e2e": {"value": job_throughput(elems_per_step, e2e_step, world), "unit": "element matrices/s",
                 "h2d_bytes_per_step": int(plan.n_cells * plan.n_q * 8),
                 "d2h_bytes_per_step": int(2 * plan.nnz * 4), "ms_per_step": e2e_step,
                 "api": "fe_assemble_host (pinned host kappa in, pinned host CSR values out)"},
