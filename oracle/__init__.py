@@ -22,6 +22,8 @@ element kernels and assembly"):
   assembly A^g = L D L^T (Sec. 3.3), kappa_q^A (Corollary 4.10), adjoint.
 * ``Problem.action`` / ``assemble_vector`` -- Algorithm 2 (the action of a
   form on a known FE function, b = sum_s B_s r_s) and v^g = L b (Sec. 3.3).
+* ``Problem.gather_values`` / ``adjoint_stiffness_values`` -- the transpose of
+  the assembly and dL/dkappa for L = sum_e g_e A^g_e (calculus on Sec. 3.1).
 * ``error_bound`` -- the per-cell bound of Theorem 4.8 / Corollary 4.10 in
   the form used by the tests (see its docstring).
 
@@ -408,6 +410,33 @@ class Problem:
                                             gk.ctypes.data if want_kappa else None,
                                             gx.ctypes.data if want_x else None, ctypes.byref(L)), "adjoint")
         return float(L.value), gk, gx
+
+    # adjoint for a general gradient on the CSR values ---------------------------
+    def gather_values(self, g):
+        """G^c [n_cells, n_phi, n_phi] with G^c_kl = g at the CSR slot of
+        (dof(c, k), dof(c, l)): the transpose of the assembly A^g = L D L^T
+        (Sec. 3.3), so that sum_e g_e A^g_e = sum_c sum_kl G^c_kl A^c_kl."""
+        dofs, nd = self.cell_dofs()
+        row_ptr, col = self.csr_pattern()
+        rows = np.repeat(np.arange(nd, dtype=np.int64), np.diff(row_ptr))
+        keys = rows * nd + col.astype(np.int64)                  # increasing along the CSR order
+        q = dofs[:, :, None].astype(np.int64) * nd + dofs[:, None, :].astype(np.int64)
+        slot = np.searchsorted(keys, q.ravel()).reshape(q.shape)
+        assert np.array_equal(keys[slot], q), "entry outside the pattern"
+        return np.asarray(g, np.float64)[slot]
+
+    def adjoint_stiffness_values(self, kappa, g):
+        """L = sum_e g_e A^g_e for the stiffness form and a given gradient g on
+        the CSR values, and dL/dkappa_cq = sum_kl G^c_kl dA^c_kl/dkappa_cq with
+        dA^c_kl/dkappa_cq = w_q grad phi_l(X_q)^T G grad phi_k(X_q) (the element
+        matrix definition, Sec. 3.1; G = |det J| J^-1 J^-T).  A^c is linear in
+        kappa, so L = sum_cq kappa_cq dL/dkappa_cq."""
+        kappa = np.asarray(kappa, np.float64).reshape(self.n_cells, self.n_q)
+        Gc = self.gather_values(g)
+        det, G = mesh_geometry(self.vertices, self.cells)
+        # grad phi_l^T G grad phi_k at every point, contracted with G^c_kl
+        gk = self.weights[None, :] * np.einsum("ckl,slq,cst,tkq->cq", Gc, self.dphi, G, self.dphi, optimize=True)
+        return float(np.sum(kappa * gk)), gk
 
     # linear forms: the action of a form on a known FE function (Algorithm 2) --
     def action(self, kappa, w, form: str, with_magnitude: bool = False):

@@ -203,3 +203,52 @@ def test_adjoint_matches_finite_differences(cell, p):
     # translation invariance and homogeneity of degree d-2
     np.testing.assert_allclose(gx.sum(axis=0), 0.0, atol=1e-12 * np.abs(gx).max())
     assert abs(np.sum(pr.vertices * gx) - (d - 2) * L) <= 1e-11 * max(abs(L), np.abs(gx).max())
+
+
+# ---------------------------------------------------------------------------
+# adjoint of L = sum_e g_e A^g_e (Poisson) for a general gradient g on the CSR values
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("cell,n,p", [("triangle", 3, 2), ("tetrahedron", 2, 2), ("tetrahedron", 1, 3)])
+def test_gather_is_the_transpose_of_the_assembly(cell, n, p):
+    pr = _problem(cell, n, p)
+    rp, ci = pr.csr_pattern()
+    rng = np.random.default_rng(31)
+    A = rng.standard_normal((pr.n_cells, pr.n_phi, pr.n_phi))     # any element matrices
+    g = rng.standard_normal(len(ci))
+    assert abs(g @ pr.assemble(A) - np.sum(pr.gather_values(g) * A)) <= 1e-12 * np.sum(np.abs(A))
+
+
+@pytest.mark.parametrize("cell,p", [("triangle", 2), ("tetrahedron", 2)])
+def test_values_adjoint_rank_one_is_the_quadratic_form_adjoint(cell, p):
+    # g_e = v_i u_j on the slot (i, j) makes sum_e g_e A^g_e = v^T A^g u
+    pr = _problem(cell, 2, p)
+    kap = inputs.lognormal_kappa(pr.n_cells, pr.n_q, 32)
+    u = inputs.gaussian_vector(pr.n_dofs, 33).astype(np.float64)
+    v = inputs.gaussian_vector(pr.n_dofs, 34).astype(np.float64)
+    rp, ci = pr.csr_pattern()
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    L, gk = pr.adjoint_stiffness_values(kap, v[rows] * u[ci])
+    L2, gk2, _ = pr.adjoint_stiffness(kap, u, v, want_x=False)
+    assert abs(L - L2) <= 1e-12 * abs(L2)
+    assert np.abs(gk - gk2).max() <= 1e-12 * np.abs(gk2).max()
+
+
+def test_values_adjoint_matches_finite_differences_in_kappa():
+    pr = _problem("tetrahedron", 2, 2)
+    kap = inputs.lognormal_kappa(pr.n_cells, pr.n_q, 35)
+    rp, ci = pr.csr_pattern()
+    g = inputs.gaussian_vector(len(ci), 36).astype(np.float64)
+
+    def L_of(k):
+        return float(g @ pr.assemble(pr.element_matrices(k, "stiffness")))
+
+    L, gk = pr.adjoint_stiffness_values(kap, g)
+    assert abs(L - L_of(kap)) <= 1e-12 * np.sum(np.abs(g))
+    rng = np.random.default_rng(37)
+    for _ in range(6):
+        c, q = rng.integers(pr.n_cells), rng.integers(pr.n_q)
+        kp, km = kap.copy(), kap.copy()
+        kp[c, q] += 1e-3
+        km[c, q] -= 1e-3
+        fd = (L_of(kp) - L_of(km)) / 2e-3
+        assert abs(fd - gk[c, q]) <= 1e-9 * np.abs(gk).max()
