@@ -234,6 +234,20 @@ fe_status fe_action(fe_plan *plan, unsigned forms, fe_precision prec, const doub
 fe_status fe_adjoint(fe_plan *plan, const double *vertices, const double *kappa, const float *u,
                      const float *v, double *g_kappa, double *g_vertices, double *L_out);
 
+/* Adjoint of L = sum_e g_e A^g_e for the stiffness form and a given gradient
+ * g on the CSR values (the backward pass of the assembly; not in the paper):
+ * with G^c_kl = g at the CSR slot of (dof(c,k), dof(c,l)) -- the transpose of
+ * A^g = L D L^T, Sec. 3.3 --
+ *   g_kappa[c][q] = dL/dkappa_cq = w_q sum_kl G^c_kl grad phi_l^T G grad phi_k (X_q),
+ *   g_vertices    = dL/dx (kappa at the quadrature points held fixed),
+ * G = |det J| J^-1 J^-T recomputed from the vertices.  grad_values: device
+ * double [nnz] in the plan's CSR order; vertices, kappa, outputs as for
+ * fe_adjoint (g_kappa / g_vertices / L_out may be NULL).  FP64 on the CUDA
+ * cores, one warp per cell with G^c in shared memory (n_phi^2 doubles: larger
+ * elements than 160 local dofs return FE_ERR_UNSUPPORTED).  Deterministic. */
+fe_status fe_adjoint_values(fe_plan *plan, const double *vertices, const double *kappa, const double *grad_values,
+                            double *g_kappa, double *g_vertices, double *L_out);
+
 /* Allocation-free variant of fe_adjoint; the paper has no counterpart.
  *
  * Some callers may not allocate device memory while they run: applications

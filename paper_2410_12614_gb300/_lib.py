@@ -62,6 +62,7 @@ SIGNATURES = {
     "fe_assemble_host": [_vp, ctypes.c_uint, ctypes.c_int, _vp, _vp, _vp],
     "fe_assemble_elements": [_vp, ctypes.c_uint, ctypes.c_int, _vp, _vp, _vp, _vp],
     "fe_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "fe_adjoint_values": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "fe_action": [_vp, ctypes.c_uint, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "fe_adjoint_noalloc": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "fe_sync_status": [_vp],

@@ -221,6 +221,21 @@ class Plan:
               "fe_adjoint")
         return L, gk, gx
 
+    def adjoint_values(self, kappa, grad_values, vertices=None, want_kappa=True, want_vertices=True, want_L=True):
+        """(L, dL/dkappa, dL/dvertices) for L = sum_e g_e A^g_e (stiffness) with the
+        gradient g (grad_values, [nnz], any float dtype) on the CSR values; FP64."""
+        self._check_dev(kappa, torch.float64, (self.n_cells, self.n_q), "kappa")
+        self._check_dev(vertices, torch.float64, (self.n_vertices, self.d), "vertices")
+        g = grad_values.detach().to(torch.float64).contiguous()
+        if g.device.type != "cuda" or g.numel() != self.nnz:
+            raise ValueError(f"grad_values: expected a CUDA tensor of {self.nnz} values")
+        gk = torch.empty((self.n_cells, self.n_q), dtype=torch.float64, device=self.device) if want_kappa else None
+        gx = torch.empty((self.n_vertices, self.d), dtype=torch.float64, device=self.device) if want_vertices else None
+        L = torch.empty(1, dtype=torch.float64, device=self.device) if want_L else None
+        check(load().fe_adjoint_values(self._h, _ptr(vertices), _ptr(kappa), _ptr(g), _ptr(gk), _ptr(gx), _ptr(L)),
+              "fe_adjoint_values")
+        return L, gk, gx
+
     def adjoint_noalloc(self, kappa, u, v, out_L, out_kappa=None, out_vertices=None, vertices=None):
         """fe_adjoint_noalloc: the adjoint without any device allocation by the
         library; the caller provides every output buffer."""
@@ -317,6 +332,29 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class AssembleStiffness(torch.autograd.Function):
+    """values = assemble(kappa, vertices): the CSR values of the stiffness form
+    (fe_assemble in the given precision).  The backward takes any gradient on
+    the values and returns dL/dkappa and dL/dvertices from the FP64 adjoint
+    fe_adjoint_values (kappa at the quadrature points held fixed when the
+    vertices move), i.e. the gradient of the exact quadrature form."""
+
+    @staticmethod
+    def forward(ctx, kappa, vertices, plan, prec="fp64"):
+        vals = plan.assemble(kappa, forms=("stiffness",), prec=prec, vertices=vertices)["stiffness"]
+        ctx.save_for_backward(kappa, vertices)
+        ctx.plan = plan
+        return vals
+
+    @staticmethod
+    def backward(ctx, grad_values):
+        kappa, vertices = ctx.saved_tensors
+        _, gk, gx = ctx.plan.adjoint_values(kappa, grad_values, vertices=vertices, want_L=False,
+                                            want_kappa=ctx.needs_input_grad[0],
+                                            want_vertices=ctx.needs_input_grad[1])
+        return gk, gx, None, None
 
 
 class QuadraticForm(torch.autograd.Function):

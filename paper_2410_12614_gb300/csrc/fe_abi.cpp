@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "fe_adjoint.h"
 #include "fe_host.h"
 #include "fe_internal.h"
 
@@ -839,6 +840,50 @@ fe_status fe_adjoint(fe_plan *plan, const double *vertices, const double *kappa,
     a.status = plan->status.as<int>();
     mark(plan, 2, true);
     int r = launch_adjoint(a, plan->vinc_ptr.as<int64_t>(), plan->vinc.as<int32_t>(), g_vertices, L_out, plan->stream);
+    if (r < 0) return cuda_fail((cudaError_t)(-r), "adjoint kernel launch");
+    mark(plan, 2, false);
+    plan->last_launches = r;
+    return FE_OK;
+}
+
+fe_status fe_adjoint_values(fe_plan *plan, const double *vertices, const double *kappa, const double *grad_values,
+                            double *g_kappa, double *g_vertices, double *L_out) {
+    g_err.clear();
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (!(plan->form_mask & FE_FORM_STIFFNESS)) return fail(FE_ERR_INVALID_ARG, "plan does not serve stiffness");
+    if (!kappa || !grad_values) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+    if ((size_t)plan->n_phi * plan->n_phi * sizeof(double) > (size_t)200 << 10)
+        return fail(FE_ERR_UNSUPPORTED, "n_phi = %d: the cell's gradient block does not fit shared memory", plan->n_phi);
+    fe_status st;
+    if (g_vertices) {
+        st = ensure_ws(plan->ws_adj_x, sizeof(double) * plan->n_cells * (plan->d + 1) * plan->d, "adjoint workspace");
+        if (st) return st;
+    }
+    st = ensure_ws(plan->ws_adj_L, sizeof(double) * plan->n_cells, "adjoint workspace");
+    if (st) return st;
+    AdjValArgs av{};
+    AdjArgs &a = av.base;
+    a.vertices = vertices ? vertices : plan->vertices.as<double>();
+    a.cells = plan->cells.as<int32_t>();
+    a.n_cells = plan->n_cells;
+    a.n_vertices = plan->n_vertices;
+    a.d = plan->d;
+    a.kappa = kappa;
+    a.weights = plan->weights.as<double>();
+    a.n_q = plan->n_q;
+    a.n_phi = plan->n_phi;
+    a.dphi = plan->dphi.as<double>();
+    a.cell_dofs = plan->cell_dofs.as<int32_t>();
+    a.g_kappa = g_kappa;
+    a.g_cell_x = g_vertices ? plan->ws_adj_x.as<double>() : nullptr;
+    a.L_cell = plan->ws_adj_L.as<double>();
+    a.status = plan->status.as<int>();
+    av.gvals = grad_values;
+    av.row_ptr = plan->row_ptr.as<int64_t>();
+    av.col_idx = plan->col_idx.as<int32_t>();
+    mark(plan, 2, true);
+    const int r = launch_adjoint_values(av, plan->vinc_ptr.as<int64_t>(), plan->vinc.as<int32_t>(), g_vertices, L_out,
+                                        plan->stream);
     if (r < 0) return cuda_fail((cudaError_t)(-r), "adjoint kernel launch");
     mark(plan, 2, false);
     plan->last_launches = r;
