@@ -371,8 +371,111 @@ def run_ours(args, rank, world):
         result["batched_256_meshes"] = run_batch(args)
     if rank == 0 and args.sweep:
         result["degree_sweep"] = run_sweep(args)
+    if rank == 0 and args.configs:
+        result["small_configs"] = run_configs(args)
     return result
 
+
+def run_configs(args):
+    """The two small configurations beside the headline:
+    P1 Laplace in FP64 on 32^2 x 2 triangles (2,048 cells, jitter 0.2h, seed 1,
+    kappa = 1, the 3-point rule): element matrices + CSR, a launch-latency-bound
+    case reported in microseconds per call (eager) and per CUDA-graph replay;
+    the adjoint of the P2 stiffness form on 32^3 x 6 tetrahedra (196,608 cells,
+    kappa lognormal at 27 points, u, v ~ N(0,1) FP32): dL/dkappa, dL/dx and L
+    by fe_adjoint, and the same for a general gradient on the CSR values by
+    fe_adjoint_values, each against its HBM bytes (L2 flushed before each run)."""
+    import torch
+    from paper_2410_12614_gb300 import api, inputs
+    hbm, _ = _peaks()
+    out = {}
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        v, c = inputs.square_mesh(32, 0.2, 1)
+        pts, w = api.quadrature_rule("triangle", 0, family=api._lib.FE_QUAD_TRIANGLE_3POINT)
+        plan = api.Plan("triangle", v, c, 1, pts, w, forms=("stiffness",), precisions=("bf16",), stream=stream)
+        kap = torch.ones((plan.n_cells, plan.n_q), dtype=torch.float64, device="cuda")
+        els = {"stiffness": plan.empty_elements("fp64")}
+        vals = {"stiffness": plan.empty_values("fp64")}
+
+        def call():
+            plan.assemble(kap, forms=("stiffness",), prec="fp64", elements=els, out=vals)
+
+        for _ in range(5):
+            call()
+        plan.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = 200
+        e0.record(stream)
+        for _ in range(n):
+            call()
+        e1.record(stream)
+        stream.synchronize()
+        c1 = {"workload": "P1 Laplace FP64, 32^2 x 2 triangles (2,048 cells, 1,089 dofs, 7,361 nnz), kappa = 1",
+              "us_per_call": e0.elapsed_time(e1) * 1e3 / n, "launches_per_call": plan.last_launches(),
+              "note": "back-to-back calls on one stream, inputs L2-resident: launch-latency bound"}
+        try:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                for _ in range(10):
+                    call()
+            g.replay()
+            stream.synchronize()
+            e0.record(stream)
+            for _ in range(20):
+                g.replay()
+            e1.record(stream)
+            stream.synchronize()
+            c1["us_per_call_graph"] = e0.elapsed_time(e1) * 1e3 / (20 * 10)
+        except Exception as ex:   # capture is reported, not required
+            c1["us_per_call_graph"] = None
+            c1["graph_error"] = str(ex)[:200]
+        out["p1_laplace_fp64"] = c1
+        del plan
+
+        v, c = inputs.cube_mesh(32, 0.15, 7)
+        pts, w = api.quadrature_rule("tetrahedron", 3)
+        plan = api.Plan("tetrahedron", v, c, 2, pts, w, forms=("stiffness",), precisions=("bf16",), stream=stream)
+        kap = torch.from_numpy(inputs.lognormal_kappa(plan.n_cells, plan.n_q, 7)).cuda()
+        u = torch.from_numpy(inputs.gaussian_vector(plan.n_dofs, 8)).cuda()
+        vv = torch.from_numpy(inputs.gaussian_vector(plan.n_dofs, 9)).cuda()
+        gvals = torch.from_numpy(inputs.gaussian_vector(plan.nnz, 10).astype(np.float64)).cuda()
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        nc, nq, nph, nv = plan.n_cells, plan.n_q, plan.n_phi, plan.n_vertices
+        d = 3
+        base = (8 * nq * nc * 2 + 16 * nc + 24 * nv + 4 * nph * nc + 96 * nc * 2 + 16 * nc + 8 * (nv + 1)
+                + 24 * nv + 16 * nc)
+        # FP64 flops per cell and point: the reference gradients (or the block
+        # contraction), their products with K, the kappa gradient and S
+        fl_uv = nc * nq * (4 * nph * d + 6 * d * d + 2 * d)
+        fl_val = nc * nq * (2 * nph * nph * d + 2 * nph * d * d + 4 * d * d)
+        for name, fn, nbytes, flops in (
+                ("adjoint_quadratic_form", lambda: plan.adjoint(kap, u, vv), base + 8 * plan.n_dofs, fl_uv),
+                ("adjoint_values", lambda: plan.adjoint_values(kap, gvals), base + 8 * plan.nnz, fl_val)):
+            for _ in range(2):
+                fn()
+            plan.sync()
+            ts = []
+            for _ in range(7):
+                flush.fill_(1.0)
+                flush.sum()
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                stream.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            out[name] = {"workload": "P2 stiffness adjoint, 32^3 x 6 tetrahedra (196,608 cells), FP64",
+                         "ms": ms, "cells_per_s": nc / (ms / 1e3), "algorithmic_bytes": nbytes,
+                         "achieved_gbs": nbytes / (ms / 1e3) / 1e9, "frac_of_hbm": nbytes / (ms / 1e3) / 1e9 / hbm,
+                         "fp64_flops": flops, "achieved_fp64_tflops": flops / (ms / 1e3) / 1e12,
+                         "bound": "alu", "fp64_peak_tflops": FP64_NOMINAL_TFLOPS,
+                         "frac_of_fp64_peak": flops / (ms / 1e3) / 1e12 / FP64_NOMINAL_TFLOPS}
+    return out
+
+
+# GB300's dense FP64 rate (nominal; the CUDA-core FP64 pipe of this part)
+FP64_NOMINAL_TFLOPS = 1.25
 
 SWEEP_PRECISIONS = ("bf16", "fp16", "tf32", "tf32x3", "e4m3")
 
@@ -651,6 +754,9 @@ def main():
                     help="also time the 256-mesh uneven batch (adds about a minute of plan set-up)")
     ap.add_argument("--sweep", action="store_true",
                     help="also time the element kernels for P1..P8 tetrahedra on 16^3 x 6 in every precision")
+    ap.add_argument("--configs", action="store_true",
+                    help="also time P1 Laplace FP64 (2,048 triangles) and the P2 adjoint on 196,608 tetrahedra")
+    ap.add_argument("--configs-only", action="store_true", help="time only those two configurations")
     ap.add_argument("--sweep-only", action="store_true",
                     help="time only the degree sweep and print it as the JSON line (a profiling entry point)")
     ap.add_argument("--sweep-degrees", default="1,2,3,4,5,6,7,8")
@@ -670,6 +776,12 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
+    if args.configs_only:
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            print(json.dumps({"small_configs": run_configs(args)}))
+        return
     if args.sweep_only:
         if rank == 0:
             import torch
