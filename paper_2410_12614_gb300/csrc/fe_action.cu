@@ -24,9 +24,11 @@
 // pairs of local dofs, both contractions as paired FP32 FMAs (two FMAs per
 // instruction) against the packed table B[q][s][k] of a window of quadrature
 // points in shared memory (every thread reads the same entry: broadcast
-// loads), and the window's kappa block copied to shared memory with all its
-// asynchronous copies in flight at once (rows at an odd pitch: conflict-free
-// reads).  FP64 and larger elements: one warp per cell, lanes over the
+// loads), and w_q z(X_q) of the window formed once per (cell, point) from
+// coalesced 16-byte kappa loads (several rows in flight per warp) and staged
+// transposed at an odd pitch (conflict-free reads).  The paired FMAs keep the
+// FP32 rounding of each product-sum exactly as scalar FMAs.  FP64 and larger
+// elements: one warp per cell, lanes over the
 // quadrature points for grad w and r, lanes over the local dofs for b (the
 // transposed table B_t[s][q][k] keeps those loads coalesced).  The vector
 // assembly sums each dof's cell entries in increasing cell order (the
