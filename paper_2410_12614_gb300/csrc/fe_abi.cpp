@@ -619,12 +619,14 @@ std::map<std::string, int> g_tune_cache;  // "(d,p,n_q,prec,form)" -> N-pass wid
 }  // namespace
 
 // Autotuner for the tile shape of every (cell type, degree, quadrature size,
-// precision, form): the N-pass width of the contraction (how many upper-
-// triangle columns one accumulator holds).  Candidates come from
-// host::np_candidates; each is timed with CUDA events on a sample of this
-// plan's own cells (unit coefficient) and the fastest is kept.  Results are
-// cached per key for the life of the process.  FE_GB300_AUTOTUNE=0 keeps the
-// default shapes.
+// precision, form): the N layout of the contraction when the symmetric pairs
+// need more than one 256-column accumulator (whole rows per pass, or pairs in
+// passes of a given width).  Candidates come from host::np_candidates; each is
+// timed with CUDA events on a sample of this plan's own cells (unit
+// coefficient) -- two full waves of tiles, so that every SM runs as in a
+// production launch, with the L2 flushed before each run -- and the fastest is
+// kept.  Results are cached per key for the life of the process.
+// FE_GB300_AUTOTUNE=0 keeps the default shapes.
 static fe_status autotune_plan(fe_plan &P) {
     const char *env = getenv("FE_GB300_AUTOTUNE");
     if (env && env[0] == '0') return FE_OK;
