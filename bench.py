@@ -719,7 +719,7 @@ def cpu_baseline_all_cores(budget_s, per_cell_1core):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    budget = max(2.0, min(30.0, 120.0 / max(1, args.steps + args.warmup)))
+    budget = getattr(args, "ref_budget_s", None) or max(2.0, min(30.0, 120.0 / max(1, args.steps + args.warmup)))
     times, val = [], None
     for i in range(args.warmup + args.steps):
         r = cpu_baseline(args, budget_s=budget)
