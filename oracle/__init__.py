@@ -24,8 +24,9 @@ element kernels and assembly"):
   form on a known FE function, b = sum_s B_s r_s) and v^g = L b (Sec. 3.3).
 * ``Problem.gather_values`` / ``adjoint_stiffness_values`` -- the transpose of
   the assembly and dL/dkappa for L = sum_e g_e A^g_e (calculus on Sec. 3.1).
-* ``error_bound`` -- the per-cell bound of Theorem 4.8 / Corollary 4.10 in
-  the form used by the tests (see its docstring).
+* ``error_bound`` / ``subnormal_term`` -- the per-cell bound of Theorem 4.8 /
+  Corollary 4.10 in the form used by the tests, written out to all orders
+  with the gradual-underflow terms of narrow formats (see their docstrings).
 
 Everything is FP64; nothing is tuned.
 """
@@ -486,18 +487,89 @@ class Problem:
 # Error bounds (Theorem 4.8 / Corollary 4.10, Corollary 4.11)
 # --------------------------------------------------------------------------
 def error_bound(kq, u_s: float, K: int, u_acc: float = 2.0 ** -23, u_out: float = 2.0 ** -24,
-                storage_roundings: int = 2):
+                storage_roundings: int = 2, u_pre: float = 0.0, abs_rel=0.0):
     """Per-cell relative max-norm bound for a reduced-precision contraction.
 
-        err_c <= (r u_s + gamma_K(2 u_acc)) kappa_q^A(c) + u_out
+        err_c <= rho kappa_q^A(c) + gamma_K(2 u_acc) (1 + rho) kappa_q^A(c) + u_out + abs_rel(c),
+        rho    = (1 + u_s)^r (1 + u_pre) - 1.
 
-    with r the number of operand roundings to storage (C and the tabulated
-    operand: r = 2), gamma_K(x) = K x / (1 - K x) the accumulation constant
-    over the contraction length K (Lemma 2.2 / matrix-product bound, Sec. 2),
-    the accumulation roundoff doubled to allow truncating (round-toward-zero)
-    accumulation, and u_out the rounding of the FP32 output.  This is the
-    bound of Corollary 4.10 with u_g = u_p ~ 0 (FP64 geometry and tabulation).
+    Derivation (Theorem 4.8 / Corollary 4.10 with u_g = u_p ~ 0, FP64
+    geometry and tabulation, written out to all orders): every product of the
+    contraction is fl(C_i) fl(P_i) with fl(x) = x (1 + delta) + eta, |delta| <=
+    u_s for a normal result and |eta| <= half the subnormal spacing otherwise
+    (only one of the two is nonzero).  For normal operands a product then
+    carries the relative error (1 + u_s)^2 - 1 = 2 u_s + u_s^2 (r = 2: C and
+    the tabulated operand; the u_s^2 term matters for e4m3, u_s = 2^-4).
+    u_pre is the relative error C already carries before its storage rounding
+    (a coefficient window and a geometry factor formed in FP32).  The products'
+    sum over K terms in FP32 adds gamma_K(2 u_acc) times the sum of the rounded
+    products' magnitudes (<= (1 + rho) sum |C||P|), the accumulation roundoff
+    doubled to allow truncating accumulation; u_out is the FP32 store.
+    sum_i |C_i||P_i| over the folded pairs is at most sum_st |B_s||C_st||B_t|^T,
+    the numerator of kappa_q^A, so each term is relative to ||A^c||_max through
+    kappa_q^A(c).  abs_rel(c) (see subnormal_term) carries the eta terms of
+    operands that fall into gradual underflow, relative to ||A^c||_max.
     """
     x = K * 2.0 * u_acc
     gamma = x / (1.0 - x)
-    return (storage_roundings * u_s + gamma) * np.asarray(kq) + u_out
+    rho = (1.0 + u_s) ** storage_roundings * (1.0 + u_pre) - 1.0
+    kq = np.asarray(kq)
+    return rho * kq + gamma * (1.0 + rho) * kq + u_out + np.asarray(abs_rel)
+
+
+def operand_magnitudes(problem, form: str):
+    """Plan-level magnitudes of the tabulated operand (Sec. 3.1, B_s = the
+    reference derivatives, mass: the basis values):
+    Pi_max = max_kl sum_q (sum_s |B_skq|)(sum_t |B_tlq|), which bounds
+    sum over the folded pairs (s <= t) and points of |B_skq B_tlq + [s != t] B_tkq B_slq|,
+    and Bmax = max |B_skq|, so that every folded entry is at most
+    n_f Bmax^2 (n_f = 2 for the stiffness form, 1 for the mass form)."""
+    B = problem.dphi if form == "stiffness" else problem.phi[None]
+    b = np.abs(B).sum(axis=0)                        # [n_phi, n_q]: sum_s |B_skq|
+    return float((b @ b.T).max()), float(np.abs(B).max())
+
+
+def subnormal_term(problem, kappa, form: str, A, mbits: int, emin: int, target: int, cell_ids=None):
+    """abs_rel(c) of error_bound for a storage format with `mbits` explicit
+    mantissa bits and smallest normal exponent `emin`, whose operands are
+    brought by powers of two to the binade [2^(target-1), 2^target) (per cell
+    for C: max_q|w_q kappa_cq| max_st|G_st|, mass |det J|; once for the
+    tabulated operand: its largest entry; target = 1: no scaling).
+
+    A value rounded in gradual underflow has absolute error at most
+    h = 2^(emin - mbits - 1) in scaled units.  The scale 2^e puts the scale's
+    magnitude M (computed by the kernels in FP32) in [2^(target-1), 2^target),
+    so 2^-e <= M 2^(1 - target) up to that FP32 rounding; with a factor two to
+    spare, unscaled a_C = h 2^(2 - target) M_c for C (M_c the exact magnitude;
+    without scaling a_C = h) and a_P = h 2^(2 - target) n_f Bmax^2 for the
+    operand.
+    Per entry (k, l) the eta terms add at most
+    (1 + u_s) (a_C Pi_kl + a_P sum_i |C_i|) + K a_C a_P; their maximum over
+    (k, l), divided by ||A^c||_max, is returned per cell (A: the exact element
+    matrices of the cells, in the order of cell_ids)."""
+    kappa = np.asarray(kappa, np.float64).reshape(-1, problem.n_q)
+    cells = problem.cells if cell_ids is None else problem.cells[np.asarray(cell_ids)]
+    if cell_ids is not None:
+        kappa = kappa[np.asarray(cell_ids)]
+    det, G = mesh_geometry(problem.vertices, cells)
+    wk = np.abs(problem.weights[None, :] * kappa)                        # |w_q kappa_cq|
+    d = problem.d
+    if form == "stiffness":
+        Gs = np.stack([np.abs(G[:, s, t]) for s in range(d) for t in range(s, d)], axis=1)
+        M = wk.max(axis=1) * Gs.max(axis=1)
+        SC = wk.sum(axis=1) * Gs.sum(axis=1)
+        K = problem.n_q * d * (d + 1) // 2
+        n_f = 2.0
+    else:
+        M = wk.max(axis=1) * np.abs(det)
+        SC = wk.sum(axis=1) * np.abs(det)
+        K = problem.n_q
+        n_f = 1.0
+    pi_max, bmax = operand_magnitudes(problem, form)
+    h = 2.0 ** (emin - mbits - 1)
+    a_C = h * 2.0 ** (2 - target) * M if target > 1 else np.full_like(M, h)
+    a_P = h * 2.0 ** (2 - target) * n_f * bmax ** 2 if target > 1 else h
+    u_s = 2.0 ** -(mbits + 1)
+    S = (1.0 + u_s) * (a_C * pi_max + a_P * SC) + K * a_C * a_P
+    amax = np.abs(np.asarray(A)).reshape(len(M), -1).max(axis=1)
+    return S / amax

@@ -30,6 +30,8 @@ and the geometry factor G32 formed from the FP64 cofactor matrix C of J
 
     BF16, FP16, TF32, e4m3:  c32 = RN_32(C), a32 = RN_32(|det J|),
                              G32_st = fl32( fma32(c0s, c0t, fma32(c1s, c1t, fl32(c2s c2t))) * fl32(1 / a32) )
+                             (a cell whose off-diagonal sums cancel by more than a
+                             factor 16 takes the TF32x3 form; see geometry32)
     TF32x3:                  G32_st = RN_32( sum_i C_is C_it / |det J| )  (FP64 first)
 
 (mass: G32 = a32).  TF32x3 splits both operands into TF32 hi and lo parts and
@@ -114,25 +116,42 @@ def cofactors(vertices, cells):
 
 
 def geometry32(vertices, cells, g64: bool):
-    """G32 [nc, n_pairs] in the pair order (s <= t) and |det J| in FP32."""
+    """G32 [nc, n_pairs] in the pair order (s <= t) and |det J| in FP32.
+
+    FP32 cells: G32 from the rounded cofactors as in the module docstring,
+    except that a cell where some off-diagonal pair cancels -- the FP32 sum
+    m_st = fma32(|c0s|,|c0t|, fma32(|c1s|,|c1t|, |fl32(c2s c2t)|)) of the
+    magnitudes exceeding 16 |acc_st| (an exact zero counts) -- takes the FP64
+    G rounded once, as the TF32x3 cells do (the kernels' guard against
+    sheared cells, whose FP32 off-diagonals would lose their relative
+    accuracy)."""
     _, C, det = cofactors(vertices, cells)
     d = C.shape[1]
     adet = np.abs(det)
+    G64 = np.stack([np.einsum("ci,ci->c", C[:, :, s], C[:, :, t]) / adet for s, t in pairs(d)], axis=1)
     if g64:
-        G = np.stack([np.einsum("ci,ci->c", C[:, :, s], C[:, :, t]) / adet for s, t in pairs(d)], axis=1)
-        return f32(G), f32(adet)
+        return f32(G64), f32(adet)
     c32 = f32(C)
     a32 = f32(adet)
     inv = (np.float32(1.0) / a32).astype(np.float32)
     out = []
+    cancel = np.zeros(C.shape[0], dtype=bool)
     for s, t in pairs(d):
         if d == 3:
             acc = fma32(c32[:, 1, s], c32[:, 1, t], (c32[:, 2, s] * c32[:, 2, t]).astype(np.float32))
+            mag = fma32(np.abs(c32[:, 1, s]), np.abs(c32[:, 1, t]),
+                        np.abs((c32[:, 2, s] * c32[:, 2, t]).astype(np.float32)))
         else:
             acc = (c32[:, 1, s] * c32[:, 1, t]).astype(np.float32)
+            mag = np.abs(acc)
         acc = fma32(c32[:, 0, s], c32[:, 0, t], acc)
+        mag = fma32(np.abs(c32[:, 0, s]), np.abs(c32[:, 0, t]), mag)
+        if s != t:
+            cancel |= ~(mag <= np.float32(16.0) * np.abs(acc))
         out.append((acc * inv).astype(np.float32))
-    return np.stack(out, axis=1), a32
+    G = np.stack(out, axis=1)
+    G[cancel] = f32(G64[cancel])
+    return G, a32
 
 
 def operand_P(problem, form: str):

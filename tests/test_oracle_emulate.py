@@ -74,18 +74,47 @@ def test_exact_mode_is_the_literal_oracle(cell, n, p):
 
 @pytest.mark.parametrize("cell,n,p", CASES)
 def test_rounded_operands_within_the_bound(cell, n, p):
+    """The emulated operands (FP64 sums, so no accumulation error) within the
+    derived bound of oracle.error_bound with gamma = 0: (1+u)^r (1+u_pre) - 1
+    times kappa_q^A plus the gradual-underflow term."""
+    from gpu_util import FORMAT, ROUNDINGS, U_PRE, U_S
     ref, kap = _problem(cell, n, p, 40 + p)
-    u_s = {"bf16": 2.0 ** -8, "fp16": 2.0 ** -11, "tf32": 2.0 ** -11, "tf32x3": 2.0 ** -21, "e4m3": 2.0 ** -4}
     for form in ("stiffness", "mass"):
         A = ref.element_matrices(kap, form)
         kq = ref.kappa_q(kap, form, A)
         for prec in ("bf16", "fp16", "tf32", "tf32x3", "e4m3"):
             E, _, K, _ = emulate.element_matrices(ref, kap, form, prec)
             err = np.abs(E - A).reshape(len(A), -1).max(1) / np.abs(A).reshape(len(A), -1).max(1)
-            r = 4 if prec == "e4m3" else 2
-            # no accumulation error here (FP64 sums): only the operand roundings and the FP32 factor
-            bnd = (r * u_s[prec] + 8 * 2.0 ** -24) * kq
-            assert np.all(err <= bnd), (form, prec, float(err.max()))
+            sub = oracle.subnormal_term(ref, kap, form, A, *FORMAT[prec])
+            bnd = oracle.error_bound(kq, U_S[prec], K, u_acc=0.0, u_out=0.0, storage_roundings=ROUNDINGS[prec],
+                                     u_pre=U_PRE[prec], abs_rel=sub)
+            assert np.all(err <= bnd), (form, prec, float((err / bnd).max()))
+
+
+def test_gradual_underflow_needs_the_absolute_term():
+    """In e4m3 (3 mantissa bits, smallest normal 2^-6, subnormal spacing 2^-9)
+    a value in gradual underflow is rounded with an absolute error up to half
+    the spacing, 2^-10, which relative to the value can exceed u = 2^-4 many
+    times over: fl(1.4 * 2^-9) = 2^-9.  A contraction whose products fall
+    there breaks the bound without the absolute term of subnormal_term and
+    keeps it with that term."""
+    mbits, emin, maxf = emulate.FORMATS["e4m3"]
+    u, h = 2.0 ** -4, 2.0 ** (emin - mbits - 1)
+    x = np.array([1.4, 1.6, 2.7, 3.5, 5.5]) * 2.0 ** -9
+    r = emulate.round_format(x, mbits, emin, maxf)
+    assert np.all(np.abs(r - x) <= h) and np.any(np.abs(r - x) > u * np.abs(x))
+    # sum_i fl(C_i) fl(P_i): C normal (scaled to [2^7, 2^8)), P entries of one
+    # column in gradual underflow
+    rng = np.random.default_rng(3)
+    C = rng.uniform(128, 256, 64)
+    P = rng.uniform(1.1, 1.45, 64) * 2.0 ** -9
+    exact = np.sum(C * P)
+    got = np.sum(emulate.round_format(C, mbits, emin, maxf) * emulate.round_format(P, mbits, emin, maxf))
+    rho = (1 + u) ** 2 - 1
+    mag = np.sum(np.abs(C) * np.abs(P))
+    assert abs(got - exact) > rho * mag                                  # the relative terms alone fail
+    a_P = h                                                              # P unscaled: its eta bound
+    assert abs(got - exact) <= rho * mag + (1 + u) * a_P * np.sum(np.abs(C))
 
 
 def test_fp32_geometry_factor_close_to_fp64():

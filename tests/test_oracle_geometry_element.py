@@ -203,3 +203,37 @@ def test_kappa_q_p1_mass_is_one_and_at_least_one():
     for form in ("stiffness", "mass"):
         A = pr3.element_matrices(kap3, form)
         assert np.all(pr3.kappa_q(kap3, form, A) >= 1.0 - 1e-14)
+
+
+def _golden_kq():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "kappa_q_closed_forms.json")) as f:
+        return json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _golden_kq(), ids=lambda c: c["name"])
+def test_kappa_q_closed_forms(case):
+    """kappa_q^A of Corollary 4.10 for the stiffness form equals hand-derived
+    values on cells whose G has nonzero off-diagonal entries (a dropped |.| on
+    G, dropped off-diagonal pairs or a wrong index in the oracle change it);
+    translating and scaling the cell leaves it unchanged."""
+    d = 3 if case["cell_type"] == "tetrahedron" else 2
+    xv = np.array(case["vertices"], dtype=np.float64)
+    cells = np.arange(d + 1, dtype=np.int32)[None, :]
+    p = case["degree"]
+    if "rule" in case:
+        pts, wts = oracle.strang_fix_3()
+    else:
+        pts, wts = oracle.rule_for_degree(case["cell_type"], 2)
+    rng = np.random.default_rng(7)
+    for shift, scale in ((0.0, 1.0), (3.25, 0.125), (-1.5, 7.0)):
+        v = shift + scale * xv
+        pr = oracle.Problem(v, cells, p, pts, wts)
+        if case["kappa"] == 1.0:
+            kap = np.ones((1, pr.n_q))
+        else:
+            kap = np.exp(rng.standard_normal((1, pr.n_q)))
+        A = pr.element_matrices(kap, "stiffness")
+        kq = pr.kappa_q(kap, "stiffness", A)
+        np.testing.assert_allclose(kq, case["kappa_q"], rtol=1e-13)
+        for wrong in case["wrong_if"].values():
+            assert abs(kq[0] - wrong) > 0.1
