@@ -159,6 +159,25 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
                          unsigned form_mask, unsigned prec_mask, void *cuda_stream);
 fe_status fe_plan_destroy(fe_plan *plan);
 fe_status fe_plan_set_stream(fe_plan *plan, void *cuda_stream);
+/* Limit on how long one bounded wait inside this plan's kernels (the
+ * pipeline barriers of the persistent tensor-core kernel) may see no
+ * progress before the kernel gives up: it then stops issuing work, lets its
+ * copies and MMAs in flight finish, releases its tensor memory and returns,
+ * and the call reports FE_ERR_TIMEOUT through fe_sync_status (outputs are
+ * then incomplete; the plan stays usable and the next call starts afresh).
+ * The limit applies to each wait from its own start, not to a whole launch,
+ * so a long launch whose waits all complete never trips it.  limit_ns = 0
+ * restores the default of 2 s.  A batch uses the largest limit of its plans
+ * at creation.  Not an error path a healthy GPU takes: it exists so that a
+ * stalled pipeline ends with an error instead of hanging the device. */
+fe_status fe_plan_set_wait_limit(fe_plan *plan, uint64_t limit_ns);
+/* Device memory the plan holds, in bytes: plan_bytes for what plan creation
+ * allocated (mesh, tabulations, operand images, dof map, pattern, assembly
+ * streams, action tables built so far), workspace_bytes for the workspaces
+ * that compute calls allocate on first use and keep (element matrices,
+ * coefficient windows, copies of host buffers, adjoint scratch).  Host only;
+ * any output pointer may be NULL. */
+fe_status fe_plan_memory(const fe_plan *plan, int64_t *plan_bytes, int64_t *workspace_bytes);
 /* Any output pointer may be NULL. */
 fe_status fe_plan_sizes(const fe_plan *plan, int64_t *n_cells, int64_t *n_vertices, int64_t *n_dofs,
                         int64_t *nnz, int32_t *n_phi, int32_t *n_q);

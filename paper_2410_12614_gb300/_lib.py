@@ -54,6 +54,8 @@ SIGNATURES = {
                        ctypes.POINTER(FeQuadrature), ctypes.c_uint, ctypes.c_uint, _vp],
     "fe_plan_destroy": [_vp],
     "fe_plan_set_stream": [_vp, _vp],
+    "fe_plan_set_wait_limit": [_vp, ctypes.c_uint64],
+    "fe_plan_memory": [_vp, _pi64, _pi64],
     "fe_plan_sizes": [_vp, _pi64, _pi64, _pi64, _pi64, _pi32, _pi32],
     "fe_csr_pattern": [_vp, _vp, _vp],
     "fe_cell_dofs": [_vp, _vp],

@@ -245,11 +245,23 @@ class Plan:
         self._check_dev(out_L, torch.float64, (1,), "out_L")
         self._check_dev(out_kappa, torch.float64, (self.n_cells, self.n_q), "out_kappa")
         self._check_dev(out_vertices, torch.float64, (self.n_vertices, self.d), "out_vertices")
+        self._check_dev(vertices, torch.float64, (self.n_vertices, self.d), "vertices")
         check(load().fe_adjoint_noalloc(self._h, _ptr(vertices), _ptr(kappa), _ptr(u), _ptr(v), _ptr(out_kappa),
                                         _ptr(out_vertices), _ptr(out_L)), "fe_adjoint_noalloc")
 
     def sync(self):
         check(load().fe_sync_status(self._h), "fe_sync_status")
+
+    def set_wait_limit(self, limit_ns: int = 0):
+        """fe_plan_set_wait_limit: the longest one bounded wait inside the
+        plan's kernels may see no progress (0 restores the default)."""
+        check(load().fe_plan_set_wait_limit(self._h, int(limit_ns)), "fe_plan_set_wait_limit")
+
+    def memory(self):
+        """(plan_bytes, workspace_bytes) of device memory the plan holds (fe_plan_memory)."""
+        pb, wb = ctypes.c_int64(), ctypes.c_int64()
+        check(load().fe_plan_memory(self._h, ctypes.byref(pb), ctypes.byref(wb)), "fe_plan_memory")
+        return pb.value, wb.value
 
     def enable_timing(self, on=True):
         check(load().fe_plan_enable_timing(self._h, int(on)))

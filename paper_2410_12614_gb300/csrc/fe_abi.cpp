@@ -1,6 +1,7 @@
 // C ABI of the library: plan lifecycle, argument validation, device memory
 // owned by plans, kernel launches and the status / error conventions of
 // fe_gb300.h.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -49,6 +50,10 @@ fe_status cuda_fail(cudaError_t e, const char *what) {
 int form_index(unsigned form) { return form == FE_FORM_STIFFNESS ? 0 : 1; }
 
 bool supported_degree(int d, int p) { return p >= 1 && ((d == 3 && p <= 8) || (d == 2 && p <= 10)); }
+
+// Default limit on how long one bounded wait inside a kernel may see no
+// progress before the kernel gives up (fe_plan_set_wait_limit).
+constexpr unsigned long long kDefaultWaitLimitNs = 2000000000ull;
 
 }  // namespace
 
@@ -102,6 +107,8 @@ struct fe_plan {
     std::vector<double> h_phi, h_dphi;   // FP64 tabulation kept for re-packing operands
     std::vector<int> col_of_sym;         // operand column of each pair (k <= l)
     int tuned_np[6][2] = {};             // autotuned N-pass width per precision and form
+    unsigned long long wait_limit_ns = kDefaultWaitLimitNs;   // no-progress limit of every bounded kernel wait
+    float act_rbound[2] = {0.f, 0.f};    // FP16 action scaling bounds (ActArgs::r_bound)
     ~fe_plan() {
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
@@ -299,6 +306,24 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
 
     P.h_phi = phi;
     P.h_dphi = dphi;
+    {
+        // a-priori bounds of the FP16 action's r_s (ActArgs::r_bound): the largest
+        // weight times max_{s,q} sum_k |B_skq| times 2^ACT_W_TARGET
+        double wmax = 0.0, bs = 0.0, bm = 0.0;
+        for (int q = 0; q < P.n_q; ++q) {
+            wmax = std::max(wmax, std::fabs(rule->weights[q]));
+            double m = 0.0;
+            for (int k = 0; k < P.n_phi; ++k) m += std::fabs(phi[(size_t)k * P.n_q + q]);
+            bm = std::max(bm, m);
+            for (int sd = 0; sd < d; ++sd) {
+                double g = 0.0;
+                for (int k = 0; k < P.n_phi; ++k) g += std::fabs(dphi[((size_t)sd * P.n_phi + k) * P.n_q + q]);
+                bs = std::max(bs, g);
+            }
+        }
+        P.act_rbound[0] = (float)std::ldexp(wmax * bs, ACT_W_TARGET);
+        P.act_rbound[1] = (float)std::ldexp(wmax * bm, ACT_W_TARGET);
+    }
     for (int prec = 1; prec <= 5; ++prec) {
         if (!(prec_mask & FE_PREC_MASK(prec))) continue;
         for (unsigned form : {(unsigned)FE_FORM_STIFFNESS, (unsigned)FE_FORM_MASS}) {
@@ -328,6 +353,33 @@ fe_status fe_plan_destroy(fe_plan *plan) {
 fe_status fe_plan_set_stream(fe_plan *plan, void *stream) {
     if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
     plan->stream = static_cast<cudaStream_t>(stream);
+    return FE_OK;
+}
+
+fe_status fe_plan_memory(const fe_plan *plan, int64_t *plan_bytes, int64_t *workspace_bytes) {
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    const fe_plan &P = *plan;
+    const DevBuf *ws[] = {&P.ws_elem[0], &P.ws_elem[1], &P.ws_kappa, &P.ws_csr[0], &P.ws_csr[1], &P.ws_adj_x,
+                          &P.ws_adj_L, &P.ws_Lsum, &P.ws_win, &P.ws_cellf, &P.ws_act_b[0], &P.ws_act_b[1]};
+    int64_t w = 0;
+    for (const DevBuf *b : ws) w += (int64_t)b->bytes;
+    int64_t t = 0;
+    const DevBuf *own[] = {&P.vertices, &P.cells, &P.weights, &P.cell_dofs, &P.row_ptr, &P.col_idx, &P.inc_ptr,
+                           &P.inc_elem, &P.vinc_ptr, &P.vinc, &P.contrib_cnt, &P.contrib_base, &P.contrib_code,
+                           &P.contrib_dest, &P.chunk_desc, &P.phi, &P.dphi, &P.sym_kl, &P.full2sym, &P.status};
+    for (const DevBuf *b : own) t += (int64_t)b->bytes;
+    for (int i = 0; i < 6; ++i)
+        for (int f = 0; f < 2; ++f) t += (int64_t)(P.img[i][f].bytes + P.act_tab[i][f].bytes + P.act_tab_t[i][f].bytes);
+    for (int i = 0; i < 6; ++i)
+        for (int f = 0; f < 3; ++f) t += (int64_t)P.act_packed[i][f].bytes;
+    if (plan_bytes) *plan_bytes = t;
+    if (workspace_bytes) *workspace_bytes = w;
+    return FE_OK;
+}
+
+fe_status fe_plan_set_wait_limit(fe_plan *plan, uint64_t limit_ns) {
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    plan->wait_limit_ns = limit_ns ? (unsigned long long)limit_ns : kDefaultWaitLimitNs;
     return FE_OK;
 }
 
@@ -396,7 +448,7 @@ fe_status fe_sync_status(fe_plan *plan) {
     if (st & ST_TIMEOUT) return fail(FE_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
     if (st & ST_NONFINITE) return fail(FE_ERR_NONFINITE, "non-finite geometry or coefficient");
     if (st & ST_DEGENERATE) return fail(FE_ERR_DEGENERATE_CELL, "degenerate cell (det J == 0)");
-    if (st & ST_SATURATED) return fail(FE_ERR_NONFINITE, "e4m3 operand saturated");
+    if (st & ST_SATURATED) return fail(FE_ERR_NONFINITE, "a reduced-precision value overflowed its storage format");
     return FE_OK;
 }
 
@@ -465,7 +517,7 @@ static TcSeg make_tc_seg(fe_plan *P, unsigned forms, int prec, const double *ver
 
 // Global launch shape over the segments: operand maxima, then the staged
 // epilogue for every segment that fits (greedy, in segment order).
-static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status) {
+static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status, unsigned long long wait_limit_ns) {
     a.prec = prec;
     a.elem_bytes = host::format_of(prec).elem_bytes;
     a.idesc = idesc_for(prec);
@@ -492,7 +544,7 @@ static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status) {
         }
     }
     a.status = status;
-    a.timeout_ns = 2000000000ull;  // 2 s per CTA (a tile needs far less)
+    a.timeout_ns = wait_limit_ns;  // per wait, counted from the wait's start
 }
 
 static AsmSeg make_asm_seg(fe_plan *P, unsigned forms, const void *const A[2], void *const csr[2]) {
@@ -555,7 +607,7 @@ static fe_status run_elements(fe_plan *P, unsigned forms, fe_precision prec, con
         a.seg0 = make_tc_seg(P, forms, prec, verts, kappa, A, P->ws_win.as<float>(), P->ws_cellf.as<float>());
         a.segs = nullptr;
         a.n_segs = 1;
-        tc_finalize(a, &a.seg0, 1, prec, P->status.as<int>());
+        tc_finalize(a, &a.seg0, 1, prec, P->status.as<int>(), P->wait_limit_ns);
         const size_t smem = tc_smem_bytes(a);
         mark(P, 3, true);
         int r = launch_factor(a, P->stream);
@@ -679,7 +731,7 @@ static fe_status autotune_plan(fe_plan &P) {
                                          cellf.as<float>());
                     a.seg0.n_cells = n;
                     a.n_segs = 1;
-                    tc_finalize(a, &a.seg0, 1, prec, P.status.as<int>());
+                    tc_finalize(a, &a.seg0, 1, prec, P.status.as<int>(), kDefaultWaitLimitNs);
                     const size_t smem = tc_smem_bytes(a);
                     {
                         const int r = launch_factor(a, P.stream);
@@ -984,6 +1036,8 @@ fe_status fe_action(fe_plan *plan, unsigned forms, fe_precision prec, const doub
     a.weights = plan->weights.as<double>();
     a.w = w;
     a.status = plan->status.as<int>();
+    a.r_bound[0] = plan->act_rbound[0];
+    a.r_bound[1] = plan->act_rbound[1];
     int launches = 0;
     if (action_per_cell(plan->d, plan->n_phi, fp64)) {
         // every requested form in one launch
@@ -1216,7 +1270,9 @@ fe_status fe_batch_create(fe_batch **out, fe_plan *const *plans, int n_plans, un
     }
     if (!fp64) {
         TcArgs &a = B.targs;
-        tc_finalize(a, tsegs.data(), (int)tsegs.size(), (int)prec, B.status.as<int>());
+        unsigned long long limit = 0;
+        for (fe_plan *P : B.plans) limit = std::max(limit, P->wait_limit_ns);
+        tc_finalize(a, tsegs.data(), (int)tsegs.size(), (int)prec, B.status.as<int>(), limit);
         FE_CUDA(upload(B.tc_segs, tsegs, B.stream), "upload batch segments");
         a.segs = B.tc_segs.as<TcSeg>();
         a.n_segs = (int)tsegs.size();
@@ -1272,6 +1328,7 @@ fe_status fe_batch_sync(fe_batch *batch) {
     if (st & ST_TIMEOUT) return fail(FE_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
     if (st & ST_NONFINITE) return fail(FE_ERR_NONFINITE, "non-finite geometry or coefficient");
     if (st & ST_DEGENERATE) return fail(FE_ERR_DEGENERATE_CELL, "degenerate cell (det J == 0)");
+    if (st & ST_SATURATED) return fail(FE_ERR_NONFINITE, "a reduced-precision value overflowed its storage format");
     return FE_OK;
 }
 

@@ -14,7 +14,16 @@
 // and w_q z(X_q) in FP32 as for the bilinear forms, r_s computed in FP32 and
 // rounded once to the storage format (the theorem on r_s), and both
 // contractions accumulated in FP32 -- each product of two stored values is
-// exact in FP32, as on the tensor cores.
+// exact in FP32, as on the tensor cores.  FP16's narrow range needs scaling:
+// on a fine mesh r_s (about w_q kappa h^d) falls far below FP16's smallest
+// normal number.  For FP16 each cell's coefficients are rounded as
+// w^c 2^e_w with max|w^c| 2^e_w in [2^7, 2^8), and r_s as r_s 2^(e_w + e_r),
+// where e_r brings the a-priori bound of |r_s / kappa| (largest weight *
+// max_s sum_t |G_st| (mass: |det J|) * max_{s,q} sum_k |B_skq| * 2^8) to
+// [2^3, 2^4); the cell vector is unscaled at the end.  Powers of two are
+// exact, so the rounding errors are those of the unscaled values wherever
+// both are normal numbers; an r_s that still overflows FP16 (kappa above
+// about 4096) sets the saturation status instead of returning infinities.
 //
 // Kernels.  The work is a few tens of flops per byte of kappa, below what the
 // tensor cores need to matter, so it runs on the CUDA cores.  Mixed
@@ -85,6 +94,21 @@ __device__ __forceinline__ float to_f32(double x, int &nonfinite) {
         return __uint_as_float((static_cast<unsigned>(r >> 29) & 0x7FFFFFFFu) | (hi & 0x80000000u));
     }
     return f64_to_f32_rne(x, nonfinite);
+}
+
+// e such that x 2^e lies in [2^(target-1), 2^target) (0 for zero or a
+// non-finite x), clamped to [-120, 120] so that 2^e and 2^-e are normal FP32.
+__device__ __forceinline__ int scale_exp(float x, int target) {
+    if (!(x > 0.f) || !isfinite(x)) return 0;
+    int e;
+    frexpf(x, &e);
+    return min(120, max(-120, target - e));
+}
+
+// Index of G_st in the packed upper triangle (G00 G01 G02 G11 G12 G22; d = 2:
+// G00 G01 G11).
+__device__ __forceinline__ constexpr int sym_index(int d, int s, int t) {
+    return (s <= t) ? s * d - s * (s - 1) / 2 + (t - s) : t * d - t * (t - 1) / 2 + (s - t);
 }
 
 // ---------------------------------------------------------------------------
@@ -170,13 +194,17 @@ action_cells_kernel(const __grid_constant__ ActArgs a) {
     }
     int nonfinite = 0;
     for (int q = tid; q < nq; q += ACT_CELLS) wts_s[q] = f64_to_f32_rne(__ldg(a.weights + q), nonfinite);
+    const bool fp16 = a.prec == FE_PREC_FP16;
+    float unscale[2] = {1.f, 1.f};   // Poisson, mass
     if (live) {
         const int32_t *dofs = a.cell_dofs + c * NPHI;
         float wl[NPHI];
+        float wmax = 0.f;
 #pragma unroll
-        for (int k = 0; k < NPHI; ++k) wl[k] = rnd(to_f32(__ldg(a.w + __ldg(dofs + k)), nonfinite));
-#pragma unroll
-        for (int p = 0; p < NP2; ++p) wp[p] = make_float2(wl[2 * p], 2 * p + 1 < NPHI ? wl[2 * p + 1] : 0.f);
+        for (int k = 0; k < NPHI; ++k) {
+            wl[k] = to_f32(__ldg(a.w + __ldg(dofs + k)), nonfinite);
+            wmax = fmaxf(wmax, fabsf(wl[k]));
+        }
         const int st = cell_g32(a.vertices, a.cells, c, D, g6, adet);
         if (st) {
             atomicOr(a.status, st);
@@ -184,6 +212,31 @@ action_cells_kernel(const __grid_constant__ ActArgs a) {
             for (int j = 0; j < 6; ++j) g6[j] = 0.f;
             adet = 0.f;
         }
+        if (fp16) {
+            const int e_w = scale_exp(wmax, ACT_W_TARGET);
+            const float sw = ldexpf(1.f, e_w);
+#pragma unroll
+            for (int k = 0; k < NPHI; ++k) wl[k] *= sw;
+            float gn = 0.f;
+#pragma unroll
+            for (int s = 0; s < D; ++s) {
+                float row = 0.f;
+#pragma unroll
+                for (int t = 0; t < D; ++t) row += fabsf(g6[sym_index(D, s, t)]);
+                gn = fmaxf(gn, row);
+            }
+            const int e_s = scale_exp(a.r_bound[0] * gn, ACT_R_TARGET);
+            const int e_m = scale_exp(a.r_bound[1] * adet, ACT_R_TARGET);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) g6[j] = ldexpf(g6[j], e_s);
+            adet = ldexpf(adet, e_m);
+            unscale[0] = ldexpf(ldexpf(1.f, -e_w), -e_s);
+            unscale[1] = ldexpf(ldexpf(1.f, -e_w), -e_m);
+        }
+#pragma unroll
+        for (int k = 0; k < NPHI; ++k) wl[k] = rnd(wl[k]);
+#pragma unroll
+        for (int p = 0; p < NP2; ++p) wp[p] = make_float2(wl[2 * p], 2 * p + 1 < NPHI ? wl[2 * p + 1] : 0.f);
     }
     // kappa rows as 16-byte pairs when the rows and the window start are even
     const bool pairs = ((nq & 1) == 0) && ((reinterpret_cast<uintptr_t>(a.kappa) & 15) == 0);
@@ -271,16 +324,19 @@ action_cells_kernel(const __grid_constant__ ActArgs a) {
     if (nonfinite) atomicOr(a.status, ST_NONFINITE);
     // cell vectors: staged, then one contiguous block per CTA and form
     float *out_s = act_sm;
+    bool overflow = false;
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
         if (!(FORMS & (1 << f))) continue;
         __syncthreads();
         if (live) {
             const float2 *bp = f == 0 ? bs : bm;
+            const float us = unscale[f];
 #pragma unroll
             for (int p = 0; p < NP2; ++p) {
-                out_s[tid * OP + 2 * p] = bp[p].x;
-                if (2 * p + 1 < NPHI) out_s[tid * OP + 2 * p + 1] = bp[p].y;
+                overflow = overflow || !isfinite(bp[p].x) || !isfinite(bp[p].y);
+                out_s[tid * OP + 2 * p] = bp[p].x * us;
+                if (2 * p + 1 < NPHI) out_s[tid * OP + 2 * p + 1] = bp[p].y * us;
             }
         }
         __syncthreads();
@@ -290,6 +346,8 @@ action_cells_kernel(const __grid_constant__ ActArgs a) {
             dst[i] = out_s[cl * OP + (i - cl * NPHI)];
         }
     }
+    // an FP16 r_s beyond the format's range (finite inputs, non-finite result)
+    if (fp16 && overflow && !nonfinite) atomicOr(a.status, ST_SATURATED);
 }
 
 // ---------------------------------------------------------------------------
@@ -309,11 +367,24 @@ __global__ void __launch_bounds__(ACT_WARPS * 32) action_kernel(const __grid_con
     const T *__restrict__ Bt = static_cast<const T *>(a.tab_t);   // [nd][nq][nph]
     const int64_t total_warps = (int64_t)gridDim.x * ACT_WARPS;
     for (int64_t c = (int64_t)blockIdx.x * ACT_WARPS + warp; c < a.n_cells; c += total_warps) {
-        // the cell's coefficients (rounded to the storage format on the mixed paths)
+        // the cell's coefficients (rounded to the storage format on the mixed
+        // paths; FP16: scaled by 2^e_w first, see the file comment)
+        const bool fp16 = sizeof(T) == 4 && a.prec == FE_PREC_FP16;
+        float wmax = 0.f;
         for (int k = lane; k < nph; k += 32) {
             const double wv = __ldg(a.w + __ldg(a.cell_dofs + c * nph + k));
-            ws[k] = (sizeof(T) == 8) ? (T)wv : (T)round_storage((float)wv, a.prec);
+            ws[k] = (T)wv;
+            wmax = fmaxf(wmax, fabsf((float)wv));
         }
+        int e_w = 0;
+        if (fp16) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wmax = fmaxf(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+            e_w = scale_exp(wmax, ACT_W_TARGET);
+        }
+        if (sizeof(T) == 4)
+            for (int k = lane; k < nph; k += 32) ws[k] = (T)round_storage(ldexpf((float)ws[k], e_w), a.prec);
+        float unscale = 1.f;
         if (lane == 0) {
             CellGeom geo;
             const int st = cell_geometry(a.vertices, a.cells, c, d, geo);
@@ -326,7 +397,25 @@ __global__ void __launch_bounds__(ACT_WARPS * 32) action_kernel(const __grid_con
                     gs[t * d + s] = g;
                 }
             gs[9] = st ? T(0) : (T)geo.absdet;
+            if (fp16) {
+                float bound;
+                if (nd == 1) {
+                    bound = a.r_bound[1] * (float)gs[9];
+                } else {
+                    float gn = 0.f;
+                    for (int s = 0; s < d; ++s) {
+                        float row = 0.f;
+                        for (int t = 0; t < d; ++t) row += fabsf((float)gs[s * d + t]);
+                        gn = fmaxf(gn, row);
+                    }
+                    bound = a.r_bound[0] * gn;
+                }
+                const int e_r = scale_exp(bound, ACT_R_TARGET);
+                for (int i = 0; i < 10; ++i) gs[i] = (T)ldexpf((float)gs[i], e_r);
+                unscale = ldexpf(ldexpf(1.f, -e_w), -e_r);
+            }
         }
+        unscale = __shfl_sync(0xffffffffu, unscale, 0);
         __syncwarp();
         // grad w (or w) at the quadrature points, then r
         for (int q = lane; q < nq; q += 32) {
@@ -352,12 +441,15 @@ __global__ void __launch_bounds__(ACT_WARPS * 32) action_kernel(const __grid_con
         }
         __syncwarp();
         // b_k = sum_s sum_q B_skq r_sq
+        bool overflow = false;
         for (int k = lane; k < nph; k += 32) {
             T acc = T(0);
             for (int s = 0; s < nd; ++s)
                 for (int q = 0; q < nq; ++q) acc = fma(Bt[((size_t)s * nq + q) * nph + k], rs[s * nq + q], acc);
-            static_cast<T *>(a.b)[c * nph + k] = acc;
+            overflow = overflow || !isfinite((float)acc);
+            static_cast<T *>(a.b)[c * nph + k] = acc * (T)unscale;
         }
+        if (fp16 && overflow) atomicOr(a.status, ST_SATURATED);
         __syncwarp();
     }
 }

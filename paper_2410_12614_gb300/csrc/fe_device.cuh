@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "fe_internal.h"
+#include "fe_wait.h"
 
 namespace fe {
 
@@ -131,10 +132,14 @@ __device__ __forceinline__ float f64_to_f32_rne(double x, int &nonfinite) {
 
 // G = |det J| J^-1 J^-T = C^T C / |det J| (upper triangle: G00 G01 G02 G11
 // G12 G22; d = 2: G00 G01 G11) and |det J| in FP32, formed from the FP64
-// cofactors and determinant rounded once each; a cell whose cofactors or
-// determinant leave FP32's normal range gets G computed in FP64 and rounded
-// once.  Returns the geometry status; on a nonzero status g6 and adet are
-// left as they were.
+// cofactors and determinant rounded once each.  A cell gets G computed in
+// FP64 and rounded once instead when its cofactors or determinant leave
+// FP32's normal range, or when an off-diagonal entry cancels: sum_r |C_rs C_rt|
+// above kG32Cancel |G_st| |det J| (a sheared or needle-shaped cell; an exact
+// zero counts).  The FP32 G therefore carries a relative error of at most
+// about (4 + 2 kG32Cancel) 2^-24 per entry.  Returns the geometry status; on a
+// nonzero status g6 and adet are left as they were.
+constexpr float kG32Cancel = 16.f;
 __device__ __forceinline__ int cell_g32(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
                                         int64_t c, int d, float (&g6)[6], float &adet) {
     CellGeom geo;
@@ -146,19 +151,30 @@ __device__ __forceinline__ int cell_g32(const double *__restrict__ vertices, con
     for (int i = 0; i < 9; ++i) C[i] = f64_to_f32_rne(geo.C[i], nf);
     adet = f64_to_f32_rne(geo.absdet, nf);
     const float inv = 1.0f / adet;
+    bool cancel = false;
     if (d == 3) {
         int j = 0;
 #pragma unroll
         for (int s = 0; s < 3; ++s)
 #pragma unroll
-            for (int u = s; u < 3; ++u)
-                g6[j++] = fmaf(C[s], C[u], fmaf(C[3 + s], C[3 + u], C[6 + s] * C[6 + u])) * inv;
+            for (int u = s; u < 3; ++u) {
+                const float sum = fmaf(C[s], C[u], fmaf(C[3 + s], C[3 + u], C[6 + s] * C[6 + u]));
+                if (u != s) {
+                    const float mag = fmaf(fabsf(C[s]), fabsf(C[u]),
+                                           fmaf(fabsf(C[3 + s]), fabsf(C[3 + u]), fabsf(C[6 + s] * C[6 + u])));
+                    cancel = cancel || !(mag <= kG32Cancel * fabsf(sum));
+                }
+                g6[j++] = sum * inv;
+            }
     } else {
         g6[0] = fmaf(C[0], C[0], C[2] * C[2]) * inv;
-        g6[1] = fmaf(C[0], C[1], C[2] * C[3]) * inv;
+        const float sum = fmaf(C[0], C[1], C[2] * C[3]);
+        const float mag = fmaf(fabsf(C[0]), fabsf(C[1]), fabsf(C[2] * C[3]));
+        cancel = !(mag <= kG32Cancel * fabsf(sum));
+        g6[1] = sum * inv;
         g6[2] = fmaf(C[1], C[1], C[3] * C[3]) * inv;
     }
-    bool fin = nf == 0 && adet > 0.f && isfinite(inv);
+    bool fin = nf == 0 && adet > 0.f && isfinite(inv) && !cancel;
 #pragma unroll
     for (int j = 0; j < 6; ++j) fin = fin && isfinite(g6[j]);
     if (!fin) {
@@ -228,19 +244,17 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
-// A waiting thread is suspended until the phase completes or this many
-// nanoseconds pass (then the caller checks its deadline and waits again), so
-// that waiting warps leave the issue slots to the working ones.
-constexpr uint32_t kWaitSuspendNs = 100000;
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+// A probing thread is suspended until the phase completes or the suspend hint
+// passes (fe_wait.h), so that waiting warps leave the issue slots to the
+// working ones.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(kWaitSuspendNs)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
         : "memory");
     return ok != 0;
 }
@@ -249,18 +263,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Bounded wait on an mbarrier phase; false once the deadline (globaltimer ns) passes.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long deadline) {
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() > deadline) return false;
+// Bounded wait on an mbarrier phase: false once the phase has made no
+// progress for limit_ns nanoseconds since this wait began (wait_expired).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit_ns) {
+    const uint32_t hint = wait_suspend_hint(limit_ns);
+    if (mbar_try_wait(bar, parity, hint)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity, hint)) {
+        if (wait_expired(t0, global_ns(), limit_ns)) return false;
     }
     return true;
 }
 
 // The same, with one outcome for the whole warp (every lane waits; a lane that
 // timed out makes the warp give up), for waits followed by warp-collective code.
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, unsigned long long deadline) {
-    return __all_sync(0xffffffffu, mbar_wait(bar, parity, deadline)) != 0;
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, unsigned long long limit_ns) {
+    return __all_sync(0xffffffffu, mbar_wait(bar, parity, limit_ns)) != 0;
 }
 
 // 1-D bulk copy global -> shared memory, completion counted on an mbarrier.

@@ -185,7 +185,16 @@ struct ActArgs {
     void *b_mass;              // thread-per-cell kernel: the mass form's cell vectors
     int *status;
     int qw;                    // quadrature points per shared-memory window (thread-per-cell kernel)
+    // FP16 range scaling (prec == FE_PREC_FP16 only; see fe_action.cu): per form
+    // (0 Poisson, 1 mass) max_q w_q * max_{s,q} sum_k |B_skq| * 2^ACT_W_TARGET, the
+    // a-priori bound on |r_s| / (kappa * gnorm) (gnorm = max_s sum_t |G_st|, mass: |det J|)
+    float r_bound[2];
 };
+// Target binades of the per-cell scales of the FP16 action: the cell's
+// coefficients to max|w^c| 2^e_w in [2^(W-1), 2^W), the a-priori bound of r_s
+// to [2^(R-1), 2^R) (so r_s stays finite for kappa below 2^(15-R) 65504/2^15).
+constexpr int ACT_W_TARGET = 8;
+constexpr int ACT_R_TARGET = 4;
 
 // Packed action table: floats per segment (one derivative direction, or the
 // basis values, over the local dofs, padded to a multiple of 4) and per

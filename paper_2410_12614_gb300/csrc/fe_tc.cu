@@ -39,8 +39,9 @@
 //              (one 1-D copy per chunk, no multicast) and tcgen05.mma into
 //              one of two 256-column FP32 TMEM accumulators (lane 0 issues).
 // So the build of tile t+1, the MMAs and the stores of tile t overlap.  Every
-// wait is bounded (globaltimer); a timeout sets the status word and all roles
-// leave after in-flight copies and MMAs have drained.
+// wait is bounded (globaltimer): a wait that sees no progress for the launch's
+// limit (timeout_ns, counted from the start of that wait) sets the status word
+// and all roles leave after in-flight copies and MMAs have drained.
 #include <cstdio>
 
 #include "fe_device.cuh"
@@ -122,8 +123,13 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
     constexpr int KIND = (PREC == FE_PREC_E4M3) ? 2 : ((EB == 4) ? 1 : 0);
     constexpr int KCE = TC_CHUNK_BYTES / EB;  // quadrature points per chunk
 
-    // a CTA that starts after another one gave up does no work at all
-    if (*reinterpret_cast<volatile int *>(a.status) & ST_TIMEOUT) return;
+    // a CTA that starts after another one gave up does no work at all: one
+    // thread reads the status word and the whole CTA takes its answer, before
+    // any barrier or warp-collective (.sync.aligned) instruction
+    __shared__ int s_gave_up;
+    if (threadIdx.x == 0) s_gave_up = (*reinterpret_cast<volatile int *>(a.status) & ST_TIMEOUT) != 0;
+    __syncthreads();
+    if (s_gave_up) return;
 
     extern __shared__ uint8_t smem_raw[];
     Smem sm = carve(smem_raw, a);
@@ -159,7 +165,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *sm.tmem_holder;
-    const unsigned long long deadline = global_ns() + a.timeout_ns;
+    const unsigned long long deadline = a.timeout_ns;   // per wait: the longest a wait may see no progress
     volatile int *abort_flag = sm.flags;
 
     if (warp < 4) {
@@ -429,7 +435,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         // drain: every issued MMA finished, every issued bulk copy landed
         if (lane == 0) umma_commit(sm.drain);
         __syncwarp();
-        const unsigned long long drain_deadline = global_ns() + 200000000ull;
+        const unsigned long long drain_deadline = 200000000ull;   // 0.2 s per wait
         mbar_wait(sm.drain, 0, drain_deadline);
         for (int64_t c = mc; c < bc; ++c) mbar_wait(&sm.b_full[c % RING], (uint32_t)((c / RING) & 1), drain_deadline);
     } else if (warp >= W_EPI0 && warp < W_EPI0 + N_EPI) {
@@ -439,12 +445,16 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         // 16h..16h+15 of the lane group when writing out.
         const int g = warp & 3;
         const int h = (warp - W_EPI0) >> 2;
+        __shared__ volatile int pair_ok[8];   // [lane group][half]: outcome of the current pass's waits
         const int pitch = a.pitch_max;
         float *stg = sm.stage + g * 32 * pitch;
         int f2s_reg[MAX_F2S_IT];
         const TcSeg *cur = nullptr;
         int jb = 0;
-        for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
+        // Every decision to stop is taken per pass, after the pass's waits, and
+        // (for staged segments) jointly by the two warps of the lane group.
+        bool stop = false;
+        for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x) {
             const TcSeg &S = seg_of<BATCHED>(a, t);
             const int nph = S.n_phi, nph2 = nph * nph;
             const int n_it = (nph2 + 31) / 32;
@@ -469,8 +479,19 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 const int32_t *__restrict__ s_symkl = S.sym_kl;
                 for (int n = 0; n < op.n_pass; ++n) {
                     const int b = jb & 1, ub = jb >> 1;
-                    if (!mbar_wait_warp(&sm.acc_full[b], ub & 1, deadline) || !mbar_wait_warp(&sm.meta_full[b], ub & 1, deadline)) {
+                    bool ok = !*abort_flag && mbar_wait_warp(&sm.acc_full[b], ub & 1, deadline) &&
+                              mbar_wait_warp(&sm.meta_full[b], ub & 1, deadline);
+                    if (s_staged) {
+                        // the two warps of this lane group meet at named barriers below:
+                        // they take one common outcome here, so that a wait that gave up
+                        // in one of them cannot leave the other alone at a barrier
+                        if (lane == 0) pair_ok[g * 2 + h] = ok ? 1 : 0;
+                        named_bar_sync(1 + g, 64);
+                        ok = pair_ok[g * 2] && pair_ok[g * 2 + 1];
+                    }
+                    if (!ok) {
                         sm.flags[0] = 1;
+                        stop = true;
                         break;
                     }
                     tc_fence_after();
@@ -588,7 +609,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                     }
                     ++jb;
                 }
-                if (*abort_flag) break;
+                if (stop) break;
             }
         }
     }

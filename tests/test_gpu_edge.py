@@ -87,3 +87,39 @@ def test_geometry_outside_fp32_range(scale):
         bnd = cell_bounds(ref, kap, "stiffness", prec, A)
         err = cell_errors(got, A)
         assert np.all(err <= bnd), (prec, float(err.max()))
+
+
+@pytest.mark.parametrize("shape", ["flat", "needle"])
+def test_distorted_cells_all_formats(shape):
+    """Tetrahedra of aspect ratio ~1e4 (a jittered cube mesh squashed along z,
+    or stretched into needles along z): G spans eight orders of magnitude and
+    its off-diagonal entries cancel, which the factor kernel detects and forms
+    in FP64.  Every format must stay within the per-cell bound (the measured
+    error and the bound are printed side by side) and match the
+    emulated-precision operands of oracle/emulate.py to FP32 accumulation."""
+    from oracle import emulate
+    v, c = inputs.structured_mesh("tetrahedron", 3, 0.15, 31)
+    v = v.copy()
+    if shape == "flat":
+        v[:, 2] *= 1e-4
+    else:
+        v[:, :2] *= 1e-4
+    p = 3
+    precs = ("bf16", "fp16", "tf32", "tf32x3", "e4m3")
+    plan, ref = _plan_and_ref("tetrahedron", v, c, p, precs)
+    kap = inputs.lognormal_kappa(plan.n_cells, plan.n_q, 32)
+    kd = cuda(kap)
+    for form in ("stiffness", "mass"):
+        A = ref.element_matrices(kap, form)
+        for prec in precs:
+            got = to_np(plan.element_matrices(kd, forms=(form,), prec=prec)[form])
+            plan.sync()
+            bnd = cell_bounds(ref, kap, form, prec, A)
+            err = cell_errors(got, A)
+            print(shape, form, prec, "max err", float(err.max()), "bound at that cell", float(bnd[err.argmax()]),
+                  "worst err/bound", float((err / bnd).max()))
+            assert np.all(err <= bnd), (shape, form, prec, float((err / bnd).max()))
+            E, M, K, slack = emulate.element_matrices(ref, kap, form, prec)
+            x = K * 2 * 2.0 ** -23
+            tol = x / (1 - x) * M + 2.0 ** -24 * np.abs(E) + slack
+            assert np.all(np.abs(got - E) <= tol), (shape, form, prec, float((np.abs(got - E) / tol).max()))

@@ -54,8 +54,16 @@ def _close(a, b):
 
 def test_noalloc_matches_adjoint_on_two_calls_in_a_row():
     plan, kap, u, vv = _plan(6, (61, 62, 63, 64))
+    # on a fresh plan the allocation-free call comes first: it must leave the
+    # plan's workspaces (where fe_adjoint keeps its scratch) empty
+    _, ws0 = plan.memory()
+    first = _noalloc(plan, kap, u, vv)
+    assert plan.memory()[1] == ws0 == 0
     L0, gk0, gx0 = plan.adjoint(kap, u, vv)
     plan.sync()
+    assert plan.memory()[1] > 0          # fe_adjoint did allocate its scratch
+    for a, b in zip(first, (L0, gk0, gx0)):
+        _close(a, b)
     for _ in range(2):
         L, gk, gx = _noalloc(plan, kap, u, vv)
         _close(L, L0)
@@ -69,6 +77,25 @@ def test_noalloc_matches_adjoint_on_two_calls_in_a_row():
     _close(gxo, gxo0)
     L, gk, gx = _noalloc(plan, kap, u, vv)
     _close(gx, gx0)
+
+
+def test_noalloc_python_wrapper_with_vertex_override():
+    # Plan.adjoint_noalloc (argument checks + the C call) with moved vertices,
+    # against fe_adjoint with the same vertices
+    plan, kap, u, vv = _plan(4, (71, 72, 73, 74))
+    moved = torch.from_numpy(inputs.cube_mesh(4, 0.15, 75)[0]).cuda()
+    L = torch.empty(1, dtype=torch.float64, device="cuda")
+    gk = torch.empty((plan.n_cells, plan.n_q), dtype=torch.float64, device="cuda")
+    gx = torch.empty((plan.n_vertices, 3), dtype=torch.float64, device="cuda")
+    plan.adjoint_noalloc(kap, u, vv, L, gk, gx, vertices=moved)
+    plan.sync()
+    L0, gk0, gx0 = plan.adjoint(kap, u, vv, vertices=moved)
+    plan.sync()
+    _close(L, L0)
+    _close(gk, gk0)
+    _close(gx, gx0)
+    with pytest.raises(ValueError):
+        plan.adjoint_noalloc(kap, u, vv, L, gk, gx, vertices=moved.float())
 
 
 def test_noalloc_rejects_plans_above_capacity():
