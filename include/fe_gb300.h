@@ -295,6 +295,52 @@ fe_status fe_adjoint_noalloc(fe_plan *plan, const double *vertices, const double
                              const float *v, double *g_kappa, double *g_vertices, double *L_out);
 
 /* ---------------------------------------------------------------------- */
+/* Diagnostics: the paper's error studies (Sec. 5.2, 5.3)                  */
+/* ---------------------------------------------------------------------- */
+
+/* Geometry tensor G = |det J| J^-1 J^-T and |det J| of cells [c0, c1)
+ * (Sec. 4.2, the Poisson geometry; Sec. 5.2 studies its rounding error
+ * against the condition number of J).  mode:
+ *   FE_GEOMETRY_FP64   J, cofactors, det J and G in FP64;
+ *   FE_GEOMETRY_FP32   the same formulas exclusively in FP32 from the vertex
+ *                      coordinates rounded to FP32, each operation an IEEE
+ *                      FP32 operation in a fixed order (reproducible bits):
+ *                      J_ij = x_{j+1,i} - x_{0,i}; cofactors C as 2x2 minors
+ *                      fl(fl(a b) - fl(c e)); det = fl(fl(J00 C0 + J01 C1) +
+ *                      J02 C2); G_st = fl(fl(sum_r C_rs C_rt, r increasing) *
+ *                      fl(1 / |det|));
+ *   FE_GEOMETRY_MIXED  the reduced-precision kernels' own path: FP64
+ *                      cofactors and det J, G in FP32, and G in FP64 rounded
+ *                      once on cells whose off-diagonal sums cancel (the
+ *                      per-cell geometry precision of the remark in Sec. 5.2);
+ *                      used_fp64[i] = 1 for those cells.
+ * vertices: device [n_vertices][d] or NULL (the plan's).  G: device double
+ * [c1-c0][d(d+1)/2], pairs (0,0),(0,1),(0,2),(1,1),(1,2),(2,2) (d = 2:
+ * (0,0),(0,1),(1,1)); absdet: device double [c1-c0] or NULL; used_fp64:
+ * device int32 [c1-c0] or NULL (MIXED only).  Asynchronous. */
+enum { FE_GEOMETRY_FP64 = 0, FE_GEOMETRY_FP32 = 1, FE_GEOMETRY_MIXED = 2 };
+fe_status fe_geometry(fe_plan *plan, int mode, const double *vertices, int64_t c0, int64_t c1, double *G,
+                      double *absdet, int32_t *used_fp64);
+
+/* The mass bilinear form and the mass action of cells [c0, c1) with the
+ * matrix-matrix (matrix-vector) products in FP16 and everything else in FP32
+ * (Sec. 5.3: u_s = u_g = u_p = 2^-24, u_q = 2^-11), the experiment that
+ * measures how the accumulation error grows with n_q:
+ *   C_q  = fl32(fl32(w_q kappa_cq) |det J|) 2^e      (|det J| in FP32 from FP32 coordinates)
+ *   H_kq = fl32(C_q phi_kq),   A_kl = 2^-e sum16_q fl16(phi_lq H_kq)
+ *   w_q  = sum32_l fl32(phi_lq w_l 2^f),  r_q = fl32(C_q w_q),
+ *   b_k  = 2^-e 2^-f sum16_q fl16(phi_kq r_q)
+ * with sums over q increasing from 0, sum16 one FP16 rounding per addition,
+ * fl16 one rounding of the exact product, and powers of two per cell (2^e:
+ * sum_q |C_q| 2^e in [2^9, 2^10); 2^f: max|w^c| 2^f in [1, 2)) that keep the
+ * FP16 values in range.  kappa: device [n_cells][n_q]; w: device double
+ * [n_dofs] (needed for b); A: device float [c1-c0][n_phi][n_phi] or NULL; b:
+ * device float [c1-c0][n_phi] or NULL.  One CUDA thread per (cell, k): a
+ * diagnostic, not a fast path.  Asynchronous. */
+fe_status fe_mass_fp16_products(fe_plan *plan, const double *kappa, const double *w, int64_t c0, int64_t c1, float *A,
+                                float *b);
+
+/* ---------------------------------------------------------------------- */
 /* Batches                                                                 */
 /* ---------------------------------------------------------------------- */
 

@@ -115,7 +115,7 @@ def cofactors(vertices, cells):
     return J, C, det
 
 
-def geometry32(vertices, cells, g64: bool):
+def geometry32(vertices, cells, g64: bool, with_mask: bool = False):
     """G32 [nc, n_pairs] in the pair order (s <= t) and |det J| in FP32.
 
     FP32 cells: G32 from the rounded cofactors as in the module docstring,
@@ -130,7 +130,7 @@ def geometry32(vertices, cells, g64: bool):
     adet = np.abs(det)
     G64 = np.stack([np.einsum("ci,ci->c", C[:, :, s], C[:, :, t]) / adet for s, t in pairs(d)], axis=1)
     if g64:
-        return f32(G64), f32(adet)
+        return (f32(G64), f32(adet), np.ones(len(adet), bool)) if with_mask else (f32(G64), f32(adet))
     c32 = f32(C)
     a32 = f32(adet)
     inv = (np.float32(1.0) / a32).astype(np.float32)
@@ -151,7 +151,7 @@ def geometry32(vertices, cells, g64: bool):
         out.append((acc * inv).astype(np.float32))
     G = np.stack(out, axis=1)
     G[cancel] = f32(G64[cancel])
-    return G, a32
+    return (G, a32, cancel) if with_mask else (G, a32)
 
 
 def operand_P(problem, form: str):

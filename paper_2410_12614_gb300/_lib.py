@@ -67,6 +67,8 @@ SIGNATURES = {
     "fe_adjoint_values": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "fe_action": [_vp, ctypes.c_uint, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "fe_adjoint_noalloc": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "fe_geometry": [_vp, ctypes.c_int, _vp, _i64, _i64, _vp, _vp, _vp],
+    "fe_mass_fp16_products": [_vp, _vp, _vp, _i64, _i64, _vp, _vp],
     "fe_sync_status": [_vp],
     "fe_batch_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_int,
                         _vp, _vp, _vp, _vp, _vp, _vp],

@@ -252,6 +252,35 @@ class Plan:
     def sync(self):
         check(load().fe_sync_status(self._h), "fe_sync_status")
 
+    # -- diagnostics (the paper's error studies) -------------------------------
+    GEOMETRY_MODES = {"fp64": 0, "fp32": 1, "mixed": 2}
+
+    def geometry(self, mode="fp64", vertices=None, cells=None):
+        """fe_geometry: (G [n, d(d+1)/2], |det J| [n], used_fp64 [n]) of the
+        cells range(*cells) (default: all) as float64 / int32 CUDA tensors."""
+        self._check_dev(vertices, torch.float64, (self.n_vertices, self.d), "vertices")
+        c0, c1 = cells if cells is not None else (0, self.n_cells)
+        n = c1 - c0
+        G = torch.empty((n, self.d * (self.d + 1) // 2), dtype=torch.float64, device=self.device)
+        ad = torch.empty(n, dtype=torch.float64, device=self.device)
+        used = torch.zeros(n, dtype=torch.int32, device=self.device)
+        check(load().fe_geometry(self._h, self.GEOMETRY_MODES[mode], _ptr(vertices), c0, c1, _ptr(G), _ptr(ad),
+                                 _ptr(used)), "fe_geometry")
+        return G, ad, used
+
+    def mass_fp16_products(self, kappa, w=None, cells=None, matrices=True):
+        """fe_mass_fp16_products: the mass matrices (and, with w, the mass
+        action) of the cells range(*cells) with FP16 products and sums."""
+        self._check_dev(kappa, torch.float64, (self.n_cells, self.n_q), "kappa")
+        self._check_dev(w, torch.float64, (self.n_dofs,), "w")
+        c0, c1 = cells if cells is not None else (0, self.n_cells)
+        n = c1 - c0
+        A = torch.empty((n, self.n_phi, self.n_phi), dtype=torch.float32, device=self.device) if matrices else None
+        b = torch.empty((n, self.n_phi), dtype=torch.float32, device=self.device) if w is not None else None
+        check(load().fe_mass_fp16_products(self._h, _ptr(kappa), _ptr(w), c0, c1, _ptr(A), _ptr(b)),
+              "fe_mass_fp16_products")
+        return A, b
+
     def set_wait_limit(self, limit_ns: int = 0):
         """fe_plan_set_wait_limit: the longest one bounded wait inside the
         plan's kernels may see no progress (0 restores the default)."""

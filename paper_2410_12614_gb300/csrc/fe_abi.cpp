@@ -1131,6 +1131,37 @@ fe_status fe_adjoint_noalloc(fe_plan *plan, const double *vertices, const double
 }
 
 // ---------------------------------------------------------------------------
+// diagnostics (Sec. 5.2, 5.3)
+// ---------------------------------------------------------------------------
+fe_status fe_geometry(fe_plan *plan, int mode, const double *vertices, int64_t c0, int64_t c1, double *G,
+                      double *absdet, int32_t *used_fp64) {
+    g_err.clear();
+    if (!plan || !G) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+    if (mode < FE_GEOMETRY_FP64 || mode > FE_GEOMETRY_MIXED) return fail(FE_ERR_INVALID_ARG, "unknown mode %d", mode);
+    if (c0 < 0 || c1 > plan->n_cells || c0 > c1) return fail(FE_ERR_INVALID_ARG, "cell range out of bounds");
+    const int r = launch_diag_geometry(vertices ? vertices : plan->vertices.as<double>(), plan->cells.as<int32_t>(), c0,
+                                       c1, plan->d, mode, G, absdet, used_fp64, plan->status.as<int>(), plan->stream);
+    if (r < 0) return cuda_fail((cudaError_t)(-r), "geometry kernel launch");
+    plan->last_launches = r;
+    return FE_OK;
+}
+
+fe_status fe_mass_fp16_products(fe_plan *plan, const double *kappa, const double *w, int64_t c0, int64_t c1, float *A,
+                                float *b) {
+    g_err.clear();
+    if (!plan || !kappa || (!A && !b)) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+    if (b && !w) return fail(FE_ERR_INVALID_ARG, "the action needs w");
+    if (c0 < 0 || c1 > plan->n_cells || c0 > c1) return fail(FE_ERR_INVALID_ARG, "cell range out of bounds");
+    const int r = launch_diag_mass_fp16(plan->vertices.as<double>(), plan->cells.as<int32_t>(),
+                                        plan->cell_dofs.as<int32_t>(), c0, c1, plan->d, plan->n_phi, plan->n_q, kappa,
+                                        plan->weights.as<double>(), plan->phi.as<double>(), w, A, b,
+                                        plan->status.as<int>(), plan->stream);
+    if (r < 0) return cuda_fail((cudaError_t)(-r), "FP16-product kernel launch");
+    plan->last_launches = r;
+    return FE_OK;
+}
+
+// ---------------------------------------------------------------------------
 // batches
 // ---------------------------------------------------------------------------
 }  // extern "C"

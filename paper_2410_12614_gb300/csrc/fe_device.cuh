@@ -140,8 +140,8 @@ __device__ __forceinline__ float f64_to_f32_rne(double x, int &nonfinite) {
 // about (4 + 2 kG32Cancel) 2^-24 per entry.  Returns the geometry status; on a
 // nonzero status g6 and adet are left as they were.
 constexpr float kG32Cancel = 16.f;
-__device__ __forceinline__ int cell_g32(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
-                                        int64_t c, int d, float (&g6)[6], float &adet) {
+__device__ __forceinline__ int cell_g32_tagged(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
+                                               int64_t c, int d, float (&g6)[6], float &adet, int &used_fp64) {
     CellGeom geo;
     const int st = cell_cofactors(vertices, cells, c, d, geo);
     if (st) return st;
@@ -177,6 +177,7 @@ __device__ __forceinline__ int cell_g32(const double *__restrict__ vertices, con
     bool fin = nf == 0 && adet > 0.f && isfinite(inv) && !cancel;
 #pragma unroll
     for (int j = 0; j < 6; ++j) fin = fin && isfinite(g6[j]);
+    used_fp64 = fin ? 0 : 1;
     if (!fin) {
         const double inv64 = 1.0 / geo.absdet;
         int j = 0;
@@ -195,6 +196,12 @@ __device__ __forceinline__ int cell_g32(const double *__restrict__ vertices, con
         adet = (float)geo.absdet;
     }
     return 0;
+}
+
+__device__ __forceinline__ int cell_g32(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
+                                        int64_t c, int d, float (&g6)[6], float &adet) {
+    int used;
+    return cell_g32_tagged(vertices, cells, c, d, g6, adet, used);
 }
 
 // --------------------------------------------------------------------------

@@ -236,6 +236,14 @@ int launch_assemble(const AsmArgs &a, bool fp64, cudaStream_t s);
 // adjoint, and the lookup of its device address on the current device.
 constexpr size_t kNoAllocScratchDoubles = size_t(1) << 22;  // 32 MiB
 cudaError_t noalloc_scratch(double **ptr);
+// Diagnostic kernels (fe_diag.cu): the geometry tensor of cells [c0, c1) in
+// FP64 (mode 0), exclusively FP32 (1) or the production mixed path (2); and the
+// mass form / action with FP16 products and sums.
+int launch_diag_geometry(const double *vertices, const int32_t *cells, int64_t c0, int64_t c1, int d, int mode,
+                         double *G, double *absdet, int32_t *used_fp64, int *status, cudaStream_t s);
+int launch_diag_mass_fp16(const double *vertices, const int32_t *cells, const int32_t *cell_dofs, int64_t c0,
+                          int64_t c1, int d, int n_phi, int n_q, const double *kappa, const double *weights,
+                          const double *phi, const double *w, float *A, float *b, int *status, cudaStream_t s);
 int launch_adjoint(const AdjArgs &a, const int64_t *vert_inc_ptr, const int32_t *vert_inc, double *g_vertices,
                    double *L_out, cudaStream_t s);
 
