@@ -91,8 +91,14 @@ def _load():
             lib.fo_adjoint_stiffness.argtypes = [c_int, c_i64, i32p, f64p, c_i64, c_int, c_int, f64p, f64p,
                                                  f64p, i32p, f64p, f64p, ctypes.c_void_p, ctypes.c_void_p,
                                                  ctypes.POINTER(ctypes.c_double)]
+            lib.fo_element_matrices_box.argtypes = [c_int, c_i64, c_i64, i32p, f64p, c_int, c_int, f64p, f64p,
+                                                    f64p, f64p, f64p, c_int, f64p]
+            lib.fo_kappa_q_box.argtypes = [c_int, c_i64, c_i64, i32p, f64p, c_int, c_int, f64p, f64p, f64p,
+                                           f64p, f64p, c_int, f64p, f64p]
+            lib.fo_dofmap_weights.argtypes = [c_int, c_int, i32p, c_i64, c_i64, i32p, i32p, ctypes.POINTER(c_i64)]
             for f in ("fo_geometry", "fo_mesh_geometry", "fo_element_matrices", "fo_kappa_q", "fo_dofmap",
-                      "fo_csr_pattern", "fo_assemble", "fo_adjoint_stiffness"):
+                      "fo_csr_pattern", "fo_assemble", "fo_adjoint_stiffness", "fo_element_matrices_box",
+                      "fo_kappa_q_box", "fo_dofmap_weights"):
                 getattr(lib, f).restype = c_int
             _lib = lib
     return _lib
@@ -104,11 +110,15 @@ def _check(status, what):
 
 
 def _dim(cell_type):
-    if cell_type in ("triangle", "tri", 2):
+    if cell_type in ("triangle", "tri", 2, "quadrilateral", "quad"):
         return 2
-    if cell_type in ("tetrahedron", "tet", 3):
+    if cell_type in ("tetrahedron", "tet", 3, "hexahedron", "hex"):
         return 3
     raise ValueError(cell_type)
+
+
+def is_boxed(cell_type) -> bool:
+    return cell_type in ("quadrilateral", "quad", "hexahedron", "hex")
 
 
 # --------------------------------------------------------------------------
@@ -179,8 +189,26 @@ def strang_fix_3():
     return pts, wts
 
 
+def tensor_rule(cell_type, m: int):
+    """Tensor-product Gauss-Legendre rule on the unit square / cube [0, 1]^d
+    (the boxed reference cells of Sec. 5.1): m points per direction, exact to
+    degree 2m-1 in each variable, n_q = m^d, point q = ia + m (ib + m ic) (x
+    fastest), 1-D nodes ascending; the 1-D rule is gauss_jacobi(m, 0)."""
+    d = _dim(cell_type)
+    t, w = gauss_jacobi(m, 0)
+    pts, wts = [], []
+    for idx in itertools.product(range(m), repeat=d):
+        i = idx[::-1]                        # x fastest
+        pts.append([t[a] for a in i])
+        wts.append(float(np.prod([w[a] for a in i])))
+    return np.array(pts, dtype=np.float64), np.array(wts, dtype=np.float64)
+
+
 def rule_for_degree(cell_type, p: int):
-    """2p-exact collapsed rule (m = p + 1)."""
+    """2p-exact rule with m = p + 1 points per direction: the collapsed rule on
+    simplices, the tensor Gauss-Legendre rule on boxed cells."""
+    if is_boxed(cell_type):
+        return tensor_rule(cell_type, p + 1)
     return collapsed_rule(cell_type, p + 1)
 
 
@@ -259,6 +287,73 @@ def n_phi(d: int, p: int) -> int:
 
 
 # --------------------------------------------------------------------------
+# Q_p Lagrange basis on boxed cells (Sec. 3.1, boxed cells; Appendix A, the
+# product representation of tensor-product Lagrange polynomials)
+# --------------------------------------------------------------------------
+def box_nodes(d: int, p: int) -> np.ndarray:
+    """Lattice indices a in {0..p}^d of the equispaced nodes X_a = a / p, in
+    lexicographic order with the x index fastest: node k = a_0 + (p+1)(a_1 +
+    (p+1) a_2).  Cell vertex v of a boxed cell is the corner with coordinates
+    (bit_0(v), bit_1(v), bit_2(v))."""
+    out = []
+    for idx in itertools.product(range(p + 1), repeat=d):
+        out.append(idx[::-1])
+    return np.array(out, dtype=np.int32)
+
+
+def box_node_weights(d: int, p: int) -> np.ndarray:
+    """[n_phi, 2^d]: the Q1 (multilinear) coordinates of each node times p^d,
+    w_v = prod_i (a_i if bit_i(v) else p - a_i): the node's weights over the
+    cell's vertices, from which the canonical dof key is formed."""
+    a = box_nodes(d, p)
+    nv = 1 << d
+    W = np.ones((a.shape[0], nv), dtype=np.int64)
+    for v in range(nv):
+        for i in range(d):
+            W[:, v] *= np.where((v >> i) & 1, a[:, i], p - a[:, i])
+    return W.astype(np.int32)
+
+
+def tabulate_box(d: int, p: int, points):
+    """phi [n_phi, n_q] and dphi [d, n_phi, n_q] of the Q_p basis at reference
+    points: phi_a(X) = prod_i l_{a_i}(X_i) with the 1-D equispaced Lagrange
+    factors l_j(t) = prod_{m != j} (p t - m) / (j - m) (a product of first-degree
+    monomials, Appendix A), derivatives by the product rule."""
+    X = np.asarray(points, dtype=np.float64)
+    n_q = X.shape[0]
+    nodes = box_nodes(d, p)
+
+    def lag(j, t):
+        v = np.ones_like(t)
+        for m in range(p + 1):
+            if m != j:
+                v = v * (p * t - m) / (j - m)
+        return v
+
+    def dlag(j, t):
+        tot = np.zeros_like(t)
+        for r in range(p + 1):
+            if r == j:
+                continue
+            term = np.full_like(t, p / (j - r))
+            for m in range(p + 1):
+                if m != j and m != r:
+                    term = term * (p * t - m) / (j - m)
+            tot = tot + term
+        return tot
+
+    phi = np.zeros((nodes.shape[0], n_q))
+    dphi = np.zeros((d, nodes.shape[0], n_q))
+    for k, a in enumerate(nodes):
+        f = [lag(a[i], X[:, i]) for i in range(d)]
+        df = [dlag(a[i], X[:, i]) for i in range(d)]
+        phi[k] = np.prod(f, axis=0)
+        for s in range(d):
+            dphi[s, k] = np.prod([df[i] if i == s else f[i] for i in range(d)], axis=0)
+    return phi, dphi
+
+
+# --------------------------------------------------------------------------
 # Mesh-level routines (C)
 # --------------------------------------------------------------------------
 def _c(a, dt):
@@ -299,8 +394,16 @@ class Problem:
         self.weights = _c(weights, np.float64)
         self.n_q = self.weights.shape[0]
         self.n_cells = self.cells.shape[0]
-        self.n_phi = n_phi(self.d, self.p)
-        self.phi, self.dphi = tabulate(self.d, self.p, self.points)
+        # boxed cells (quadrilaterals, hexahedra) have 2^d vertices in tensor order
+        self.boxed = self.cells.shape[1] == (1 << self.d)
+        if self.boxed:
+            self.n_phi = (self.p + 1) ** self.d
+            self.phi, self.dphi = tabulate_box(self.d, self.p, self.points)
+            _, dpsi = tabulate_box(self.d, 1, self.points)        # Q1 map derivatives [d][2^d][n_q]
+            self.dpsi = _c(dpsi, np.float64)
+        else:
+            self.n_phi = n_phi(self.d, self.p)
+            self.phi, self.dphi = tabulate(self.d, self.p, self.points)
         self.phi = _c(self.phi, np.float64)
         self.dphi = _c(self.dphi, np.float64)
         self._dofs = None
@@ -313,6 +416,11 @@ class Problem:
         kappa = _c(kappa, np.float64).reshape(self.n_cells, self.n_q)
         A = np.zeros((self.n_cells, self.n_phi, self.n_phi))
         f = {"mass": 1, "stiffness": 2}[form]
+        if self.boxed:
+            _check(_load().fo_element_matrices_box(self.d, c0, c1, self.cells, self.vertices, self.n_phi, self.n_q,
+                                                   self.weights, self.phi, self.dphi, self.dpsi, kappa.ravel(), f,
+                                                   A.reshape(-1)), "element_matrices_box")
+            return A
         _check(_load().fo_element_matrices(self.d, c0, c1, self.cells, self.vertices, self.n_phi, self.n_q,
                                            self.weights, self.phi, self.dphi, kappa.ravel(), f, A.reshape(-1)),
                "element_matrices")
@@ -337,13 +445,38 @@ class Problem:
         nc = cells.shape[0]
         kq = np.zeros(nc)
         f = {"mass": 1, "stiffness": 2}[form]
+        if self.boxed:
+            _check(_load().fo_kappa_q_box(self.d, 0, nc, cells, self.vertices, self.n_phi, self.n_q, self.weights,
+                                          self.phi, self.dphi, self.dpsi, kappa.ravel(), f,
+                                          _c(A, np.float64).reshape(-1), kq), "kappa_q_box")
+            return kq
         _check(_load().fo_kappa_q(self.d, 0, nc, cells, self.vertices, self.n_phi, self.n_q, self.weights,
                                   self.phi, self.dphi, kappa.ravel(), f, _c(A, np.float64).reshape(-1), kq),
                "kappa_q")
         return kq
 
+    def point_geometry(self, cell_ids=None):
+        """Boxed cells: |det J_q| [nc, n_q] and G_q = |det J_q| J_q^-1 J_q^-T
+        [nc, n_q, d, d] at every quadrature point (numpy det / inv of
+        J_q = sum_v x_v grad psi_v(X_q)^T; bound arithmetic only)."""
+        cells = self.cells if cell_ids is None else self.cells[np.asarray(cell_ids)]
+        x = self.vertices[cells]                                        # [nc, nv, d]
+        J = np.einsum("cvi,jvq->cqij", x, self.dpsi)
+        det = np.linalg.det(J)
+        Ji = np.linalg.inv(J)
+        G = np.abs(det)[:, :, None, None] * np.einsum("cqik,cqjk->cqij", Ji, Ji)
+        return np.abs(det), G
+
     # dof map / pattern ----------------------------------------------------
     def cell_dofs(self):
+        if self._dofs is None and self.boxed:
+            W = _c(box_node_weights(self.d, self.p), np.int32)
+            dofs = np.zeros((self.n_cells, self.n_phi), dtype=np.int32)
+            nd = ctypes.c_int64(0)
+            _check(_load().fo_dofmap_weights(1 << self.d, self.n_phi, W.ravel(), self.vertices.shape[0],
+                                             self.n_cells, self.cells, dofs.reshape(-1), ctypes.byref(nd)),
+                   "dofmap_weights")
+            self._dofs = (dofs, int(nd.value))
         if self._dofs is None:
             nodes = _c(lattice_nodes(self.d, self.p), np.int32)
             dofs = np.zeros((self.n_cells, self.n_phi), dtype=np.int32)
@@ -390,9 +523,12 @@ class Problem:
     def dof_points(self):
         """Physical coordinates of every global dof (from the cell that first lists it)."""
         dofs, nd = self.cell_dofs()
-        lam = _barycentric(node_points(self.d, self.p))
+        if self.boxed:
+            lam = box_node_weights(self.d, self.p).astype(np.float64) / float(self.p) ** self.d
+        else:
+            lam = _barycentric(node_points(self.d, self.p))
         pts = np.full((nd, self.d), np.nan)
-        xv = self.vertices[self.cells]  # [nc, d+1, d]
+        xv = self.vertices[self.cells]  # [nc, nv, d]
         phys = np.einsum("kv,cvi->cki", lam, xv)
         pts[dofs.reshape(-1)] = phys.reshape(-1, self.d)
         return pts
@@ -551,9 +687,30 @@ def subnormal_term(problem, kappa, form: str, A, mbits: int, emin: int, target: 
     cells = problem.cells if cell_ids is None else problem.cells[np.asarray(cell_ids)]
     if cell_ids is not None:
         kappa = kappa[np.asarray(cell_ids)]
-    det, G = mesh_geometry(problem.vertices, cells)
     wk = np.abs(problem.weights[None, :] * kappa)                        # |w_q kappa_cq|
     d = problem.d
+    if getattr(problem, "boxed", False):
+        # geometry at every point: C_(st),q = w_q kappa_cq G_st(X_q)
+        adet, Gq = problem.point_geometry(cell_ids)
+        if form == "stiffness":
+            Cs = np.stack([np.abs(Gq[:, :, s, t]) for s in range(d) for t in range(s, d)], axis=2) * wk[:, :, None]
+            K = problem.n_q * d * (d + 1) // 2
+            n_f = 2.0
+        else:
+            Cs = (adet * wk)[:, :, None]
+            K = problem.n_q
+            n_f = 1.0
+        M = Cs.reshape(len(Cs), -1).max(axis=1)
+        SC = Cs.reshape(len(Cs), -1).sum(axis=1)
+        pi_max, bmax = operand_magnitudes(problem, form)
+        h = 2.0 ** (emin - mbits - 1)
+        a_C = h * 2.0 ** (2 - target) * M if target > 1 else np.full_like(M, h)
+        a_P = h * 2.0 ** (2 - target) * n_f * bmax ** 2 if target > 1 else h
+        u_s = 2.0 ** -(mbits + 1)
+        S = (1.0 + u_s) * (a_C * pi_max + a_P * SC) + K * a_C * a_P
+        amax = np.abs(np.asarray(A)).reshape(len(M), -1).max(axis=1)
+        return S / amax
+    det, G = mesh_geometry(problem.vertices, cells)
     if form == "stiffness":
         Gs = np.stack([np.abs(G[:, s, t]) for s in range(d) for t in range(s, d)], axis=1)
         M = wk.max(axis=1) * Gs.max(axis=1)

@@ -504,3 +504,196 @@ int fo_adjoint_stiffness(int d, int64_t n_cells, const int32_t *cells, const dou
     if (L_out) *L_out = L;
     return FO_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Boxed cells (quadrilaterals, hexahedra; Sec. 3.1 and the lemma on the     */
+/* Jacobian in Sec. 4.2): the reference cell is [0,1]^d, the map is the      */
+/* multilinear Q1 map x(X) = sum_v x_v psi_v(X) over the 2^d vertices, so    */
+/* J(X) = sum_v x_v grad psi_v(X)^T varies with X and the geometry is        */
+/* formed at every quadrature point.                                         */
+/* ------------------------------------------------------------------------ */
+
+/* J at quadrature point q of cell c: J_ij = sum_v x_{v,i} dpsi[j][v][q]. */
+static void box_jacobian(int d, int nv, const int32_t *cells, const double *vertices, int64_t c,
+                         const double *dpsi, int n_q, int q, double *J) {
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double s = 0.0;
+            for (int v = 0; v < nv; ++v)
+                s += vertices[(int64_t)cells[c * nv + v] * d + i] * dpsi[((int64_t)j * nv + v) * n_q + q];
+            J[i * d + j] = s;
+        }
+}
+
+/* J^{-1} and det J of the d x d matrix J by LU with partial pivoting. */
+static int lu_geometry(int d, const double *J, double *det, double *Jinv) {
+    double M[9];
+    int perm[3], sign;
+    memcpy(M, J, sizeof(double) * d * d);
+    if (lu_factor(d, M, perm, &sign) != 0) return FO_ERR_DEGENERATE;
+    double dt = sign;
+    for (int i = 0; i < d; ++i) dt *= M[i * d + i];
+    *det = dt;
+    for (int col = 0; col < d; ++col) {
+        double e[3] = {0, 0, 0}, x[3];
+        e[col] = 1.0;
+        lu_solve(d, M, perm, e, x);
+        for (int i = 0; i < d; ++i) Jinv[i * d + col] = x[i];
+    }
+    return FO_OK;
+}
+
+/* Element matrices of boxed cells [c0, c1): the literal quadrature sum of
+ * Sec. 3.1 with the geometry of every point:
+ *   mass       A_kl = sum_q w_q kappa_cq |det J_q| phi_k phi_l
+ *   stiffness  A_kl = sum_q w_q kappa_cq |det J_q| (J_q^-T grad phi_k).(J_q^-T grad phi_l). */
+int fo_element_matrices_box(int d, int64_t c0, int64_t c1, const int32_t *cells, const double *vertices,
+                            int n_phi, int n_q, const double *w, const double *phi, const double *dphi,
+                            const double *dpsi, const double *kappa, int form, double *A) {
+    const int nv = 1 << d;
+    double *grad = (double *)malloc(sizeof(double) * (size_t)n_phi * d);
+    if (!grad) return FO_ERR_OOM;
+    for (int64_t c = c0; c < c1; ++c) {
+        double *Ac = A + c * (int64_t)n_phi * n_phi;
+        for (int64_t i = 0; i < (int64_t)n_phi * n_phi; ++i) Ac[i] = 0.0;
+        for (int q = 0; q < n_q; ++q) {
+            double J[9], Jinv[9], det;
+            box_jacobian(d, nv, cells, vertices, c, dpsi, n_q, q, J);
+            if (lu_geometry(d, J, &det, Jinv) != FO_OK) { free(grad); return FO_ERR_DEGENERATE; }
+            const double f = w[q] * kappa[c * n_q + q] * fabs(det);
+            if (form == 2)
+                for (int k = 0; k < n_phi; ++k)
+                    for (int i = 0; i < d; ++i) {
+                        double s = 0.0;
+                        for (int r = 0; r < d; ++r) s += Jinv[r * d + i] * dphi[((int64_t)r * n_phi + k) * n_q + q];
+                        grad[k * d + i] = s;
+                    }
+            for (int k = 0; k < n_phi; ++k)
+                for (int l = 0; l < n_phi; ++l) {
+                    double integrand;
+                    if (form == 1) {
+                        integrand = phi[(int64_t)k * n_q + q] * phi[(int64_t)l * n_q + q];
+                    } else {
+                        integrand = 0.0;
+                        for (int i = 0; i < d; ++i) integrand += grad[k * d + i] * grad[l * d + i];
+                    }
+                    Ac[(int64_t)k * n_phi + l] += f * integrand;
+                }
+        }
+    }
+    free(grad);
+    return FO_OK;
+}
+
+/* kappa_q^A of Corollary 4.10 for boxed cells [c0, c1): C_st = diag_q(w_q
+ * kappa_cq G_st(X_q)) with G(X_q) = |det J_q| J_q^-1 J_q^-T (mass: w_q
+ * kappa_cq |det J_q|); A: the exact element matrices of the same cells. */
+int fo_kappa_q_box(int d, int64_t c0, int64_t c1, const int32_t *cells, const double *vertices, int n_phi,
+                   int n_q, const double *w, const double *phi, const double *dphi, const double *dpsi,
+                   const double *kappa, int form, const double *A, double *kq) {
+    const int nv = 1 << d;
+    const int nd = (form == 2) ? d : 1;
+    double *Cq = (double *)malloc(sizeof(double) * (size_t)n_q * 9);
+    if (!Cq) return FO_ERR_OOM;
+    for (int64_t c = c0; c < c1; ++c) {
+        for (int q = 0; q < n_q; ++q) {
+            double J[9], Jinv[9], det, G[9];
+            box_jacobian(d, nv, cells, vertices, c, dpsi, n_q, q, J);
+            if (lu_geometry(d, J, &det, Jinv) != FO_OK) { free(Cq); return FO_ERR_DEGENERATE; }
+            geometry_tensor(d, Jinv, fabs(det), G);
+            for (int a = 0; a < nd; ++a)
+                for (int b = 0; b < nd; ++b)
+                    Cq[(int64_t)q * 9 + a * nd + b] = fabs(w[q] * kappa[c * n_q + q] * ((form == 2) ? G[a * d + b] : fabs(det)));
+        }
+        double num = 0.0, den = 0.0;
+        const double *Ac = A + c * (int64_t)n_phi * n_phi;
+        for (int k = 0; k < n_phi; ++k)
+            for (int l = 0; l < n_phi; ++l) {
+                double s = 0.0;
+                for (int a = 0; a < nd; ++a)
+                    for (int b = 0; b < nd; ++b)
+                        for (int q = 0; q < n_q; ++q) {
+                            double bk = (form == 2) ? dphi[((int64_t)a * n_phi + k) * n_q + q] : phi[(int64_t)k * n_q + q];
+                            double bl = (form == 2) ? dphi[((int64_t)b * n_phi + l) * n_q + q] : phi[(int64_t)l * n_q + q];
+                            s += fabs(bk) * Cq[(int64_t)q * 9 + a * nd + b] * fabs(bl);
+                        }
+                if (s > num) num = s;
+                if (fabs(Ac[(int64_t)k * n_phi + l]) > den) den = fabs(Ac[(int64_t)k * n_phi + l]);
+            }
+        kq[c] = (den > 0.0) ? num / den : INFINITY;
+    }
+    free(Cq);
+    return FO_OK;
+}
+
+/* Canonical dof map from node weights: node k of a cell carries the integer
+ * weights node_w[k][v] >= 0 over the cell's nv vertices (the multilinear, or
+ * barycentric, coordinates of the node times p^d, resp. p).  Its key is the
+ * multiset {(g_v, node_w[k][v]) : node_w[k][v] > 0} sorted by global vertex
+ * id g_v; a node with one nonzero weight is that vertex's dof; all other keys
+ * are sorted by (support size, vertex ids, weights in that order) and numbered
+ * from n_vertices.  For simplices with the barycentric multiplicities this is
+ * the numbering of fo_dofmap. */
+typedef struct {
+    int32_t size;
+    int32_t g[8];
+    int32_t a[8];
+    int64_t slot;
+} node_key8;
+
+static int key8_cmp(const void *pa, const void *pb) {
+    const node_key8 *x = (const node_key8 *)pa, *y = (const node_key8 *)pb;
+    if (x->size != y->size) return x->size < y->size ? -1 : 1;
+    for (int i = 0; i < x->size; ++i)
+        if (x->g[i] != y->g[i]) return x->g[i] < y->g[i] ? -1 : 1;
+    for (int i = 0; i < x->size; ++i)
+        if (x->a[i] != y->a[i]) return x->a[i] < y->a[i] ? -1 : 1;
+    if (x->slot != y->slot) return x->slot < y->slot ? -1 : 1;
+    return 0;
+}
+
+int fo_dofmap_weights(int nv, int n_phi, const int32_t *node_w, int64_t n_vertices, int64_t n_cells,
+                      const int32_t *cells, int32_t *cell_dofs, int64_t *n_dofs) {
+    if (nv > 8) return FO_ERR_ARG;
+    node_key8 *keys = (node_key8 *)malloc(sizeof(node_key8) * (size_t)(n_phi * n_cells + 1));
+    if (!keys) return FO_ERR_OOM;
+    int64_t m = 0;
+    for (int64_t c = 0; c < n_cells; ++c)
+        for (int k = 0; k < n_phi; ++k) {
+            const int32_t *a = node_w + k * nv;
+            node_key8 key;
+            key.size = 0;
+            for (int v = 0; v < nv; ++v)
+                if (a[v] > 0) {
+                    key.g[key.size] = cells[c * nv + v];
+                    key.a[key.size] = a[v];
+                    key.size++;
+                }
+            if (key.size == 1) {
+                cell_dofs[c * n_phi + k] = key.g[0];
+                continue;
+            }
+            for (int i = 1; i < key.size; ++i)
+                for (int j = i; j > 0 && key.g[j - 1] > key.g[j]; --j) {
+                    int32_t tg = key.g[j]; key.g[j] = key.g[j - 1]; key.g[j - 1] = tg;
+                    int32_t ta = key.a[j]; key.a[j] = key.a[j - 1]; key.a[j - 1] = ta;
+                }
+            for (int i = key.size; i < 8; ++i) { key.g[i] = -1; key.a[i] = 0; }
+            key.slot = c * n_phi + k;
+            keys[m++] = key;
+        }
+    qsort(keys, (size_t)m, sizeof(node_key8), key8_cmp);
+    int64_t next = n_vertices;
+    for (int64_t i = 0; i < m; ++i) {
+        if (i > 0) {
+            const node_key8 *x = &keys[i], *y = &keys[i - 1];
+            int same = x->size == y->size;
+            for (int j = 0; same && j < x->size; ++j) same = x->g[j] == y->g[j] && x->a[j] == y->a[j];
+            if (!same) next++;
+        }
+        cell_dofs[keys[i].slot] = (int32_t)next;
+    }
+    *n_dofs = (m > 0) ? next + 1 : n_vertices;
+    free(keys);
+    return FO_OK;
+}

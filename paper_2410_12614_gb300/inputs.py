@@ -17,6 +17,9 @@ Mesh recipe (the paper's Gmsh meshes are replaced by structured meshes):
   ``[o, o + e_a, o + e_a + e_b, o + (1,1,1)]`` for the permutations (a, b, c)
   of the axes in lexicographic order; cell id ``6 box + perm``, box id
   ``(k N + j) N + i``.  The Kuhn split is conforming across boxes.
+* boxed cells (quadrilaterals, hexahedra): the same vertex grids, one cell
+  per box with its 2^d corners in tensor order (corner v at box offset
+  (bit_0(v), bit_1(v), bit_2(v))); cell id = box id.
 * jitter: every strictly interior vertex moves each coordinate by an
   independent U(-alpha h, alpha h) draw.  alpha <= 0.2 keeps every cell valid.
 * kappa[c, q] = exp(N(0, 1)), i.i.d. per cell and quadrature point.
@@ -33,6 +36,8 @@ import numpy as np
 __all__ = [
     "square_mesh",
     "cube_mesh",
+    "quad_mesh",
+    "hex_mesh",
     "structured_mesh",
     "lognormal_kappa",
     "gaussian_vector",
@@ -97,12 +102,55 @@ def cube_mesh(n: int, alpha: float = 0.0, seed: int = 0):
     return vertices, cells
 
 
+def _box_cells(n: int, d: int):
+    nv = 1 << d
+    grids = np.meshgrid(*[np.arange(n)] * d, indexing="ij")      # [k][j][i] order for d = 3
+    idx = [g.ravel() for g in grids[::-1]]                        # i, j(, k): x fastest
+    cells = np.empty((n ** d, nv), dtype=np.int64)
+    for v in range(nv):
+        vid = np.zeros(n ** d, dtype=np.int64)
+        for axis in reversed(range(d)):
+            vid = vid * (n + 1) + idx[axis] + ((v >> axis) & 1)
+        cells[:, v] = vid
+    return cells.astype(np.int32)
+
+
+def quad_mesh(n: int, alpha: float = 0.0, seed: int = 0):
+    """Unit square, n x n quadrilaterals (vertex ids as square_mesh).
+    Returns (vertices float64 [(n+1)^2, 2], cells int32 [n^2, 4])."""
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    h = 1.0 / n
+    j, i = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="ij")
+    vertices = np.stack([i.ravel() * h, j.ravel() * h], axis=1).astype(np.float64)
+    cells = _box_cells(n, 2)
+    _jitter(vertices, n, 2, alpha, h, seed)
+    return vertices, cells
+
+
+def hex_mesh(n: int, alpha: float = 0.0, seed: int = 0):
+    """Unit cube, n^3 hexahedra (vertex ids as cube_mesh).
+    Returns (vertices float64 [(n+1)^3, 3], cells int32 [n^3, 8])."""
+    if n < 1:
+        raise ValueError("n must be >= 1")
+    h = 1.0 / n
+    k, j, i = np.meshgrid(np.arange(n + 1), np.arange(n + 1), np.arange(n + 1), indexing="ij")
+    vertices = np.stack([i.ravel() * h, j.ravel() * h, k.ravel() * h], axis=1).astype(np.float64)
+    cells = _box_cells(n, 3)
+    _jitter(vertices, n, 3, alpha, h, seed)
+    return vertices, cells
+
+
 def structured_mesh(cell_type: str, n: int, alpha: float, seed: int):
-    """``cell_type`` in {"triangle", "tetrahedron"}."""
+    """``cell_type`` in {"triangle", "tetrahedron", "quadrilateral", "hexahedron"}."""
     if cell_type in ("triangle", "tri"):
         return square_mesh(n, alpha, seed)
     if cell_type in ("tetrahedron", "tet"):
         return cube_mesh(n, alpha, seed)
+    if cell_type in ("quadrilateral", "quad"):
+        return quad_mesh(n, alpha, seed)
+    if cell_type in ("hexahedron", "hex"):
+        return hex_mesh(n, alpha, seed)
     raise ValueError(f"unknown cell type {cell_type!r}")
 
 
