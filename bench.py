@@ -184,7 +184,15 @@ def _traffic(kernel):
         return None
 
 
-def fp64_peak_and_fraction(plan, element_ms):
+_FP64_PEAK = None
+
+
+def measured_fp64_peak():
+    """FP64 peak of this GPU measured as a cuBLAS DGEMM burst (torch.matmul on
+    float64, 6144^3, best of 3, CUDA events), measured once per process."""
+    global _FP64_PEAK
+    if _FP64_PEAK is not None:
+        return _FP64_PEAK
     import torch
     n = 6144
     a = torch.randn((n, n), dtype=torch.float64, device="cuda")
@@ -199,7 +207,13 @@ def fp64_peak_and_fraction(plan, element_ms):
         e1.record()
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
-    peak = 2.0 * n ** 3 / (best / 1e3) / 1e12
+    del a, b
+    _FP64_PEAK = 2.0 * n ** 3 / (best / 1e3) / 1e12
+    return _FP64_PEAK
+
+
+def fp64_peak_and_fraction(plan, element_ms):
+    peak = measured_fp64_peak()
     nph, nq = plan.n_phi, plan.n_q
     nsym = nph * (nph + 1) // 2
     flops = 0
@@ -207,7 +221,6 @@ def fp64_peak_and_fraction(plan, element_ms):
         flops += 2 * nd * nq * nsym + 2 * nd * nd * nq * nph
     flops *= plan.n_cells
     got = flops / (element_ms / 1e3) / 1e12
-    del a, b
     return {"fp64_peak_tflops": peak, "fp64_peak_source": "measured: torch.matmul float64 6144^3 (cuBLAS DGEMM), "
                                                           "best of 3, CUDA events",
             "element_kernel_fp64_flops": flops, "element_kernel_fp64_tflops": got, "frac_of_fp64_peak": got / peak}
@@ -289,17 +302,31 @@ def run_ours(args, rank, world):
         value = job_throughput(elems_per_step, ms_step, world)
         nnz_per_s = job_throughput(2 * plan.nnz, ms_step, world)
 
-        # end to end through the public API with host buffers
+        # end to end through the public API with host buffers: a sequence of
+        # `steps` coefficient sets through fe_assemble_host_many (each item's
+        # kappa uploaded from pinned host memory and its CSR values downloaded,
+        # uploads, compute and downloads overlapped), and single
+        # fe_assemble_host calls for comparison
         kap_pinned = torch.from_numpy(kap_h).pin_memory()
-        host_out = {f: torch.empty(plan.nnz, dtype=torch.float32, pin_memory=True) for f in ("stiffness", "mass")}
+        host_out = [{f: torch.empty(plan.nnz, dtype=torch.float32, pin_memory=True) for f in ("stiffness", "mass")}
+                    for _ in range(2)]
+        seq_k = [kap_pinned] * args.steps
+        seq_o = [host_out[i % 2] for i in range(args.steps)]
+        plan.assemble_host_many(seq_k[:4], seq_o[:4], prec="bf16")
+        e2e_runs = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            plan.assemble_host_many(seq_k, seq_o, prec="bf16")
+            e2e_runs.append((time.perf_counter() - t0) * 1e3 / args.steps)
+        e2e_step = max_over_ranks(statistics.median(e2e_runs), world)
         for _ in range(2):
-            plan.assemble_host(kap_pinned, prec="bf16", out=host_out)
-        e2e_ms = []
+            plan.assemble_host(kap_pinned, prec="bf16", out=host_out[0])
+        single_ms = []
         for _ in range(max(3, args.steps // 2)):
             t0 = time.perf_counter()
-            plan.assemble_host(kap_pinned, prec="bf16", out=host_out)
-            e2e_ms.append((time.perf_counter() - t0) * 1e3)
-        e2e_step = max_over_ranks(statistics.median(e2e_ms), world)
+            plan.assemble_host(kap_pinned, prec="bf16", out=host_out[0])
+            single_ms.append((time.perf_counter() - t0) * 1e3)
+        single_step = max_over_ranks(statistics.median(single_ms), world)
 
         # other precisions (context lines)
         extra = {}
@@ -395,7 +422,11 @@ def run_ours(args, rank, world):
         "e2e": {"value": job_throughput(elems_per_step, e2e_step, world), "unit": "element matrices/s",
                 "h2d_bytes_per_step": int(plan.n_cells * plan.n_q * 8),
                 "d2h_bytes_per_step": int(2 * plan.nnz * 4), "ms_per_step": e2e_step,
-                "api": "fe_assemble_host (pinned host kappa in, pinned host CSR values out)"},
+                "api": f"fe_assemble_host_many over {args.steps} coefficient sets (pinned host kappa in, pinned "
+                       "host CSR values out per item; uploads, compute and downloads overlapped), wall time / items, "
+                       "median of 3 sequences",
+                "single_call_ms_per_step": single_step,
+                "single_call_api": "fe_assemble_host (one synchronous call: upload, compute, download in turn)"},
         "gpu_launches": launches,
         "clocks": clocks,
         "per_precision": extra,
@@ -408,6 +439,17 @@ def run_ours(args, rank, world):
         result["degree_sweep"] = run_sweep(args)
     if rank == 0 and args.configs:
         result["small_configs"] = run_configs(args)
+    if rank == 0 and args.boxed_sweep:
+        result["boxed_sweep"] = run_boxed_sweep(args)
+    if rank == 0 and not args.headline_only:
+        # compact context lines of the other configurations, recorded with every run:
+        # the high-degree tetrahedra (P5, P7), Q3 hexahedra against FP64, and the
+        # small configurations (P1 Laplace latency, P2 adjoints, fused assembly)
+        sargs = argparse.Namespace(**vars(args))
+        sargs.sweep_degrees, sargs.sweep_precisions = "5,7", "bf16,e4m3,fp64"
+        result["context"] = {"degree_sweep_tet16": run_sweep(sargs),
+                             "boxed_q3_hex16": run_boxed_sweep(args, degrees=[3], precs=("bf16", "e4m3")),
+                             "small_configs": result.get("small_configs") or run_configs(args)}
     return result
 
 
@@ -504,13 +546,41 @@ def run_configs(args):
                          "ms": ms, "cells_per_s": nc / (ms / 1e3), "algorithmic_bytes": nbytes,
                          "achieved_gbs": nbytes / (ms / 1e3) / 1e9, "frac_of_hbm": nbytes / (ms / 1e3) / 1e9 / hbm,
                          "fp64_flops": flops, "achieved_fp64_tflops": flops / (ms / 1e3) / 1e12,
-                         "bound": "alu", "fp64_peak_tflops": FP64_NOMINAL_TFLOPS,
-                         "frac_of_fp64_peak": flops / (ms / 1e3) / 1e12 / FP64_NOMINAL_TFLOPS}
+                         "bound": "alu", "fp64_peak_tflops": measured_fp64_peak(),
+                         "fp64_peak_source": "measured cuBLAS DGEMM burst",
+                         "frac_of_fp64_peak": flops / (ms / 1e3) / 1e12 / measured_fp64_peak()}
+        del plan
+
+        # the fused assembly (no element matrices written out) against the unfused
+        # one on the same mesh: P2 stiffness + mass, BF16, CSR of both forms
+        plan = api.Plan("tetrahedron", v, c, 2, pts, w, precisions=("bf16",), stream=stream)
+        kap = torch.from_numpy(inputs.lognormal_kappa(plan.n_cells, plan.n_q, 7)).cuda()
+        vals = {f: plan.empty_values("bf16") for f in ("stiffness", "mass")}
+        els = {f: plan.empty_elements("bf16") for f in ("stiffness", "mass")}
+        res = {"workload": "P2 stiffness + mass, 32^3 x 6 tetrahedra (196,608 cells, 274,625 dofs, 7,678,721 nnz "
+                           "per matrix), BF16, CSR of both forms",
+               "fused_active": plan.set_fusion(1)}
+        for name, fn in (("fused", lambda: plan.assemble(kap, prec="bf16", out=vals)),
+                         ("unfused", lambda: plan.assemble(kap, prec="bf16", elements=els, out=vals))):
+            for _ in range(3):
+                fn()
+            plan.sync()
+            ts = []
+            for _ in range(9):
+                flush.fill_(1.0)
+                flush.sum()
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                stream.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            res[name + "_ms"] = statistics.median(ts)
+            res[name + "_launches"] = plan.last_launches()
+        res["element_matrices_per_s_fused"] = 2 * plan.n_cells / (res["fused_ms"] / 1e3)
+        res["speedup_fused_vs_unfused"] = res["unfused_ms"] / res["fused_ms"]
+        out["p2_assembly_fused"] = res
     return out
 
-
-# GB300's dense FP64 rate (nominal; the CUDA-core FP64 pipe of this part)
-FP64_NOMINAL_TFLOPS = 1.25
 
 SWEEP_PRECISIONS = ("bf16", "fp16", "tf32", "tf32x3", "e4m3")
 
@@ -578,6 +648,71 @@ def run_sweep(args):
                                 "frac_of_roofline": max(t_bytes, t_flops) / (ms / 1e3)})
                 out["runs"].append(run)
                 del els
+            del plan, kap
+            torch.cuda.empty_cache()
+    return out
+
+
+def run_boxed_sweep(args, degrees=None, precs=("bf16", "fp16", "e4m3"), n_by_degree=None):
+    """Boxed cells (the paper's 60x case is hexahedra): Q_p hexahedra on a
+    jittered structured mesh (16^3 cells up to Q4, 10^3 at Q5: the CSR pattern
+    every plan builds grows as ((p N + 1)^3 (2p + 1)^3)), kappa lognormal at the
+    (p+1)^3 tensor Gauss-Legendre points, element matrices of both forms per
+    precision and in FP64 (per-point FP64 geometry in every path), inputs
+    resident, L2 flushed before each timed run; the tensor-core speed-up over
+    the FP64 path and the fraction of the roofline as in run_sweep."""
+    import torch
+    from paper_2410_12614_gb300 import api, inputs
+    hbm, _ = _peaks()
+    try:
+        bf16 = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        bf16 = 1900.0
+    peaks = {"bf16": bf16, "fp16": bf16, "tf32": bf16 / 2, "e4m3": 2 * bf16, "tf32x3": bf16 / 6}
+    degrees = degrees or [int(x) for x in args.boxed_degrees.split(",")]
+    n_by_degree = n_by_degree or {1: 16, 2: 16, 3: 16, 4: 16, 5: 10}
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {"mesh": "Q_p hexahedra, N^3 jittered cells (N = 16, Q5: 10)", "runs": []}
+    with torch.cuda.stream(stream):
+        for p in degrees:
+            n = n_by_degree.get(p, 10)
+            v, c = inputs.hex_mesh(n, 0.15, 40 + p)
+            plan = api.Plan("hexahedron", v, c, p, precisions=precs, stream=stream)
+            kap = torch.from_numpy(inputs.lognormal_kappa(plan.n_cells, plan.n_q, 50 + p)).cuda()
+            nc, nq, nph = plan.n_cells, plan.n_q, plan.n_phi
+            flops = 2.0 * (3 + 1) * nq * nph * nph * nc
+            times = {}
+            for prec in precs + ("fp64",):
+                eb = 8 if prec == "fp64" else 4
+                els = {f: plan.empty_elements(prec) for f in ("stiffness", "mass")}
+                nbytes = nc * (8 * nq + 8 * 4 + 2 * eb * nph * nph) + plan.n_vertices * 3 * 8
+                for _ in range(2):
+                    plan.element_matrices(kap, prec=prec, out=els)
+                plan.sync()
+                ts = []
+                for _ in range(5 if prec != "fp64" else 3):
+                    flush.fill_(1.0)
+                    flush.sum()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    plan.element_matrices(kap, prec=prec, out=els)
+                    e1.record(stream)
+                    stream.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                ms = statistics.median(ts)
+                times[prec] = ms
+                run = {"p": p, "cells": nc, "prec": prec, "n_phi": nph, "n_q": nq, "ms": ms,
+                       "element_matrices_per_s": 2 * nc / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12}
+                if prec != "fp64":
+                    t_bytes, t_flops = nbytes / (hbm * 1e9), flops / (peaks[prec] * 1e12)
+                    run.update({"bound": "tensor" if t_flops > t_bytes else "hbm",
+                                "frac_of_roofline": max(t_bytes, t_flops) / (ms / 1e3)})
+                out["runs"].append(run)
+                del els
+            for prec in precs:
+                out["runs"].append({"p": p, "speedup_vs_fp64": {prec: times["fp64"] / times[prec]}})
             del plan, kap
             torch.cuda.empty_cache()
     return out
@@ -794,6 +929,11 @@ def main():
     ap.add_argument("--configs-only", action="store_true", help="time only those two configurations")
     ap.add_argument("--sweep-only", action="store_true",
                     help="time only the degree sweep and print it as the JSON line (a profiling entry point)")
+    ap.add_argument("--boxed-sweep", action="store_true", help="Q_p hexahedra against FP64 (--boxed-degrees)")
+    ap.add_argument("--boxed-degrees", default="1,2,3,4,5")
+    ap.add_argument("--boxed-only", action="store_true", help="time only the boxed sweep (a profiling entry point)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the compact context lines (sweep points, Q3 hexahedra, small configurations)")
     ap.add_argument("--sweep-degrees", default="1,2,3,4,5,6,7,8")
     ap.add_argument("--sweep-precisions", default="bf16,fp16,tf32,tf32x3,e4m3,fp64")
     args = ap.parse_args()
@@ -816,6 +956,12 @@ def main():
             import torch
             torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
             print(json.dumps({"small_configs": run_configs(args)}))
+        return
+    if args.boxed_only:
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            print(json.dumps({"boxed_sweep": run_boxed_sweep(args)}))
         return
     if args.sweep_only:
         if rank == 0:

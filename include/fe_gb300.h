@@ -65,7 +65,14 @@ typedef enum {
     FE_ERR_NO_DEVICE = -8        /* no CUDA device is visible                 */
 } fe_status;
 
-typedef enum { FE_TRIANGLE = 2, FE_TETRAHEDRON = 3 } fe_cell_type;
+/* Cell types.  Simplices (Sec. 3.1, affine: J constant per cell) and boxed
+ * cells (Sec. 3.1 boxed cells on the reference [0,1]^d, Sec. 5.1: the
+ * multilinear Q1 map, so J, det J and G are formed at every quadrature
+ * point).  A boxed cell lists its 2^d vertices in tensor order: vertex v is
+ * the corner (bit_0(v), bit_1(v), bit_2(v)) of the reference cell.  Boxed
+ * cells carry the Q_p Lagrange space on the equispaced lattice a/p,
+ * a in {0..p}^d, node k = a_0 + (p+1)(a_1 + (p+1) a_2), n_phi = (p+1)^d. */
+typedef enum { FE_TRIANGLE = 2, FE_TETRAHEDRON = 3, FE_QUADRILATERAL = 4, FE_HEXAHEDRON = 5 } fe_cell_type;
 
 /* Forms (bitmask).  Sec. 3.1: mass a(w,v) = int z w v and Poisson
  * a(w,v) = int z grad w . grad v with coefficient z = kappa. */
@@ -88,8 +95,10 @@ typedef enum {
 
 /* Quadrature families for fe_quadrature_rule. */
 enum {
-    FE_QUAD_COLLAPSED_GAUSS_JACOBI = 0, /* m points per direction, exact to 2m-1 */
-    FE_QUAD_TRIANGLE_3POINT = 1         /* (1/6,1/6),(2/3,1/6),(1/6,2/3), w = 1/6 */
+    FE_QUAD_COLLAPSED_GAUSS_JACOBI = 0, /* simplices: m points per direction, exact to 2m-1 */
+    FE_QUAD_TRIANGLE_3POINT = 1,        /* (1/6,1/6),(2/3,1/6),(1/6,2/3), w = 1/6 */
+    FE_QUAD_GAUSS_LEGENDRE_TENSOR = 2   /* boxed cells: m^d Gauss-Legendre points on [0,1]^d,
+                                           exact to degree 2m-1 in each variable, x fastest */
 };
 
 typedef struct fe_plan fe_plan;
@@ -100,7 +109,7 @@ typedef struct {
     int64_t n_vertices;
     const double *vertices; /* host, [n_vertices][d] */
     int64_t n_cells;
-    const int32_t *cells;   /* host, [n_cells][d+1], vertex ids */
+    const int32_t *cells;   /* host, [n_cells][d+1] (simplices) or [n_cells][2^d] (boxed cells), vertex ids */
 } fe_mesh;
 
 typedef struct {
@@ -119,14 +128,21 @@ typedef struct {
  * tetrahedra), exact to degree 2m-1, n_q = m^d, point q = ia + m (ib + m ic)
  * with the 1-D nodes ascending; x = a(1-b)(1-c), y = b(1-c), z = c.
  * FE_QUAD_TRIANGLE_3POINT: the degree-2 interior rule (m ignored).
- * points/weights (host) may be NULL to query n_q only.  m in 1..32. */
+ * FE_QUAD_GAUSS_LEGENDRE_TENSOR (quadrilaterals, hexahedra): the tensor
+ * product of m-point Gauss-Legendre rules on [0,1], point q = ia + m (ib +
+ * m ic).  points/weights (host) may be NULL to query n_q only.  m in 1..32. */
 fe_status fe_quadrature_rule(fe_cell_type type, int family, int m, int32_t *n_q, double *points,
                              double *weights);
 
 /* Continuous Lagrange dof map and CSR pattern (Sec. 3.3, assembly matrix L).
- * cells: host [n_cells][d+1].  degree 1..8 (tetrahedra) or 1..10
- * (triangles).  The pattern of row i is the sorted set of global dofs that
- * share a cell with dof i; the diagonal is always present. */
+ * cells: host [n_cells][vertices per cell].  degree 1..8 (tetrahedra), 1..10
+ * (triangles), 1..5 (hexahedra), 1..8 (quadrilaterals).  The pattern of row i
+ * is the sorted set of global dofs that share a cell with dof i; the diagonal
+ * is always present.  Boxed cells: a node's key is its Q1 weights over the
+ * cell's vertices, w_v = prod_i (bit_i(v) ? a_i : p - a_i), on the vertices
+ * with w_v > 0 sorted by global id (simplices: the barycentric multiplicities);
+ * vertex nodes take the vertex id, the other keys are numbered from
+ * n_vertices in (support size, vertex ids, weights) order. */
 fe_status fe_pattern_create(fe_pattern **out, fe_cell_type type, int64_t n_vertices, int64_t n_cells,
                             const int32_t *cells, int degree);
 /* n_dofs, nnz, n_phi, and the longest row; any output pointer may be NULL. */
@@ -171,6 +187,19 @@ fe_status fe_plan_set_stream(fe_plan *plan, void *cuda_stream);
  * at creation.  Not an error path a healthy GPU takes: it exists so that a
  * stalled pipeline ends with an error instead of hanging the device. */
 fe_status fe_plan_set_wait_limit(fe_plan *plan, uint64_t limit_ns);
+/* Fused assembly of fe_assemble (see there): mode 1 on, 0 off (the default).
+ * active (may be NULL) receives 1 when fe_assemble without element-matrix
+ * outputs will take the fused path on this plan. */
+fe_status fe_plan_set_fusion(fe_plan *plan, int mode, int *active);
+/* Assembly algorithm of this plan's fe_assemble / fe_assemble_elements (and
+ * of batches, from their first plan): 0 (default) the chunked segmented
+ * reduction (element entries staged in segment order, one thread per CSR
+ * value); 1 one warp per CSR row walking the row's element rows in cell order
+ * into shared-memory accumulators at their column slots (also the kernel of
+ * the fused path; measured about 2x slower than 0 on the P3 24^3 x 6
+ * workload, where rows are short).  Both sum every CSR value's entries in
+ * increasing cell order from zero: bitwise the same values. */
+fe_status fe_plan_set_assembly(fe_plan *plan, int algo);
 /* Device memory the plan holds, in bytes: plan_bytes for what plan creation
  * allocated (mesh, tabulations, operand images, dof map, pattern, assembly
  * streams, action tables built so far), workspace_bytes for the workspaces
@@ -206,7 +235,18 @@ fe_status fe_element_matrices(fe_plan *plan, unsigned forms, fe_precision prec, 
  * workspace.  csr_stiffness / csr_mass: device [nnz] values in the plan's
  * pattern (double for FE_PREC_FP64 else float).  Each CSR value is the sum
  * of its element entries in increasing (cell, k, l) order starting from 0,
- * so results are bitwise reproducible. */
+ * so results are bitwise reproducible.
+ * Fused assembly (opt-in, fe_plan_set_fusion): with both element-matrix
+ * pointers NULL (reduced precision), the plan processes the cells in slices
+ * of one wave of tiles (SMs * 128 cells): each slice's element matrices go to
+ * a ring of a few slices that stays in L2, and the rows whose cells are all
+ * done are assembled from it at once (row-wise kernel), so the element
+ * matrices make no round trip through HBM.  The results are bitwise those of
+ * the unfused path.  Eligible where the mesh spans several slices, each
+ * row's cells span at most three slices, and the ring (both forms) fits in a
+ * third of the L2 cache.  Off by default: on this part the per-slice launches
+ * cost the persistent kernel its overlap across tiles, which outweighs the
+ * saved traffic (measured slower on P2 32^3 x 6 tetrahedra). */
 fe_status fe_assemble(fe_plan *plan, unsigned forms, fe_precision prec, const double *vertices,
                       const double *kappa, void *A_stiffness, void *A_mass, void *csr_stiffness,
                       void *csr_mass);
@@ -217,6 +257,21 @@ fe_status fe_assemble(fe_plan *plan, unsigned forms, fe_precision prec, const do
  * memory gives the fastest copies. */
 fe_status fe_assemble_host(fe_plan *plan, unsigned forms, fe_precision prec, const double *kappa_host,
                            void *csr_stiffness_host, void *csr_mass_host);
+
+/* fe_assemble_host for a sequence of n coefficient sets (a parameter sweep,
+ * samples of a random coefficient): item i takes kappa_host[i] (host
+ * [n_cells][n_q]) and leaves its CSR values in csr_stiffness_host[i] /
+ * csr_mass_host[i] (host [nnz] each; either array, or an entry, may be NULL
+ * to skip that form's copy).  The upload of item i+1, the computation of item
+ * i and the download of item i-1 overlap: two slots of device buffers (kept
+ * by the plan), an upload and a download stream, ordered by events, so that
+ * the host link in both directions and the GPU work at once.  Results are
+ * bitwise those of fe_assemble_host.  A host output buffer may be reused by
+ * item i+2 and later (their downloads are ordered).  Synchronous: returns
+ * after the last download; pinned host memory gives the fastest copies. */
+fe_status fe_assemble_host_many(fe_plan *plan, unsigned forms, fe_precision prec, int n,
+                                const double *const *kappa_host, void *const *csr_stiffness_host,
+                                void *const *csr_mass_host);
 
 /* Assembly only, from caller element matrices (device, layout as above). */
 fe_status fe_assemble_elements(fe_plan *plan, unsigned forms, fe_precision prec, const void *A_stiffness,

@@ -24,10 +24,13 @@ STATUS_NAMES = {
     -7: "FE_ERR_TIMEOUT",
     -8: "FE_ERR_NO_DEVICE",
 }
-FE_TRIANGLE, FE_TETRAHEDRON = 2, 3
+FE_TRIANGLE, FE_TETRAHEDRON, FE_QUADRILATERAL, FE_HEXAHEDRON = 2, 3, 4, 5
 FE_FORM_MASS, FE_FORM_STIFFNESS = 1, 2
 PRECISIONS = {"fp64": 0, "tf32x3": 1, "tf32": 2, "bf16": 3, "fp16": 4, "e4m3": 5}
-FE_QUAD_COLLAPSED_GAUSS_JACOBI, FE_QUAD_TRIANGLE_3POINT = 0, 1
+FE_QUAD_COLLAPSED_GAUSS_JACOBI, FE_QUAD_TRIANGLE_3POINT, FE_QUAD_GAUSS_LEGENDRE_TENSOR = 0, 1, 2
+CELL_TYPES = {"triangle": (FE_TRIANGLE, 2), "tri": (FE_TRIANGLE, 2), "tetrahedron": (FE_TETRAHEDRON, 3),
+              "tet": (FE_TETRAHEDRON, 3), "quadrilateral": (FE_QUADRILATERAL, 2), "quad": (FE_QUADRILATERAL, 2),
+              "hexahedron": (FE_HEXAHEDRON, 3), "hex": (FE_HEXAHEDRON, 3)}
 
 # every exported symbol, with (restype, argtypes)
 _vp, _i32, _i64, _u32, _dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p
@@ -55,6 +58,8 @@ SIGNATURES = {
     "fe_plan_destroy": [_vp],
     "fe_plan_set_stream": [_vp, _vp],
     "fe_plan_set_wait_limit": [_vp, ctypes.c_uint64],
+    "fe_plan_set_fusion": [_vp, ctypes.c_int, _pi32],
+    "fe_plan_set_assembly": [_vp, ctypes.c_int],
     "fe_plan_memory": [_vp, _pi64, _pi64],
     "fe_plan_sizes": [_vp, _pi64, _pi64, _pi64, _pi64, _pi32, _pi32],
     "fe_csr_pattern": [_vp, _vp, _vp],
@@ -62,6 +67,7 @@ SIGNATURES = {
     "fe_element_matrices": [_vp, ctypes.c_uint, ctypes.c_int, _vp, _vp, _vp, _vp],
     "fe_assemble": [_vp, ctypes.c_uint, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _vp],
     "fe_assemble_host": [_vp, ctypes.c_uint, ctypes.c_int, _vp, _vp, _vp],
+    "fe_assemble_host_many": [_vp, ctypes.c_uint, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp],
     "fe_assemble_elements": [_vp, ctypes.c_uint, ctypes.c_int, _vp, _vp, _vp, _vp],
     "fe_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "fe_adjoint_values": [_vp, _vp, _vp, _vp, _vp, _vp, _vp],

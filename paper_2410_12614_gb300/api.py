@@ -21,13 +21,16 @@ def _ptr(t):
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
 
 
-def quadrature_rule(cell_type: str, m: int, family: int = _lib.FE_QUAD_COLLAPSED_GAUSS_JACOBI):
-    """Reference rule from the library's host helper: (points [n_q, d], weights [n_q]) float64 numpy."""
+def quadrature_rule(cell_type: str, m: int, family: int | None = None):
+    """Reference rule from the library's host helper: (points [n_q, d], weights [n_q]) float64 numpy.
+    Default family: collapsed Gauss-Jacobi on simplices, tensor Gauss-Legendre on boxed cells."""
     lib = load()
-    t = _lib.FE_TETRAHEDRON if cell_type in ("tet", "tetrahedron") else _lib.FE_TRIANGLE
+    t, d = _lib.CELL_TYPES[cell_type]
+    if family is None:
+        boxed = t in (_lib.FE_QUADRILATERAL, _lib.FE_HEXAHEDRON)
+        family = _lib.FE_QUAD_GAUSS_LEGENDRE_TENSOR if boxed else _lib.FE_QUAD_COLLAPSED_GAUSS_JACOBI
     nq = ctypes.c_int32(0)
     check(lib.fe_quadrature_rule(t, family, m, ctypes.byref(nq), None, None), "fe_quadrature_rule")
-    d = 3 if t == _lib.FE_TETRAHEDRON else 2
     pts = np.zeros((nq.value, d))
     wts = np.zeros(nq.value)
     check(lib.fe_quadrature_rule(t, family, m, ctypes.byref(nq), pts.ctypes.data, wts.ctypes.data),
@@ -41,7 +44,7 @@ class Pattern:
     def __init__(self, cell_type: str, n_vertices: int, cells, degree: int):
         lib = load()
         cells = np.ascontiguousarray(cells, dtype=np.int32)
-        t = _lib.FE_TETRAHEDRON if cell_type in ("tet", "tetrahedron") else _lib.FE_TRIANGLE
+        t, _ = _lib.CELL_TYPES[cell_type]
         h = ctypes.c_void_p()
         check(lib.fe_pattern_create(ctypes.byref(h), t, n_vertices, cells.shape[0], cells.ctypes.data, degree),
               "fe_pattern_create")
@@ -72,8 +75,10 @@ class Plan:
     def __init__(self, cell_type: str, vertices, cells, degree: int, points=None, weights=None,
                  forms=("stiffness", "mass"), precisions=("bf16",), stream: torch.cuda.Stream | None = None):
         lib = load()
-        self.cell_type = "tetrahedron" if cell_type in ("tet", "tetrahedron") else "triangle"
-        self.d = 3 if self.cell_type == "tetrahedron" else 2
+        t, self.d = _lib.CELL_TYPES[cell_type]
+        self.cell_type = {_lib.FE_TRIANGLE: "triangle", _lib.FE_TETRAHEDRON: "tetrahedron",
+                          _lib.FE_QUADRILATERAL: "quadrilateral", _lib.FE_HEXAHEDRON: "hexahedron"}[t]
+        self.boxed = t in (_lib.FE_QUADRILATERAL, _lib.FE_HEXAHEDRON)
         vertices = np.ascontiguousarray(np.asarray(vertices, dtype=np.float64))
         cells = np.ascontiguousarray(np.asarray(cells, dtype=np.int32))
         if points is None:
@@ -81,8 +86,7 @@ class Plan:
         points = np.ascontiguousarray(points, dtype=np.float64)
         weights = np.ascontiguousarray(weights, dtype=np.float64)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        mesh = _lib.FeMesh(_lib.FE_TETRAHEDRON if self.d == 3 else _lib.FE_TRIANGLE, vertices.shape[0],
-                           vertices.ctypes.data, cells.shape[0], cells.ctypes.data)
+        mesh = _lib.FeMesh(t, vertices.shape[0], vertices.ctypes.data, cells.shape[0], cells.ctypes.data)
         rule = _lib.FeQuadrature(weights.shape[0], points.ctypes.data, weights.ctypes.data)
         fmask = 0
         for f in forms:
@@ -191,6 +195,22 @@ class Plan:
                                       _ptr(out.get("stiffness")), _ptr(out.get("mass"))), "fe_assemble_host")
         return out
 
+    def assemble_host_many(self, kappas_host, outs, forms=("stiffness", "mass"), prec="bf16"):
+        """fe_assemble_host_many: a sequence of host coefficient sets (contiguous
+        CPU float64 tensors, pinned preferred) -> their CSR values in the host
+        tensors outs[i][form]; uploads, computation and downloads overlap."""
+        n = len(kappas_host)
+        for k in kappas_host:
+            if k.is_cuda or k.dtype != torch.float64 or not k.is_contiguous():
+                raise ValueError("kappa_host entries must be contiguous CPU float64 tensors")
+        kap = (ctypes.c_void_p * n)(*[ctypes.c_void_p(k.data_ptr()) for k in kappas_host])
+        arrs = {}
+        for f in ("stiffness", "mass"):
+            arrs[f] = (ctypes.c_void_p * n)(*[ctypes.c_void_p(o[f].data_ptr()) for o in outs]) if f in forms else None
+        check(load().fe_assemble_host_many(self._h, self._forms_mask(forms), PRECISIONS[prec], n, kap,
+                                           arrs["stiffness"], arrs["mass"]), "fe_assemble_host_many")
+        return outs
+
     def action(self, kappa, w, forms=("stiffness", "mass"), prec="fp64", vertices=None, cell_vectors=False,
                out=None):
         """Algorithm 2: v^g = L b with b^c_j = a_K(w, phi_j) for the FE function with
@@ -285,6 +305,18 @@ class Plan:
         """fe_plan_set_wait_limit: the longest one bounded wait inside the
         plan's kernels may see no progress (0 restores the default)."""
         check(load().fe_plan_set_wait_limit(self._h, int(limit_ns)), "fe_plan_set_wait_limit")
+
+    def set_fusion(self, mode: int = 1) -> bool:
+        """fe_plan_set_fusion: 1 on, 0 off (the default); returns whether
+        fe_assemble without element-matrix outputs takes the fused path."""
+        act = ctypes.c_int32()
+        check(load().fe_plan_set_fusion(self._h, int(mode), ctypes.byref(act)), "fe_plan_set_fusion")
+        return bool(act.value)
+
+    def set_assembly(self, algo: int = 0):
+        """fe_plan_set_assembly: 0 the chunked segmented reduction (default), 1
+        one warp per CSR row; the CSR values are bitwise the same."""
+        check(load().fe_plan_set_assembly(self._h, int(algo)), "fe_plan_set_assembly")
 
     def memory(self):
         """(plan_bytes, workspace_bytes) of device memory the plan holds (fe_plan_memory)."""

@@ -49,7 +49,20 @@ fe_status cuda_fail(cudaError_t e, const char *what) {
 
 int form_index(unsigned form) { return form == FE_FORM_STIFFNESS ? 0 : 1; }
 
-bool supported_degree(int d, int p) { return p >= 1 && ((d == 3 && p <= 8) || (d == 2 && p <= 10)); }
+bool supported_degree(int d, int p, bool boxed = false) {
+    if (boxed) return p >= 1 && ((d == 3 && p <= 5) || (d == 2 && p <= 8));
+    return p >= 1 && ((d == 3 && p <= 8) || (d == 2 && p <= 10));
+}
+
+// Dimension and kind of a cell type (0 for an unknown type).
+int cell_dim(fe_cell_type t, bool &boxed) {
+    boxed = (t == FE_QUADRILATERAL || t == FE_HEXAHEDRON);
+    switch (t) {
+        case FE_TRIANGLE: case FE_QUADRILATERAL: return 2;
+        case FE_TETRAHEDRON: case FE_HEXAHEDRON: return 3;
+        default: return 0;
+    }
+}
 
 // Default limit on how long one bounded wait inside a kernel may see no
 // progress before the kernel gives up (fe_plan_set_wait_limit).
@@ -82,6 +95,20 @@ struct DevBuf {
 
 struct fe_plan {
     int d = 0, p = 0, n_phi = 0, n_q = 0, n_pairs = 0, n_sym = 0;
+    bool boxed = false;                  // quadrilaterals / hexahedra: geometry per quadrature point
+    int nv = 0;                          // vertices per cell
+    DevBuf dpsi_box;                     // boxed: Q1 derivatives at the rule's points [d][nv][n_q]
+    DevBuf ws_geoq;                      // boxed FP64 path: G pairs and |det J| per point [n_cells][n_q][7]
+    // fused assembly: cells in slices of fuse_cells, element matrices in a ring of
+    // fuse_slots slices, the chunks of each slice (device list + host offsets)
+    int64_t fuse_cells = 0;
+    int fuse_slots = 0, fuse_slices = 0;
+    bool fuse_ok = false;
+    DevBuf fuse_rows, ws_ring[2];
+    std::vector<int64_t> fuse_row_off;
+    DevBuf inc_slot;                     // [n_inc][n_phi] column slots (row-wise assembly)
+    int asm_algo = 0;                    // fe_plan_set_assembly: 0 chunked segments (default), 1 one warp per row
+    int fuse_mode = 0;                   // fe_plan_set_fusion: 1 on where eligible, 0 off (default)
     unsigned form_mask = 0, prec_mask = 0;
     int64_t n_cells = 0, n_vertices = 0, n_dofs = 0, nnz = 0;
     int max_row = 0;
@@ -109,9 +136,20 @@ struct fe_plan {
     int tuned_np[6][2] = {};             // autotuned N-pass width per precision and form
     unsigned long long wait_limit_ns = kDefaultWaitLimitNs;   // no-progress limit of every bounded kernel wait
     float act_rbound[2] = {0.f, 0.f};    // FP16 action scaling bounds (ActArgs::r_bound)
+    // pipelined host path (fe_assemble_host_many): two slots of device inputs and outputs,
+    // an upload and a download stream, and the events that order them
+    DevBuf ws_pipe_kappa[2], ws_pipe_csr[2][2];
+    bool pipe_ready = false;
+    cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr;
+    cudaEvent_t pipe_in[2] = {}, pipe_used[2] = {}, pipe_out[2] = {};
     ~fe_plan() {
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
+        for (int i = 0; i < 2; ++i)
+            for (cudaEvent_t e : {pipe_in[i], pipe_used[i], pipe_out[i]})
+                if (e) cudaEventDestroy(e);
+        if (pipe_h2d) cudaStreamDestroy(pipe_h2d);
+        if (pipe_d2h) cudaStreamDestroy(pipe_d2h);
     }
 };
 
@@ -144,8 +182,23 @@ const char *fe_last_error(void) { return g_err.c_str(); }
 fe_status fe_quadrature_rule(fe_cell_type type, int family, int m, int32_t *n_q, double *points, double *weights) {
     g_err.clear();
     if (!n_q) return fail(FE_ERR_INVALID_ARG, "n_q is NULL");
-    const int d = (int)type;
-    if (d != 2 && d != 3) return fail(FE_ERR_INVALID_ARG, "unknown cell type %d", (int)type);
+    bool boxed = false;
+    const int d = cell_dim(type, boxed);
+    if (d == 0) return fail(FE_ERR_INVALID_ARG, "unknown cell type %d", (int)type);
+    if (family == FE_QUAD_GAUSS_LEGENDRE_TENSOR) {
+        if (!boxed) return fail(FE_ERR_INVALID_ARG, "the tensor Gauss-Legendre rule is for boxed cells");
+        if (m < 1 || m > 32) return fail(FE_ERR_UNSUPPORTED, "m must lie in 1..32");
+        int nq = 1;
+        for (int i = 0; i < d; ++i) nq *= m;
+        *n_q = nq;
+        if (!points || !weights) return FE_OK;
+        std::vector<double> pts, wts;
+        if (!host::tensor_rule(d, m, pts, wts)) return fail(FE_ERR_INVALID_ARG, "rule construction failed");
+        std::memcpy(points, pts.data(), sizeof(double) * pts.size());
+        std::memcpy(weights, wts.data(), sizeof(double) * wts.size());
+        return FE_OK;
+    }
+    if (boxed) return fail(FE_ERR_INVALID_ARG, "boxed cells take FE_QUAD_GAUSS_LEGENDRE_TENSOR");
     if (family == FE_QUAD_TRIANGLE_3POINT) {
         if (d != 2) return fail(FE_ERR_INVALID_ARG, "the 3-point rule is for triangles");
         *n_q = 3;
@@ -174,12 +227,13 @@ fe_status fe_pattern_create(fe_pattern **out, fe_cell_type type, int64_t n_verti
     g_err.clear();
     if (!out || !cells) return fail(FE_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
-    const int d = (int)type;
-    if (d != 2 && d != 3) return fail(FE_ERR_INVALID_ARG, "unknown cell type %d", (int)type);
-    if (!supported_degree(d, degree)) return fail(FE_ERR_UNSUPPORTED, "degree %d not supported", degree);
+    bool boxed = false;
+    const int d = cell_dim(type, boxed);
+    if (d == 0) return fail(FE_ERR_INVALID_ARG, "unknown cell type %d", (int)type);
+    if (!supported_degree(d, degree, boxed)) return fail(FE_ERR_UNSUPPORTED, "degree %d not supported", degree);
     if (n_vertices <= 0 || n_cells <= 0) return fail(FE_ERR_INVALID_ARG, "empty mesh");
     auto pat = std::make_unique<fe_pattern>();
-    std::string err = host::build_pattern(d, degree, n_vertices, n_cells, cells, pat->P, false);
+    std::string err = host::build_pattern(d, degree, n_vertices, n_cells, cells, pat->P, false, boxed);
     if (!err.empty()) return fail(FE_ERR_INVALID_ARG, "%s", err.c_str());
     *out = pat.release();
     return FE_OK;
@@ -217,9 +271,11 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
     if (!out || !mesh || !rule || !mesh->vertices || !mesh->cells || !rule->points || !rule->weights)
         return fail(FE_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
-    const int d = (int)mesh->type;
-    if (d != 2 && d != 3) return fail(FE_ERR_INVALID_ARG, "unknown cell type %d", (int)mesh->type);
-    if (!supported_degree(d, degree)) return fail(FE_ERR_UNSUPPORTED, "degree %d not supported for d=%d", degree, d);
+    bool boxed = false;
+    const int d = cell_dim(mesh->type, boxed);
+    if (d == 0) return fail(FE_ERR_INVALID_ARG, "unknown cell type %d", (int)mesh->type);
+    if (!supported_degree(d, degree, boxed))
+        return fail(FE_ERR_UNSUPPORTED, "degree %d not supported for this cell type", degree);
     if (mesh->n_vertices <= 0 || mesh->n_cells <= 0) return fail(FE_ERR_INVALID_ARG, "empty mesh");
     if (rule->n_q <= 0 || rule->n_q > 4096) return fail(FE_ERR_UNSUPPORTED, "n_q must lie in 1..4096");
     if (form_mask == 0 || (form_mask & ~3u)) return fail(FE_ERR_INVALID_ARG, "bad form mask");
@@ -237,7 +293,9 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
     fe_plan &P = *pl;
     P.d = d;
     P.p = degree;
-    P.n_phi = host::n_phi(d, degree);
+    P.boxed = boxed;
+    P.nv = boxed ? (1 << d) : d + 1;
+    P.n_phi = boxed ? host::n_phi_box(d, degree) : host::n_phi(d, degree);
     P.n_q = rule->n_q;
     P.n_pairs = d * (d + 1) / 2;
     P.n_sym = P.n_phi * (P.n_phi + 1) / 2;
@@ -253,19 +311,26 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
     if ((int64_t)mesh->n_cells * P.n_phi * P.n_phi >= INT32_MAX)
         return fail(FE_ERR_UNSUPPORTED, "n_cells * n_phi^2 must stay below 2^31 (32-bit element offsets)");
     host::Pattern pat;
-    std::string err = host::build_pattern(d, degree, mesh->n_vertices, mesh->n_cells, mesh->cells, pat, true);
+    // slices of one wave of tiles for the fused assembly
+    P.fuse_cells = (int64_t)std::max(1, P.sms) * TC_M;
+    std::string err = host::build_pattern(d, degree, mesh->n_vertices, mesh->n_cells, mesh->cells, pat, true, boxed);
     if (!err.empty()) return fail(FE_ERR_INVALID_ARG, "%s", err.c_str());
     P.n_dofs = pat.n_dofs;
     P.nnz = pat.nnz;
     P.max_row = pat.max_row;
     P.n_chunks = (int64_t)pat.chunk_row.size() - 1;
 
-    std::vector<double> phi, dphi;
-    host::tabulate(d, degree, rule->points, rule->n_q, phi, dphi);
+    std::vector<double> phi, dphi, psi_box, dpsi_box;
+    if (boxed) {
+        host::tabulate_box(d, degree, rule->points, rule->n_q, phi, dphi);
+        host::tabulate_box(d, 1, rule->points, rule->n_q, psi_box, dpsi_box);   // the multilinear map
+    } else {
+        host::tabulate(d, degree, rule->points, rule->n_q, phi, dphi);
+    }
 
     cudaStream_t s = P.stream;
     std::vector<double> verts(mesh->vertices, mesh->vertices + mesh->n_vertices * d);
-    std::vector<int32_t> cl(mesh->cells, mesh->cells + mesh->n_cells * (d + 1));
+    std::vector<int32_t> cl(mesh->cells, mesh->cells + mesh->n_cells * P.nv);
     std::vector<double> wts(rule->weights, rule->weights + rule->n_q);
     FE_CUDA(upload(P.vertices, verts, s), "upload vertices");
     FE_CUDA(upload(P.cells, cl, s), "upload cells");
@@ -280,10 +345,12 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
     FE_CUDA(upload(P.contrib_code, pat.contrib_code, s), "upload contribution codes");
     FE_CUDA(upload(P.contrib_dest, pat.contrib_dest, s), "upload contribution destinations");
     FE_CUDA(upload(P.chunk_desc, pat.chunk_desc, s), "upload assembly chunks");
+    FE_CUDA(upload(P.inc_slot, pat.inc_slot, s), "upload column slots");
     FE_CUDA(upload(P.vinc_ptr, pat.vinc_ptr, s), "upload vinc_ptr");
     FE_CUDA(upload(P.vinc, pat.vinc, s), "upload vinc");
     FE_CUDA(upload(P.phi, phi, s), "upload phi");
     FE_CUDA(upload(P.dphi, dphi, s), "upload dphi");
+    if (boxed) FE_CUDA(upload(P.dpsi_box, dpsi_box, s), "upload Q1 derivatives");
     // operand column of every pair (k <= l): a bank-conflict-free order for the
     // staged epilogue's gathers; sym_kl maps a column back to its pair (-1: padding)
     P.col_of_sym = host::stage_columns(P.n_phi, (P.n_phi * P.n_phi) % 4 == 0);
@@ -304,6 +371,41 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
     std::vector<int> zero(4, 0);
     FE_CUDA(upload(P.status, zero, s), "status word");
 
+    // fused assembly (fe_assemble without element-matrix outputs): used when the
+    // mesh spans several slices and the ring of element matrices of
+    // slice_span slices (both forms) fits in a third of the L2 cache
+    {
+        P.fuse_slices = (int)((P.n_cells + P.fuse_cells - 1) / P.fuse_cells);
+        // the widest range of slices one row's cells span (incidences are in cell order)
+        P.fuse_slots = 0;
+        for (int64_t i = 0; i < P.n_dofs; ++i)
+            if (pat.inc_ptr[i + 1] > pat.inc_ptr[i]) {
+                const int64_t lo = (pat.inc_elem[pat.inc_ptr[i]] / P.n_phi) / P.fuse_cells;
+                const int64_t hi = (pat.inc_elem[pat.inc_ptr[i + 1] - 1] / P.n_phi) / P.fuse_cells;
+                P.fuse_slots = std::max<int>(P.fuse_slots, (int)(hi - lo + 1));
+            }
+        int l2 = 0;
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+        int nf = 0;
+        for (unsigned f : {(unsigned)FE_FORM_STIFFNESS, (unsigned)FE_FORM_MASS}) nf += (form_mask & f) ? 1 : 0;
+        const double ring = (double)P.fuse_slots * P.fuse_cells * P.n_phi * P.n_phi * 4.0 * nf;
+        P.fuse_ok = P.fuse_slices >= 2 && P.fuse_slots >= 1 && P.fuse_slots <= 3 && l2 > 0 && ring <= l2 / 3.0;
+        if (P.fuse_ok) {
+            // rows grouped by the slice of their last cell (the row-wise kernel's lists)
+            std::vector<int32_t> rows((size_t)P.n_dofs);
+            std::vector<int32_t> rs((size_t)P.n_dofs, 0);
+            for (int64_t i = 0; i < P.n_dofs; ++i) {
+                rows[i] = (int32_t)i;
+                if (pat.inc_ptr[i + 1] > pat.inc_ptr[i])
+                    rs[i] = (int32_t)((pat.inc_elem[pat.inc_ptr[i + 1] - 1] / P.n_phi) / P.fuse_cells);
+            }
+            std::stable_sort(rows.begin(), rows.end(), [&](int32_t x, int32_t y) { return rs[x] < rs[y]; });
+            P.fuse_row_off.assign(P.fuse_slices + 1, 0);
+            for (int64_t i = 0; i < P.n_dofs; ++i) P.fuse_row_off[rs[i] + 1]++;
+            for (int sl = 0; sl < P.fuse_slices; ++sl) P.fuse_row_off[sl + 1] += P.fuse_row_off[sl];
+            FE_CUDA(upload(P.fuse_rows, rows, s), "upload fused row lists");
+        }
+    }
     P.h_phi = phi;
     P.h_dphi = dphi;
     {
@@ -363,10 +465,14 @@ fe_status fe_plan_memory(const fe_plan *plan, int64_t *plan_bytes, int64_t *work
                           &P.ws_adj_L, &P.ws_Lsum, &P.ws_win, &P.ws_cellf, &P.ws_act_b[0], &P.ws_act_b[1]};
     int64_t w = 0;
     for (const DevBuf *b : ws) w += (int64_t)b->bytes;
+    for (int i = 0; i < 2; ++i)
+        w += (int64_t)(P.ws_pipe_kappa[i].bytes + P.ws_pipe_csr[i][0].bytes + P.ws_pipe_csr[i][1].bytes);
+    w += (int64_t)P.ws_geoq.bytes + (int64_t)P.ws_ring[0].bytes + (int64_t)P.ws_ring[1].bytes;
     int64_t t = 0;
     const DevBuf *own[] = {&P.vertices, &P.cells, &P.weights, &P.cell_dofs, &P.row_ptr, &P.col_idx, &P.inc_ptr,
                            &P.inc_elem, &P.vinc_ptr, &P.vinc, &P.contrib_cnt, &P.contrib_base, &P.contrib_code,
-                           &P.contrib_dest, &P.chunk_desc, &P.phi, &P.dphi, &P.sym_kl, &P.full2sym, &P.status};
+                           &P.contrib_dest, &P.chunk_desc, &P.phi, &P.dphi, &P.sym_kl, &P.full2sym, &P.status,
+                           &P.fuse_rows, &P.inc_slot, &P.dpsi_box};
     for (const DevBuf *b : own) t += (int64_t)b->bytes;
     for (int i = 0; i < 6; ++i)
         for (int f = 0; f < 2; ++f) t += (int64_t)(P.img[i][f].bytes + P.act_tab[i][f].bytes + P.act_tab_t[i][f].bytes);
@@ -374,6 +480,21 @@ fe_status fe_plan_memory(const fe_plan *plan, int64_t *plan_bytes, int64_t *work
         for (int f = 0; f < 3; ++f) t += (int64_t)P.act_packed[i][f].bytes;
     if (plan_bytes) *plan_bytes = t;
     if (workspace_bytes) *workspace_bytes = w;
+    return FE_OK;
+}
+
+fe_status fe_plan_set_assembly(fe_plan *plan, int algo) {
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (algo != 0 && algo != 1) return fail(FE_ERR_INVALID_ARG, "algo must be 0 or 1");
+    plan->asm_algo = algo;
+    return FE_OK;
+}
+
+fe_status fe_plan_set_fusion(fe_plan *plan, int mode, int *active) {
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (mode != 0 && mode != 1) return fail(FE_ERR_INVALID_ARG, "mode must be 1 (on) or 0 (off)");
+    plan->fuse_mode = mode;
+    if (active) *active = (plan->fuse_ok && mode == 1) ? 1 : 0;
     return FE_OK;
 }
 
@@ -482,7 +603,10 @@ static fe_status ensure_ws(DevBuf &b, size_t bytes, const char *what) {
 }
 
 // Bytes of the factor kernel's outputs for one plan.
-static size_t win_bytes(const fe_plan *P) { return sizeof(float) * (size_t)P->n_cells * win_ld(P->n_q); }
+static int win_slots(const fe_plan *P) { return P->boxed ? P->n_pairs + 1 : 1; }
+static size_t win_bytes(const fe_plan *P) {
+    return sizeof(float) * (size_t)P->n_cells * win_ld(P->n_q) * win_slots(P);
+}
 static size_t cellf_bytes(const fe_plan *P) { return sizeof(float) * (size_t)P->n_cells * CELLF; }
 
 static TcSeg make_tc_seg(fe_plan *P, unsigned forms, int prec, const double *vertices, const double *kappa,
@@ -512,6 +636,9 @@ static TcSeg make_tc_seg(fe_plan *P, unsigned forms, int prec, const double *ver
     g.full2sym = P->full2sym.as<int16_t>();
     g.staged = 0;
     g.tile_begin = 0;
+    g.win_slots = win_slots(P);
+    g.nv = P->nv;
+    g.dpsi = P->boxed ? P->dpsi_box.as<double>() : nullptr;
     return g;
 }
 
@@ -560,6 +687,7 @@ static AsmSeg make_asm_seg(fe_plan *P, unsigned forms, const void *const A[2], v
     g.chunk_desc = P->chunk_desc.as<int64_t>();
     g.n_chunks = P->n_chunks;
     g.n_phi = P->n_phi;
+    g.inc_slot = P->inc_slot.as<uint16_t>();
     int nf = 0;
     for (int fi = 0; fi < 2; ++fi) {
         unsigned form = fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS;
@@ -580,6 +708,17 @@ static fe_status run_elements(fe_plan *P, unsigned forms, fe_precision prec, con
     const double *verts = vertices ? vertices : P->vertices.as<double>();
     if (prec == FE_PREC_FP64) {
         mark(P, 0, true);
+        const double *geo_q = nullptr;
+        if (P->boxed) {
+            fe_status st = ensure_ws(P->ws_geoq, sizeof(double) * 7 * (size_t)P->n_cells * P->n_q, "geometry workspace");
+            if (st) return st;
+            const int r = launch_box_geometry(verts, P->cells.as<int32_t>(), P->n_cells, P->d, P->nv,
+                                              P->dpsi_box.as<double>(), P->n_q, P->ws_geoq.as<double>(),
+                                              P->status.as<int>(), P->stream);
+            if (r < 0) return cuda_fail((cudaError_t)(-r), "geometry kernel launch");
+            launches += r;
+            geo_q = P->ws_geoq.as<double>();
+        }
         for (unsigned form : {(unsigned)FE_FORM_STIFFNESS, (unsigned)FE_FORM_MASS}) {
             if (!(forms & form)) continue;
             F64Args a{};
@@ -595,6 +734,7 @@ static fe_status run_elements(fe_plan *P, unsigned forms, fe_precision prec, con
             a.form = (int)form;
             a.out = static_cast<double *>(A[form_index(form)]);
             a.status = P->status.as<int>();
+            a.geo_q = geo_q;
             int r = launch_f64_elements(a, P->stream);
             if (r < 0) return cuda_fail((cudaError_t)(-r), "FP64 element kernel launch");
             launches += r;
@@ -634,11 +774,84 @@ static fe_status run_assembly(fe_plan *P, unsigned forms, bool fp64, const void 
     a.n_rows = P->n_dofs;
     a.n_chunks = P->n_chunks;
     a.n_forms = n_forms_of(forms);
+    a.algo = P->asm_algo;
     mark(P, 1, true);
     int r = launch_assemble(a, fp64, P->stream);
     if (r < 0) return cuda_fail((cudaError_t)(-r), "assembly kernel launch");
     launches += r;
     mark(P, 1, false);
+    return FE_OK;
+}
+
+// Fused assembly (no element-matrix outputs): the cells in slices of one wave
+// of tiles; per slice the factor and element kernels write the slice's element
+// matrices into ring slot (slice mod fuse_slots) -- a few tens of MB that stay
+// in L2 -- and the assembly kernel sums the rows whose last incident cell lies
+// in that slice, reading the ring.  Every CSR value is still the sum of its
+// entries in increasing cell order from zero: bitwise the unfused result.
+static fe_status run_fused(fe_plan *P, unsigned forms, fe_precision prec, const double *vertices, const double *kappa,
+                           void *csr[2]) {
+    for (int fi = 0; fi < 2; ++fi)
+        if ((forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS)) && !csr[fi])
+            return fail(FE_ERR_INVALID_ARG, "NULL CSR output");
+    const int64_t S = P->fuse_cells;
+    const size_t slot_elems = (size_t)S * P->n_phi * P->n_phi;
+    void *ring[2] = {nullptr, nullptr};
+    for (int fi = 0; fi < 2; ++fi)
+        if (forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS)) {
+            fe_status st = ensure_ws(P->ws_ring[fi], sizeof(float) * slot_elems * P->fuse_slots, "fused ring");
+            if (st) return st;
+            ring[fi] = P->ws_ring[fi].p;
+        }
+    fe_status st = ensure_ws(P->ws_win, win_bytes(P), "coefficient window workspace");
+    if (!st) st = ensure_ws(P->ws_cellf, cellf_bytes(P), "cell factor workspace");
+    if (st) return st;
+    const double *verts = vertices ? vertices : P->vertices.as<double>();
+    const int ldw = win_ld(P->n_q), slots = win_slots(P);
+    int launches = 0;
+    mark(P, 0, true);
+    for (int sl = 0; sl < P->fuse_slices; ++sl) {
+        const int64_t c0 = (int64_t)sl * S;
+        const int64_t cnt = std::min<int64_t>(S, P->n_cells - c0);
+        void *A[2] = {nullptr, nullptr};
+        for (int fi = 0; fi < 2; ++fi)
+            if (ring[fi]) A[fi] = static_cast<float *>(ring[fi]) + (size_t)(sl % P->fuse_slots) * slot_elems;
+        TcArgs a{};
+        a.seg0 = make_tc_seg(P, forms, prec, verts, kappa + c0 * P->n_q, A, P->ws_win.as<float>() + c0 * ldw * slots,
+                             P->ws_cellf.as<float>() + c0 * CELLF);
+        a.seg0.cells = P->cells.as<int32_t>() + c0 * P->nv;
+        a.seg0.n_cells = cnt;
+        a.segs = nullptr;
+        a.n_segs = 1;
+        tc_finalize(a, &a.seg0, 1, prec, P->status.as<int>(), P->wait_limit_ns);
+        int r = launch_factor(a, P->stream);
+        if (r < 0) return cuda_fail((cudaError_t)(-r), "factor kernel launch");
+        launches += r;
+        r = launch_tc_elements(a, tc_smem_bytes(a), P->stream);
+        if (r < 0) return cuda_fail((cudaError_t)(-r), "tensor-core element kernel launch");
+        launches += r;
+        const int64_t lc = P->fuse_row_off[sl + 1] - P->fuse_row_off[sl];
+        if (lc > 0) {
+            AsmArgs as{};
+            const void *Ar[2] = {ring[0], ring[1]};
+            as.seg0 = make_asm_seg(P, forms, Ar, csr);
+            as.seg0.ring_cells = S;
+            as.seg0.ring_slots = P->fuse_slots;
+            as.segs = nullptr;
+            as.n_segs = 1;
+            as.n_rows = P->n_dofs;
+            as.n_chunks = P->n_chunks;
+            as.n_forms = n_forms_of(forms);
+            as.algo = 1;   // the row-wise kernel over the slice's completed rows
+            as.row_list = P->fuse_rows.as<int32_t>() + P->fuse_row_off[sl];
+            as.row_count = lc;
+            r = launch_assemble(as, false, P->stream);
+            if (r < 0) return cuda_fail((cudaError_t)(-r), "assembly kernel launch");
+            launches += r;
+        }
+    }
+    mark(P, 0, false);
+    P->last_launches = launches;
     return FE_OK;
 }
 
@@ -714,7 +927,9 @@ static fe_status autotune_plan(fe_plan &P) {
                 // layouts differ in how many partially written sectors they leave
                 const size_t flush_bytes = (size_t)256 << 20;
                 FE_CUDA(flush.alloc(flush_bytes), "autotune buffer");
-                FE_CUDA(win.alloc(sizeof(float) * n * win_ld(P.n_q)), "autotune buffer");
+                // the factor kernel's windows: one per cell (simplices) or one per
+                // pair and one for the mass form (boxed cells), as win_bytes
+                FE_CUDA(win.alloc(sizeof(float) * n * win_ld(P.n_q) * win_slots(&P)), "autotune buffer");
                 FE_CUDA(cellf.alloc(sizeof(float) * n * CELLF), "autotune buffer");
                 FE_CUDA(out.alloc(sizeof(float) * n * P.n_phi * P.n_phi), "autotune buffer");
                 std::vector<double> ones((size_t)n * P.n_q, 1.0);
@@ -797,6 +1012,10 @@ fe_status fe_assemble(fe_plan *plan, unsigned forms, fe_precision prec, const do
     if (st) return st;
     if (!kappa) return fail(FE_ERR_INVALID_ARG, "NULL kappa");
     const bool fp64 = prec == FE_PREC_FP64;
+    if (!fp64 && !A_stiffness && !A_mass && plan->fuse_ok && plan->fuse_mode == 1) {
+        void *csr[2] = {csr_stiffness, csr_mass};
+        return run_fused(plan, forms, prec, vertices, kappa, csr);
+    }
     const size_t ebytes = (fp64 ? 8 : 4) * (size_t)plan->n_cells * plan->n_phi * plan->n_phi;
     void *A[2] = {A_stiffness, A_mass};
     for (int fi = 0; fi < 2; ++fi) {
@@ -861,10 +1080,79 @@ fe_status fe_assemble_host(fe_plan *plan, unsigned forms, fe_precision prec, con
     return fe_sync_status(plan);
 }
 
+fe_status fe_assemble_host_many(fe_plan *plan, unsigned forms, fe_precision prec, int n,
+                                const double *const *kappa_host, void *const *csr_stiffness_host,
+                                void *const *csr_mass_host) {
+    g_err.clear();
+    fe_status st = check_call(plan, forms, prec);
+    if (st) return st;
+    if (n <= 0 || !kappa_host) return fail(FE_ERR_INVALID_ARG, "empty sequence or NULL kappa array");
+    for (int i = 0; i < n; ++i)
+        if (!kappa_host[i]) return fail(FE_ERR_INVALID_ARG, "NULL kappa for item %d", i);
+    fe_plan &P = *plan;
+    const bool fp64 = prec == FE_PREC_FP64;
+    const size_t kbytes = sizeof(double) * (size_t)P.n_cells * P.n_q;
+    const size_t vbytes = (fp64 ? 8 : 4) * (size_t)P.nnz;
+    // two slots of device inputs and outputs (allocated once, kept by the plan)
+    for (int slot = 0; slot < 2; ++slot) {
+        st = ensure_ws(P.ws_pipe_kappa[slot], kbytes, "pipeline kappa workspace");
+        if (st) return st;
+        for (int fi = 0; fi < 2; ++fi)
+            if (forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS)) {
+                st = ensure_ws(P.ws_pipe_csr[slot][fi], vbytes, "pipeline CSR workspace");
+                if (st) return st;
+            }
+    }
+    if (!P.pipe_ready) {
+        FE_CUDA(cudaStreamCreateWithFlags(&P.pipe_h2d, cudaStreamNonBlocking), "pipeline stream");
+        FE_CUDA(cudaStreamCreateWithFlags(&P.pipe_d2h, cudaStreamNonBlocking), "pipeline stream");
+        for (int slot = 0; slot < 2; ++slot) {
+            FE_CUDA(cudaEventCreateWithFlags(&P.pipe_in[slot], cudaEventDisableTiming), "pipeline event");
+            FE_CUDA(cudaEventCreateWithFlags(&P.pipe_used[slot], cudaEventDisableTiming), "pipeline event");
+            FE_CUDA(cudaEventCreateWithFlags(&P.pipe_out[slot], cudaEventDisableTiming), "pipeline event");
+        }
+        P.pipe_ready = true;
+    }
+    // everything issued earlier on the plan's stream comes first
+    FE_CUDA(cudaEventRecord(P.pipe_used[0], P.stream), "pipeline event");
+    FE_CUDA(cudaStreamWaitEvent(P.pipe_h2d, P.pipe_used[0], 0), "pipeline wait");
+    FE_CUDA(cudaStreamWaitEvent(P.pipe_d2h, P.pipe_used[0], 0), "pipeline wait");
+    FE_CUDA(cudaEventRecord(P.pipe_used[1], P.stream), "pipeline event");
+    FE_CUDA(cudaEventRecord(P.pipe_out[0], P.pipe_d2h), "pipeline event");
+    FE_CUDA(cudaEventRecord(P.pipe_out[1], P.pipe_d2h), "pipeline event");
+    for (int i = 0; i < n; ++i) {
+        const int slot = i & 1;
+        // upload item i once the computation of item i - 2 has consumed the slot
+        FE_CUDA(cudaStreamWaitEvent(P.pipe_h2d, P.pipe_used[slot], 0), "pipeline wait");
+        FE_CUDA(cudaMemcpyAsync(P.ws_pipe_kappa[slot].p, kappa_host[i], kbytes, cudaMemcpyHostToDevice, P.pipe_h2d),
+                "copy kappa");
+        FE_CUDA(cudaEventRecord(P.pipe_in[slot], P.pipe_h2d), "pipeline event");
+        // compute item i once its input has landed and item i - 2's results have left the slot
+        FE_CUDA(cudaStreamWaitEvent(P.stream, P.pipe_in[slot], 0), "pipeline wait");
+        FE_CUDA(cudaStreamWaitEvent(P.stream, P.pipe_out[slot], 0), "pipeline wait");
+        void *csr[2] = {P.ws_pipe_csr[slot][0].p, P.ws_pipe_csr[slot][1].p};
+        st = fe_assemble(plan, forms, prec, nullptr, P.ws_pipe_kappa[slot].as<double>(), nullptr, nullptr,
+                         (forms & FE_FORM_STIFFNESS) ? csr[0] : nullptr, (forms & FE_FORM_MASS) ? csr[1] : nullptr);
+        if (st) return st;
+        FE_CUDA(cudaEventRecord(P.pipe_used[slot], P.stream), "pipeline event");
+        // download item i's CSR values
+        FE_CUDA(cudaStreamWaitEvent(P.pipe_d2h, P.pipe_used[slot], 0), "pipeline wait");
+        void *hout[2] = {csr_stiffness_host ? csr_stiffness_host[i] : nullptr, csr_mass_host ? csr_mass_host[i] : nullptr};
+        for (int fi = 0; fi < 2; ++fi)
+            if ((forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS)) && hout[fi])
+                FE_CUDA(cudaMemcpyAsync(hout[fi], csr[fi], vbytes, cudaMemcpyDeviceToHost, P.pipe_d2h), "copy CSR");
+        FE_CUDA(cudaEventRecord(P.pipe_out[slot], P.pipe_d2h), "pipeline event");
+    }
+    FE_CUDA(cudaStreamSynchronize(P.pipe_d2h), "pipeline sync");
+    FE_CUDA(cudaStreamSynchronize(P.pipe_h2d), "pipeline sync");
+    return fe_sync_status(plan);
+}
+
 fe_status fe_adjoint(fe_plan *plan, const double *vertices, const double *kappa, const float *u, const float *v,
                      double *g_kappa, double *g_vertices, double *L_out) {
     g_err.clear();
     if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (plan->boxed) return fail(FE_ERR_UNSUPPORTED, "fe_adjoint: simplices only");
     if (!(plan->form_mask & FE_FORM_STIFFNESS)) return fail(FE_ERR_INVALID_ARG, "plan does not serve stiffness");
     if (!kappa || !u || !v) return fail(FE_ERR_INVALID_ARG, "NULL argument");
     fe_status st;
@@ -904,6 +1192,7 @@ fe_status fe_adjoint_values(fe_plan *plan, const double *vertices, const double 
                             double *g_kappa, double *g_vertices, double *L_out) {
     g_err.clear();
     if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (plan->boxed) return fail(FE_ERR_UNSUPPORTED, "fe_adjoint_values: simplices only");
     if (!(plan->form_mask & FE_FORM_STIFFNESS)) return fail(FE_ERR_INVALID_ARG, "plan does not serve stiffness");
     if (!kappa || !grad_values) return fail(FE_ERR_INVALID_ARG, "NULL argument");
     if ((size_t)plan->n_phi * plan->n_phi * sizeof(double) > (size_t)200 << 10)
@@ -1004,6 +1293,7 @@ fe_status fe_action(fe_plan *plan, unsigned forms, fe_precision prec, const doub
                     const double *w, void *b_stiffness, void *b_mass, void *v_stiffness, void *v_mass) {
     g_err.clear();
     if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (plan->boxed) return fail(FE_ERR_UNSUPPORTED, "fe_action: simplices only");
     if (forms == 0 || (forms & ~plan->form_mask)) return fail(FE_ERR_INVALID_ARG, "forms not served by the plan");
     if (prec != FE_PREC_FP64 && prec != FE_PREC_TF32 && prec != FE_PREC_BF16 && prec != FE_PREC_FP16)
         return fail(FE_ERR_UNSUPPORTED, "fe_action supports FP64, TF32, BF16 and FP16");
@@ -1091,6 +1381,7 @@ fe_status fe_adjoint_noalloc(fe_plan *plan, const double *vertices, const double
                              const float *v, double *g_kappa, double *g_vertices, double *L_out) {
     g_err.clear();
     if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (plan->boxed) return fail(FE_ERR_UNSUPPORTED, "fe_adjoint_noalloc: simplices only");
     if (!(plan->form_mask & FE_FORM_STIFFNESS)) return fail(FE_ERR_INVALID_ARG, "plan does not serve stiffness");
     if (!kappa || !u || !v) return fail(FE_ERR_INVALID_ARG, "NULL argument");
     const size_t per_cell = (g_vertices ? (size_t)(plan->d + 1) * plan->d : 0) + 1;
@@ -1137,6 +1428,7 @@ fe_status fe_geometry(fe_plan *plan, int mode, const double *vertices, int64_t c
                       double *absdet, int32_t *used_fp64) {
     g_err.clear();
     if (!plan || !G) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+    if (plan->boxed) return fail(FE_ERR_UNSUPPORTED, "fe_geometry: simplices only");
     if (mode < FE_GEOMETRY_FP64 || mode > FE_GEOMETRY_MIXED) return fail(FE_ERR_INVALID_ARG, "unknown mode %d", mode);
     if (c0 < 0 || c1 > plan->n_cells || c0 > c1) return fail(FE_ERR_INVALID_ARG, "cell range out of bounds");
     const int r = launch_diag_geometry(vertices ? vertices : plan->vertices.as<double>(), plan->cells.as<int32_t>(), c0,
@@ -1150,6 +1442,7 @@ fe_status fe_mass_fp16_products(fe_plan *plan, const double *kappa, const double
                                 float *b) {
     g_err.clear();
     if (!plan || !kappa || (!A && !b)) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+    if (plan->boxed) return fail(FE_ERR_UNSUPPORTED, "fe_mass_fp16_products: simplices only");
     if (b && !w) return fail(FE_ERR_INVALID_ARG, "the action needs w");
     if (c0 < 0 || c1 > plan->n_cells || c0 > c1) return fail(FE_ERR_INVALID_ARG, "cell range out of bounds");
     const int r = launch_diag_mass_fp16(plan->vertices.as<double>(), plan->cells.as<int32_t>(),
@@ -1227,6 +1520,7 @@ fe_status fe_batch_create(fe_batch **out, fe_plan *const *plans, int n_plans, un
     for (int i = 0; i < n_plans; ++i) {
         fe_status st = check_call(plans[i], forms, prec);
         if (st) return st;
+        if (plans[i]->boxed) return fail(FE_ERR_UNSUPPORTED, "batches take simplex plans only (plan %d is boxed)", i);
         if (!kappa[i]) return fail(FE_ERR_INVALID_ARG, "NULL kappa for plan %d", i);
         if (want_csr) {
             if ((forms & FE_FORM_STIFFNESS) && (!csr_stiffness || !csr_stiffness[i]))
@@ -1317,6 +1611,7 @@ fe_status fe_batch_create(fe_batch **out, fe_plan *const *plans, int n_plans, un
         B.aargs.n_rows = rows;
         B.aargs.n_chunks = chunks;
         B.aargs.n_forms = n_forms_of(forms);
+        B.aargs.algo = plans[0]->asm_algo;
     }
     // one eager run (sets kernel attributes, checks the inputs), then capture
     int launches = 0;

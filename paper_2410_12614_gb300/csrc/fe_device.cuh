@@ -35,15 +35,9 @@ __device__ __forceinline__ void cell_vertices(const double *__restrict__ vertice
     }
 }
 
-// J, its cofactor matrix and det J in FP64 (G left out) from the vertex
-// coordinates; returns the status bits.
-__device__ __forceinline__ int cell_cofactors_x(const double (&x)[4][3], int d, CellGeom &g) {
-    double J[3][3];
+// Cofactor matrix and det J in FP64 from J; returns the status bits.
+__device__ __forceinline__ int cofactors_of(const double (&J)[3][3], int d, CellGeom &g) {
     if (d == 3) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) J[i][j] = x[j + 1][i] - x[0][i];
         g.C[0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
         g.C[1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
         g.C[2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
@@ -55,10 +49,6 @@ __device__ __forceinline__ int cell_cofactors_x(const double (&x)[4][3], int d, 
         g.C[8] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
         g.det = J[0][0] * g.C[0] + J[0][1] * g.C[1] + J[0][2] * g.C[2];
     } else {
-        J[0][0] = x[1][0] - x[0][0];
-        J[0][1] = x[2][0] - x[0][0];
-        J[1][0] = x[1][1] - x[0][1];
-        J[1][1] = x[2][1] - x[0][1];
         g.C[0] = J[1][1];
         g.C[1] = -J[1][0];
         g.C[2] = -J[0][1];
@@ -69,6 +59,42 @@ __device__ __forceinline__ int cell_cofactors_x(const double (&x)[4][3], int d, 
     int st = 0;
     if (!isfinite(g.det)) st |= ST_NONFINITE;
     else if (g.det == 0.0) st |= ST_DEGENERATE;
+    return st;
+}
+
+// J = [x1 - x0, ..., xd - x0] of an affine simplex, its cofactors and det J.
+__device__ __forceinline__ int cell_cofactors_x(const double (&x)[4][3], int d, CellGeom &g) {
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            if (i < d && j < d) J[i][j] = x[j + 1][i] - x[0][i];
+    return cofactors_of(J, d, g);
+}
+
+// Boxed cells: J at one quadrature point of the multilinear map,
+// J_ij = sum_v x_{v,i} dpsi[j][v][q] (dpsi: the Q1 derivative table
+// [d][nv][n_q] at the rule's points), then its cofactors, det J and
+// G = C^T C / |det J|, all in FP64.  Returns the status bits.
+__device__ __forceinline__ int box_point_geometry(const double *__restrict__ xv, int nv, const double *__restrict__ dpsi,
+                                                  int n_q, int q, int d, CellGeom &g) {
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int j = 0; j < d; ++j)
+        for (int v = 0; v < nv; ++v) {
+            const double dp = __ldg(dpsi + ((size_t)j * nv + v) * n_q + q);
+            for (int i = 0; i < d; ++i) J[i][j] = fma(xv[v * 3 + i], dp, J[i][j]);
+        }
+    const int st = cofactors_of(J, d, g);
+    const double inv = (st == 0) ? 1.0 / g.absdet : 0.0;
+    int k = 0;
+    for (int s2 = 0; s2 < d; ++s2)
+        for (int t = s2; t < d; ++t) {
+            double acc = 0.0;
+            for (int r = 0; r < d; ++r) acc = fma(g.C[r * d + s2], g.C[r * d + t], acc);
+            g.G[k++] = acc * inv;
+        }
+    for (; k < 6; ++k) g.G[k] = 0.0;
     return st;
 }
 

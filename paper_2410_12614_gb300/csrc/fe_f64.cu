@@ -5,6 +5,8 @@
 //   H~_s[q][l] = sum_t C_stq B_tlq,   C_stq = w_q kappa_cq G_st   (Sec. 3.1)
 //   A[k][l]    = sum_s sum_q B_skq H~_s[q][l]                      (k <= l)
 // (mass: one "s", C_q = w_q kappa_cq |det J|, B = phi).  Everything is FP64.
+// Boxed cells take G_st and |det J| per quadrature point from geo_q, which
+// box_geometry_kernel forms from the multilinear map at every point.
 // A block owns `tc` cells; the tabulation B and H~ are staged in shared
 // memory `qc` quadrature points at a time; every thread accumulates EPT
 // upper-triangle entries in registers and writes both mirror positions.
@@ -39,7 +41,7 @@ __global__ void __launch_bounds__(F64_THREADS) f64_element_kernel(const __grid_c
         const int64_t cg = cell0 + c;
         double *g = Gs + c * 7;
         for (int j = 0; j < 7; ++j) g[j] = 0.0;
-        if (cg < a.n_cells) {
+        if (cg < a.n_cells && !a.geo_q) {
             CellGeom geo;
             int st = cell_geometry(a.vertices, a.cells, cg, d, geo);
             if (st) {
@@ -85,7 +87,9 @@ __global__ void __launch_bounds__(F64_THREADS) f64_element_kernel(const __grid_c
         for (int i = tid; i < TC * nd * QC * nph; i += F64_THREADS) {
             const int l = i % nph, qq = (i / nph) % QC, s = (i / (nph * QC)) % nd, c = i / (nph * QC * nd);
             const double w = W[c * QC + qq];
+            // simplices: the cell's G; boxed cells: G at this point (zero weight past the ends)
             const double *g = Gs + c * 7;
+            if (a.geo_q && w != 0.0) g = a.geo_q + ((cell0 + c) * a.n_q + q0 + qq) * 7;
             double h;
             if (nd == 1) {
                 h = w * g[6] * tab[l * QC + qq];
@@ -125,7 +129,39 @@ __global__ void __launch_bounds__(F64_THREADS) f64_element_kernel(const __grid_c
     }
 }
 
+// One thread per (cell, point): G pairs and |det J| of a boxed cell at a
+// quadrature point, FP64 (box_point_geometry).
+__global__ void box_geometry_kernel(const double *__restrict__ vertices, const int32_t *__restrict__ cells,
+                                    int64_t n_cells, int d, int nv, const double *__restrict__ dpsi, int n_q,
+                                    double *__restrict__ geo_q, int *status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_cells * n_q) return;
+    const int64_t c = i / n_q;
+    const int q = (int)(i - c * n_q);
+    double xv[8 * 3];
+    for (int v = 0; v < nv; ++v) {
+        const int64_t vid = __ldg(cells + c * nv + v);
+        for (int r = 0; r < 3; ++r) xv[v * 3 + r] = (r < d) ? __ldg(vertices + vid * d + r) : 0.0;
+    }
+    CellGeom g;
+    const int st = box_point_geometry(xv, nv, dpsi, n_q, q, d, g);
+    if (st) atomicOr(status, st);
+    double *o = geo_q + i * 7;
+    for (int j = 0; j < 6; ++j) o[j] = st ? 0.0 : g.G[j];
+    o[6] = st ? 0.0 : g.absdet;
+}
+
 }  // namespace
+
+int launch_box_geometry(const double *vertices, const int32_t *cells, int64_t n_cells, int d, int nv,
+                        const double *dpsi, int n_q, double *geo_q, int *status, cudaStream_t s) {
+    const int64_t n = n_cells * n_q;
+    if (n <= 0) return 0;
+    box_geometry_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(vertices, cells, n_cells, d, nv, dpsi, n_q, geo_q,
+                                                                     status);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? 1 : -(int)e;
+}
 
 int launch_f64_elements(const F64Args &a0, cudaStream_t s) {
     if (a0.n_cells <= 0) return 0;

@@ -138,9 +138,36 @@ bool collapsed_rule(int d, int m, std::vector<double> &pts, std::vector<double> 
     return true;
 }
 
+bool tensor_rule(int d, int m, std::vector<double> &pts, std::vector<double> &wts) {
+    std::vector<double> t, w;
+    if (!gauss_jacobi(m, 0, t, w)) return false;
+    int n = 1;
+    for (int i = 0; i < d; ++i) n *= m;
+    pts.assign((size_t)n * d, 0.0);
+    wts.assign(n, 0.0);
+    for (int q = 0; q < n; ++q) {
+        int r = q;
+        double wq = 1.0;
+        for (int i = 0; i < d; ++i) {   // x index fastest
+            const int ii = r % m;
+            r /= m;
+            pts[(size_t)q * d + i] = t[ii];
+            wq *= w[ii];
+        }
+        wts[q] = wq;
+    }
+    return true;
+}
+
 // --------------------------------------------------------------------------
 // Reference basis
 // --------------------------------------------------------------------------
+int n_phi_box(int d, int p) {
+    int n = 1;
+    for (int i = 0; i < d; ++i) n *= (p + 1);
+    return n;
+}
+
 int n_phi(int d, int p) {
     int64_t n = 1;
     for (int i = 1; i <= d; ++i) n = n * (p + i) / i;
@@ -217,6 +244,49 @@ void tabulate(int d, int p, const double *pts, int n_q, std::vector<double> &phi
             }
             phi[(size_t)n * n_q + q] = acc.v;
             for (int k = 0; k < d; ++k) dphi[((size_t)k * nph + n) * n_q + q] = acc.g[k];
+        }
+    }
+}
+
+// Q_p basis of boxed cells: phi_a(X) = prod_i l_{a_i}(X_i), each 1-D factor
+// l_j(t) = prod_{m != j} (p t - m)/(j - m) evaluated as a dual number (value
+// and derivative), the product over the directions formed with the gradient.
+void tabulate_box(int d, int p, const double *pts, int n_q, std::vector<double> &phi, std::vector<double> &dphi) {
+    const int nph = n_phi_box(d, p);
+    phi.assign((size_t)nph * n_q, 0.0);
+    dphi.assign((size_t)d * nph * n_q, 0.0);
+    std::vector<double> lv((size_t)d * (p + 1)), ld((size_t)d * (p + 1));
+    for (int q = 0; q < n_q; ++q) {
+        for (int i = 0; i < d; ++i) {
+            const double t = pts[q * d + i];
+            for (int j = 0; j <= p; ++j) {
+                double v = 1.0, g = 0.0;   // dual number (v, g) of the running product
+                for (int m = 0; m <= p; ++m) {
+                    if (m == j) continue;
+                    const double inv = 1.0 / (double)(j - m);
+                    const double fv = (p * t - m) * inv, fg = p * inv;
+                    g = g * fv + v * fg;
+                    v = v * fv;
+                }
+                lv[(size_t)i * (p + 1) + j] = v;
+                ld[(size_t)i * (p + 1) + j] = g;
+            }
+        }
+        for (int k = 0; k < nph; ++k) {
+            int a[3] = {0, 0, 0}, r = k;
+            for (int i = 0; i < d; ++i) {
+                a[i] = r % (p + 1);
+                r /= (p + 1);
+            }
+            double v = 1.0;
+            double g[3] = {1.0, 1.0, 1.0};
+            for (int i = 0; i < d; ++i) {
+                const double fv = lv[(size_t)i * (p + 1) + a[i]], fd = ld[(size_t)i * (p + 1) + a[i]];
+                for (int s2 = 0; s2 < d; ++s2) g[s2] *= (s2 == i) ? fd : fv;
+                v *= fv;
+            }
+            phi[(size_t)k * n_q + q] = v;
+            for (int s2 = 0; s2 < d; ++s2) dphi[((size_t)s2 * nph + k) * n_q + q] = g[s2];
         }
     }
 }
@@ -324,10 +394,106 @@ static std::string build_dofmap(int d, int p, int64_t n_vertices, int64_t n_cell
     return "";
 }
 
+// Boxed cells.  Node k (lattice a) weighs each cell vertex v with
+// w_v = prod_i (bit_i(v) ? a_i : p - a_i) (its Q1 coordinates times p^d); its
+// support is the set of vertices with w_v > 0, i.e. the vertex, edge, face or
+// cell interior it lies on.  Entities of each support size are ranked by their
+// sorted global vertex ids; inside an entity the nodes are ranked by their
+// weights listed in that sorted-id order (lexicographic).  dof = vertex id for
+// vertex nodes, else offset(size) + entity rank * nodes per entity + node rank,
+// the sizes in increasing order: the same numbering as keys sorted by (support
+// size, vertex ids, weights), computed entity by entity.
+static std::string build_dofmap_box(int d, int p, int64_t n_vertices, int64_t n_cells, const int32_t *cells,
+                                    std::vector<int32_t> &cell_dofs, int64_t &n_dofs) {
+    const int nv = 1 << d;
+    const int nph = n_phi_box(d, p);
+    std::vector<std::array<int, 8>> W(nph);
+    std::vector<int> supmask(nph, 0);
+    for (int k = 0; k < nph; ++k) {
+        int a[3] = {0, 0, 0}, r = k;
+        for (int i = 0; i < d; ++i) {
+            a[i] = r % (p + 1);
+            r /= (p + 1);
+        }
+        for (int v = 0; v < nv; ++v) {
+            int w = 1;
+            for (int i = 0; i < d; ++i) w *= ((v >> i) & 1) ? a[i] : p - a[i];
+            W[k][v] = w;
+            if (w > 0) supmask[k] |= 1 << v;
+        }
+    }
+    // the distinct supports (local vertex masks) of size >= 2 and the nodes on each
+    std::map<int, std::vector<int>> on_support;
+    for (int k = 0; k < nph; ++k)
+        if (__builtin_popcount(supmask[k]) >= 2) on_support[supmask[k]].push_back(k);
+    // unique global entities per support size, as sorted vertex tuples
+    std::map<int, std::vector<std::array<int32_t, 8>>> ent;
+    for (auto &kv : on_support) {
+        const int mask = kv.first, s = __builtin_popcount(mask);
+        auto &E = ent[s];
+        for (int64_t c = 0; c < n_cells; ++c) {
+            std::array<int32_t, 8> t;
+            t.fill(-1);
+            int n = 0;
+            for (int v = 0; v < nv; ++v)
+                if (mask & (1 << v)) t[n++] = cells[c * nv + v];
+            std::sort(t.begin(), t.begin() + s);
+            E.push_back(t);
+        }
+    }
+    int per_size[9] = {0};
+    for (auto &kv : on_support) per_size[__builtin_popcount(kv.first)] = (int)kv.second.size();
+    int64_t off[10];
+    off[2] = n_vertices;
+    for (int s = 2; s <= 8; ++s) {
+        auto it = ent.find(s);
+        if (it != ent.end()) {
+            std::sort(it->second.begin(), it->second.end());
+            it->second.erase(std::unique(it->second.begin(), it->second.end()), it->second.end());
+        }
+        const int64_t cnt = (it == ent.end()) ? 0 : (int64_t)it->second.size() * per_size[s];
+        off[s + 1] = off[s] + cnt;
+    }
+    n_dofs = off[9];
+    if (n_dofs > INT32_MAX) return "too many degrees of freedom for int32 indices";
+    cell_dofs.assign((size_t)n_cells * nph, -1);
+    std::vector<std::pair<std::array<int, 8>, int>> tuples;
+    for (int64_t c = 0; c < n_cells; ++c) {
+        for (int k = 0; k < nph; ++k)
+            if (__builtin_popcount(supmask[k]) == 1)
+                cell_dofs[c * nph + k] = cells[c * nv + __builtin_ctz(supmask[k])];
+        for (auto &kv : on_support) {
+            const int mask = kv.first, s = __builtin_popcount(mask);
+            // local vertices of the support in increasing global id
+            std::array<std::pair<int32_t, int>, 8> gv;
+            int n = 0;
+            for (int v = 0; v < nv; ++v)
+                if (mask & (1 << v)) gv[n++] = {cells[c * nv + v], v};
+            std::sort(gv.begin(), gv.begin() + s);
+            std::array<int32_t, 8> t;
+            t.fill(-1);
+            for (int i = 0; i < s; ++i) t[i] = gv[i].first;
+            const auto &E = ent[s];
+            const int64_t er = std::lower_bound(E.begin(), E.end(), t) - E.begin();
+            tuples.clear();
+            for (int k : kv.second) {
+                std::array<int, 8> wt;
+                wt.fill(0);
+                for (int i = 0; i < s; ++i) wt[i] = W[k][gv[i].second];
+                tuples.push_back({wt, k});
+            }
+            std::sort(tuples.begin(), tuples.end());
+            for (size_t r = 0; r < tuples.size(); ++r)
+                cell_dofs[c * nph + tuples[r].second] = (int32_t)(off[s] + er * per_size[s] + (int64_t)r);
+        }
+    }
+    return "";
+}
+
 std::string build_pattern(int d, int p, int64_t n_vertices, int64_t n_cells, const int32_t *cells, Pattern &P,
-                          bool with_streams) {
-    if (d != 2 && d != 3) return "cell type must be triangle or tetrahedron";
-    const int nv = d + 1;
+                          bool with_streams, bool boxed, int64_t slice_cells) {
+    if (d != 2 && d != 3) return "cell dimension must be 2 or 3";
+    const int nv = boxed ? (1 << d) : d + 1;
     for (int64_t i = 0; i < n_cells * nv; ++i)
         if (cells[i] < 0 || cells[i] >= n_vertices) return "cell vertex index out of range";
     for (int64_t c = 0; c < n_cells; ++c)
@@ -336,11 +502,12 @@ std::string build_pattern(int d, int p, int64_t n_vertices, int64_t n_cells, con
                 if (cells[c * nv + i] == cells[c * nv + j]) return "cell with a repeated vertex";
     P.d = d;
     P.p = p;
-    P.n_phi = n_phi(d, p);
+    P.n_phi = boxed ? n_phi_box(d, p) : n_phi(d, p);
     P.n_vertices = n_vertices;
     P.n_cells = n_cells;
     const int nph = P.n_phi;
-    std::string err = build_dofmap(d, p, n_vertices, n_cells, cells, P.cell_dofs, P.n_dofs);
+    std::string err = boxed ? build_dofmap_box(d, p, n_vertices, n_cells, cells, P.cell_dofs, P.n_dofs)
+                            : build_dofmap(d, p, n_vertices, n_cells, cells, P.cell_dofs, P.n_dofs);
     if (!err.empty()) return err;
     const int64_t nd = P.n_dofs;
     // incidence dof -> (c, k) with c ascending (counting sort, stable)
@@ -455,20 +622,39 @@ std::string build_pattern(int d, int p, int64_t n_vertices, int64_t n_cells, con
             }
         });
         if (overflow) return "a CSR entry has more than 255 contributions";
-        // assembly chunks, and the codes re-counted from each chunk's first incidence
+        // assembly chunks, and the codes re-counted from each chunk's first incidence;
+        // with slicing a chunk also ends where the completion slice of its rows
+        // (the slice of the row's last incident cell) changes
+        auto row_slice = [&](int64_t i) -> int64_t {
+            return (slice_cells > 0 && iptr[i + 1] > iptr[i]) ? (int64_t)(ielem[iptr[i + 1] - 1] / nph) / slice_cells : 0;
+        };
         P.chunk_row.assign(1, 0);
-        int64_t ent = 0, inc = 0;
+        int64_t ent = 0, inc = 0, cur_slice = row_slice(0);
         for (int64_t i = 0; i < nd; ++i) {
             const int64_t ei = P.contrib_base[i + 1] - P.contrib_base[i], ii = iptr[i + 1] - iptr[i];
-            if (i > P.chunk_row.back() && (ent + ei > kAsmChunkEntries || inc + ii > kAsmChunkIncidences)) {
+            const int64_t sl = row_slice(i);
+            if (i > P.chunk_row.back() &&
+                (ent + ei > kAsmChunkEntries || inc + ii > kAsmChunkIncidences || sl != cur_slice)) {
                 P.chunk_row.push_back((int32_t)i);
                 ent = inc = 0;
             }
+            cur_slice = sl;
             ent += ei;
             inc += ii;
         }
         P.chunk_row.push_back((int32_t)nd);
         const int64_t n_chunks = (int64_t)P.chunk_row.size() - 1;
+        P.chunk_slice.clear();
+        P.slice_span = 0;
+        if (slice_cells > 0) {
+            P.chunk_slice.resize(n_chunks);
+            for (int64_t k = 0; k < n_chunks; ++k) P.chunk_slice[k] = (int32_t)row_slice(P.chunk_row[k]);
+            for (int64_t i = 0; i < nd; ++i)
+                if (iptr[i + 1] > iptr[i]) {
+                    const int64_t lo = (int64_t)(ielem[iptr[i]] / nph) / slice_cells;
+                    P.slice_span = std::max<int>(P.slice_span, (int)(row_slice(i) - lo + 1));
+                }
+        }
         P.chunk_desc.resize((size_t)(n_chunks + 1) * 4);
         for (int64_t k = 0; k <= n_chunks; ++k) {
             const int64_t r = P.chunk_row[k];

@@ -19,6 +19,14 @@ std::vector<int> lattice_nodes(int d, int p);
 // phi [n_phi][n_q] and dphi [d][n_phi][n_q] at the points [n_q][d], FP64.
 void tabulate(int d, int p, const double *pts, int n_q, std::vector<double> &phi, std::vector<double> &dphi);
 
+// Boxed cells (quadrilaterals d = 2, hexahedra d = 3) on the reference
+// [0,1]^d: tensor Gauss-Legendre rule (m points per direction, x fastest),
+// n_phi = (p+1)^d, lattice nodes a in {0..p}^d with node k = a_0 + (p+1)(a_1 +
+// (p+1) a_2), cell vertex v at the corner (bit_0(v), bit_1(v), bit_2(v)).
+bool tensor_rule(int d, int m, std::vector<double> &pts, std::vector<double> &wts);
+int n_phi_box(int d, int p);
+void tabulate_box(int d, int p, const double *pts, int n_q, std::vector<double> &phi, std::vector<double> &dphi);
+
 // Row chunks of the block-wide assembly: consecutive CSR rows holding at most
 // kAsmChunkEntries element entries and kAsmChunkIncidences incidences (a row
 // above the entry limit forms a chunk of its own).
@@ -49,14 +57,24 @@ struct Pattern {
     // chunk, local column l at t * n_phi + l) mapped to their position in the
     // chunk's code order (the concatenated CSR-value segments)
     std::vector<uint16_t> contrib_dest; // [n_cells * n_phi * n_phi]
+    // fused assembly (cells in slices of slice_cells): the slice after which
+    // every row of a chunk is complete (the largest slice of its rows' cells),
+    // and the widest range of slices one row's cells span (+1); empty / 0
+    // without slicing
+    std::vector<int32_t> chunk_slice;   // [n_chunks]
+    int slice_span = 0;
     // vertex -> (cell, local vertex) incidence for the adjoint scatter
     std::vector<int64_t> vinc_ptr;    // [n_vertices+1]
     std::vector<int32_t> vinc;        // c * (d+1) + j, sorted by (vertex, c)
 };
 
-// Returns "" on success, else an error message.
+// Returns "" on success, else an error message.  boxed: cells are
+// quadrilaterals / hexahedra with 2^d vertices in tensor order.
+// slice_cells > 0: assembly chunks also end where the rows' completion slice
+// (the slice of their last incident cell, cells in slices of slice_cells)
+// changes, and chunk_slice / slice_span are filled.
 std::string build_pattern(int d, int p, int64_t n_vertices, int64_t n_cells, const int32_t *cells, Pattern &out,
-                          bool with_streams);
+                          bool with_streams, bool boxed = false, int64_t slice_cells = 0);
 
 // Round x to a binary format with `mbits` explicit mantissa bits, minimum
 // normal exponent `emin` and largest finite value `maxfinite`

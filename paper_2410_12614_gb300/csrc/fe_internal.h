@@ -62,9 +62,17 @@ struct TcSeg {
     int staged;                // 1: staged coalesced epilogue (single pass)
     int64_t tile_begin;        // first global tile of this segment
     // written by the factor kernel, read by the element kernel
-    float *win;                // [n_cells][ldw] w_q kappa_cq in FP32 (zero past n_q)
+    float *win;                // [n_cells][win_slots][ldw] coefficient windows in FP32 (zero past n_q)
     float *cellf;              // [n_cells][CELLF] per-cell factors (CELLF_* slots)
     int ldw;                   // n_q rounded up to a multiple of 4
+    // Simplices: win_slots = 1, the window w_q kappa_cq shared by every pair and
+    // form (G constant per cell, in cellf).  Boxed cells: win_slots = n_pairs + 1,
+    // slot j < n_pairs holding w_q kappa_cq G_j(X_q) and slot n_pairs w_q kappa_cq
+    // |det J(X_q)| (the geometry varies with the point); cellf then carries only
+    // the power-of-two scales.
+    int win_slots;
+    int nv;                    // vertices per cell (d + 1, or 2^d for boxed cells)
+    const double *dpsi;        // boxed cells: Q1 derivatives at the rule's points [d][nv][n_q]
 };
 
 // Per-cell factor record (floats): the scaled geometry of each pair, the
@@ -106,6 +114,7 @@ struct F64Args {
     int tc;              // cells per block
     int qc;              // quadrature points per chunk
     int *status;
+    const double *geo_q; // boxed cells: [n_cells][n_q][7] G pairs and |det J| per point (else null)
 };
 
 // One plan's share of a (possibly batched) assembly launch.
@@ -129,6 +138,11 @@ struct AsmSeg {
     void *out[MAX_FORMS];
     int64_t row_begin;         // first global row of this segment
     int64_t chunk_begin;       // first global chunk of this segment
+    const uint16_t *inc_slot;       // [n_inc][n_phi] column slot of entry (incidence, l) in its row (row kernel)
+    // fused assembly: the element matrices of cell c sit in ring slot
+    // (c / ring_cells) % ring_slots at cell offset c % ring_cells (0: no ring)
+    int64_t ring_cells;
+    int ring_slots;
 };
 
 struct AsmArgs {
@@ -138,7 +152,13 @@ struct AsmArgs {
     int64_t n_rows;            // total rows over all segments
     int64_t n_chunks;          // total chunks over all segments
     int n_forms;
+    const int32_t *chunk_list; // optional: the chunks to assemble (device), walked from its end
+    int64_t list_count;
+    int algo;                  // 0: chunked segmented reduction, 1: one warp per row (assemble_rows_kernel)
+    const int32_t *row_list;   // row kernel, optional: the rows to assemble (device)
+    int64_t row_count;
 };
+constexpr int ASM_ROW_CAP = 512;   // row kernel: longest row summed in shared memory
 
 struct AdjArgs {
     const double *vertices;
@@ -231,6 +251,10 @@ int launch_vector_assemble(int64_t n_dofs, const int64_t *inc_ptr, const int32_t
 // Whether a segment can use the staged epilogue under the given global shape.
 bool tc_can_stage(const TcArgs &a, const TcSeg &seg);
 int launch_f64_elements(const F64Args &a, cudaStream_t s);
+// Boxed cells: G pairs and |det J| at every quadrature point in FP64 into
+// geo_q [n_cells][n_q][7] (the per-point geometry of the FP64 path).
+int launch_box_geometry(const double *vertices, const int32_t *cells, int64_t n_cells, int d, int nv,
+                        const double *dpsi, int n_q, double *geo_q, int *status, cudaStream_t s);
 int launch_assemble(const AsmArgs &a, bool fp64, cudaStream_t s);
 // Capacity (in doubles) of the fixed scratch array of the allocation-free
 // adjoint, and the lookup of its device address on the current device.

@@ -184,9 +184,10 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         const int wrow0 = warp * 32;
         int ac = 0, jb = 0;
         float win[CELL_ROWS ? KCE : 1];
-        // win[i] = w_q kappa_{cell, q}, q = qw * KCE + i (this thread's cell)
-        auto load_own = [&](const float *__restrict__ W, int ldw, int64_t cell, bool valid, int qw) {
-            const float *row = W + cell * ldw + qw * KCE;
+        // win[i] = the window row wrow's entry q = qw * KCE + i (wrow = this
+        // thread's cell, times the slots per cell, plus the slot)
+        auto load_own = [&](const float *__restrict__ W, int ldw, int64_t wrow, bool valid, int qw) {
+            const float *row = W + wrow * ldw + qw * KCE;
 #pragma unroll
             for (int i = 0; i < KCE; i += 4) {
                 const float4 v = (valid && qw * KCE + i < ldw) ? __ldg(reinterpret_cast<const float4 *>(row + i))
@@ -197,15 +198,17 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 win[i + 3] = v.w;
             }
         };
-        // dst[r * QL + i] = w_q kappa_{cell r, q}, q = qw * KCE + lane * QL + i (e4m3)
-        auto load_rows = [&](const float *__restrict__ W, int ldw, int64_t n_cells, int64_t tile_cell0, int qw,
-                             float *dst) {
+        // dst[r * QL + i] = entry q = qw * KCE + lane * QL + i of slot `slot` of
+        // cell r's window (e4m3)
+        auto load_rows = [&](const float *__restrict__ W, int ldw, int slots, int slot, int64_t n_cells,
+                             int64_t tile_cell0, int qw, float *dst) {
             const int q = qw * KCE + lane * QL;
 #pragma unroll
             for (int r = 0; r < 32; ++r) {
                 const int64_t cell_r = tile_cell0 + wrow0 + r;
-                const float4 v = (cell_r < n_cells && q < ldw) ? __ldg(reinterpret_cast<const float4 *>(W + cell_r * ldw + q))
-                                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 v = (cell_r < n_cells && q < ldw)
+                                     ? __ldg(reinterpret_cast<const float4 *>(W + (cell_r * slots + slot) * ldw + q))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
                 dst[r * QL] = v.x;
                 dst[r * QL + 1] = v.y;
                 dst[r * QL + 2] = v.z;
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             const TcSeg &S = seg_of<BATCHED>(a, tt);
             const int64_t c0 = (tt - S.tile_begin) * TC_M;
             const int64_t nc = (S.n_cells - c0) < TC_M ? (S.n_cells - c0) : TC_M;
-            prefetch_l2(S.win + c0 * S.ldw, (uint32_t)(nc * S.ldw * sizeof(float)));
+            prefetch_l2(S.win + c0 * S.ldw * S.win_slots, (uint32_t)(nc * S.ldw * S.win_slots * sizeof(float)));
             prefetch_l2(S.cellf + c0 * CELLF, (uint32_t)(nc * CELLF * sizeof(float)));
         };
         prefetch_tile(blockIdx.x);
@@ -253,9 +256,11 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                     unscale_f[1] = rec[CELLF_UNSCALE + 1];
                 }
             }
-            // a tile whose points fit one window loads it once, here
+            // a tile whose points fit one window (shared by every pair) loads it
+            // once, here; loaded = qw * 16 + slot of the registers' window
+            const int s_slots = S.win_slots;
             int qw_loaded = -1;
-            if (CELL_ROWS && s_nq <= KCE) {
+            if (CELL_ROWS && s_nq <= KCE && s_slots == 1) {
                 load_own(s_win, s_ldw, cell, valid, 0);
                 qw_loaded = 0;
             }
@@ -283,11 +288,13 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         const int j = (ch / op.n_blk) % op.n_pairs;
                         const int blk = ch % op.n_blk;
                         const int cidx = (f == 0) ? j : 6;
+                        // window slot: simplices share one; boxed cells have one per pair and one for the mass form
+                        const int slot = (s_slots == 1) ? 0 : ((f == 0) ? j : s_slots - 1);
                         uint8_t *stA = sm.A + s * (TC_M * TC_CHUNK_BYTES);
                         if constexpr (CELL_ROWS) {
-                            if (qw != qw_loaded) {
-                                qw_loaded = qw;
-                                load_own(s_win, s_ldw, cell, valid, qw);
+                            if (qw * 16 + slot != qw_loaded) {
+                                qw_loaded = qw * 16 + slot;
+                                load_own(s_win, s_ldw, cell * s_slots + slot, valid, qw);
                             }
                             const float gj = sm.rowc[cl * 8 + cidx];
                             uint8_t *rowp = stA + (cl >> 3) * 1024 + (cl & 7) * 128;
@@ -320,7 +327,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                             }
                         } else {
                             float w[32 * QL];
-                            load_rows(s_win, s_ldw, s_ncells, tile_cell0, qw, w);
+                            load_rows(s_win, s_ldw, s_slots, slot, s_ncells, tile_cell0, qw, w);
                             const int byte = lane * 4;   // this lane's word inside a 128-byte row
 #pragma unroll
                             for (int r = 0; r < 32; ++r) {

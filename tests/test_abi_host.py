@@ -91,3 +91,49 @@ def test_pattern_rejects_bad_connectivity():
     with pytest.raises(_lib.FeError) as e:
         api.Pattern("tetrahedron", v.shape[0], c, 9)
     assert e.value.status == -2
+
+
+@pytest.mark.parametrize("cell", ["quadrilateral", "hexahedron"])
+@pytest.mark.parametrize("m", [1, 2, 4, 7])
+def test_tensor_rule_helper_matches_oracle(cell, m):
+    p1, w1 = api.quadrature_rule(cell, m)
+    p2, w2 = oracle.tensor_rule(cell, m)
+    np.testing.assert_allclose(p1, p2, rtol=4e-15, atol=1e-16)
+    np.testing.assert_allclose(w1, w2, rtol=4e-14, atol=0)
+
+
+@pytest.mark.parametrize("cell,n,p", [("quadrilateral", 4, 1), ("quadrilateral", 3, 3), ("quadrilateral", 2, 8),
+                                      ("hexahedron", 3, 1), ("hexahedron", 2, 2), ("hexahedron", 2, 4),
+                                      ("hexahedron", 1, 5)])
+def test_box_pattern_bit_exact_vs_oracle(cell, n, p):
+    # the library numbers boxed-cell dofs entity by entity; the oracle sorts
+    # the nodes' Q1-weight keys: the two must agree bit for bit
+    v, c = inputs.structured_mesh(cell, n, 0.1, 2)
+    pat = api.Pattern(cell, v.shape[0], c, p)
+    dofs, rp, ci = pat.arrays()
+    pr = oracle.Problem(v, c, p, *oracle.rule_for_degree(cell, 1))
+    odofs, nd = pr.cell_dofs()
+    orp, oci = pr.csr_pattern()
+    assert pat.n_dofs == nd == (p * n + 1) ** pr.d
+    assert np.array_equal(dofs, odofs)
+    assert np.array_equal(rp, orp)
+    assert np.array_equal(ci, oci)
+
+
+def test_box_pattern_on_a_permuted_mesh():
+    # renumbered vertices and cells with every cell's corners in tensor order
+    # but the mesh numbering scrambled: entity orientations now differ between
+    # neighbours, and the numbering must still agree with the oracle's keys
+    v, c = inputs.hex_mesh(3, 0.1, 3)
+    rng = np.random.default_rng(4)
+    perm = rng.permutation(len(v))
+    inv = np.argsort(perm)
+    v2 = v[perm]
+    c2 = inv[c][rng.permutation(len(c))].astype(np.int32)
+    for p in (2, 3):
+        pat = api.Pattern("hexahedron", v2.shape[0], c2, p)
+        dofs, rp, ci = pat.arrays()
+        pr = oracle.Problem(v2, c2, p, *oracle.rule_for_degree("hexahedron", 1))
+        odofs, nd = pr.cell_dofs()
+        assert np.array_equal(dofs, odofs)
+        assert np.array_equal(rp, pr.csr_pattern()[0]) and np.array_equal(ci, pr.csr_pattern()[1])

@@ -252,3 +252,40 @@ def test_values_adjoint_matches_finite_differences_in_kappa():
         km[c, q] -= 1e-3
         fd = (L_of(kp) - L_of(km)) / 2e-3
         assert abs(fd - gk[c, q]) <= 1e-9 * np.abs(gk).max()
+
+
+def _L_complex(pr, kap, u, v, X):
+    """L = sum_c u_c^T A^c v_c (stiffness) for complex vertex coordinates X: the
+    element matrix definition (Sec. 3.1) with |det J| replaced by sign(det J) det J
+    (analytic in X, equal to |det J| for real X), J^-1 by complex inversion."""
+    dofs, _ = pr.cell_dofs()
+    x = X[pr.cells]                                                  # [nc, d+1, d]
+    J = np.transpose(x[:, 1:, :] - x[:, :1, :], (0, 2, 1))           # J[:, i, j] = x^{j+1}_i - x^0_i
+    det = np.linalg.det(J)
+    sgn = np.sign(det.real)
+    Ji = np.linalg.inv(J)
+    # physical gradients J^-T grad phi at every point: [nc, k, q, i]
+    grad = np.einsum("cri,rkq->ckqi", Ji, pr.dphi)
+    Ac = np.einsum("q,cq,c,ckqi,clqi->ckl", pr.weights, kap, sgn * det, grad, grad)
+    return np.einsum("ck,ckl,cl->", u[dofs], Ac, v[dofs])
+
+
+@pytest.mark.parametrize("cell,p", [("triangle", 3), ("tetrahedron", 2)])
+def test_adjoint_vertex_gradient_by_complex_step(cell, p):
+    """dL/dx of the oracle's closed form against the complex-step derivative
+    Im L(x + i h e) / h with h = 1e-30: no subtractive cancellation, so the two
+    must agree to rounding (1e-13 of the largest gradient entry)."""
+    pr = _problem(cell, 2, p)
+    kap = inputs.lognormal_kappa(pr.n_cells, pr.n_q, 41)
+    u = inputs.gaussian_vector(pr.n_dofs, 42).astype(np.float64)
+    v = inputs.gaussian_vector(pr.n_dofs, 43).astype(np.float64)
+    L, _, gx = pr.adjoint_stiffness(kap, u, v)
+    X0 = pr.vertices.astype(np.complex128)
+    assert abs(_L_complex(pr, kap, u, v, X0).real - L) <= 1e-12 * abs(L)
+    h = 1e-30
+    for vi in range(pr.vertices.shape[0]):
+        for i in range(pr.d):
+            X = X0.copy()
+            X[vi, i] += 1j * h
+            cs = _L_complex(pr, kap, u, v, X).imag / h
+            assert abs(cs - gx[vi, i]) <= 1e-13 * np.abs(gx).max(), (vi, i, cs, gx[vi, i])
