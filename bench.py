@@ -615,7 +615,7 @@ def run_sweep(args):
     with torch.cuda.stream(stream):
         for p in degrees:
             pts, w = api.quadrature_rule("tetrahedron", p + 1)
-            plan = api.Plan("tetrahedron", v, c, p, pts, w, precisions=precs, stream=stream)
+            plan = api.Plan("tetrahedron", v, c, p, pts, w, precisions=precs, stream=stream, elements_only=True)
             kap = torch.from_numpy(inputs.lognormal_kappa(plan.n_cells, plan.n_q, 5)).cuda()
             nc, nq, nph = plan.n_cells, plan.n_q, plan.n_phi
             flops = 2.0 * (3 + 1) * nq * nph * nph * nc
@@ -655,12 +655,13 @@ def run_sweep(args):
 
 def run_boxed_sweep(args, degrees=None, precs=("bf16", "fp16", "e4m3"), n_by_degree=None):
     """Boxed cells (the paper's 60x case is hexahedra): Q_p hexahedra on a
-    jittered structured mesh (16^3 cells up to Q4, 10^3 at Q5: the CSR pattern
-    every plan builds grows as ((p N + 1)^3 (2p + 1)^3)), kappa lognormal at the
-    (p+1)^3 tensor Gauss-Legendre points, element matrices of both forms per
-    precision and in FP64 (per-point FP64 geometry in every path), inputs
-    resident, L2 flushed before each timed run; the tensor-core speed-up over
-    the FP64 path and the fraction of the roofline as in run_sweep."""
+    jittered structured mesh of N^3 cells (N = 34: 39,304 cells, two full waves
+    of 128-cell tiles; Q5: N = 32), element-matrix-only plans (no CSR pattern,
+    as the paper's kernel experiments), kappa lognormal at the (p+1)^3 tensor
+    Gauss-Legendre points, element matrices of both forms per precision and in
+    FP64 (per-point FP64 geometry in every path), inputs resident, L2 flushed
+    before each timed run; the tensor-core speed-up over the FP64 path and the
+    fraction of the roofline as in run_sweep."""
     import torch
     from paper_2410_12614_gb300 import api, inputs
     hbm, _ = _peaks()
@@ -670,15 +671,15 @@ def run_boxed_sweep(args, degrees=None, precs=("bf16", "fp16", "e4m3"), n_by_deg
         bf16 = 1900.0
     peaks = {"bf16": bf16, "fp16": bf16, "tf32": bf16 / 2, "e4m3": 2 * bf16, "tf32x3": bf16 / 6}
     degrees = degrees or [int(x) for x in args.boxed_degrees.split(",")]
-    n_by_degree = n_by_degree or {1: 16, 2: 16, 3: 16, 4: 16, 5: 10}
+    n_by_degree = n_by_degree or {1: 34, 2: 34, 3: 34, 4: 34, 5: 32}
     stream = torch.cuda.Stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    out = {"mesh": "Q_p hexahedra, N^3 jittered cells (N = 16, Q5: 10)", "runs": []}
+    out = {"mesh": "Q_p hexahedra, N^3 jittered cells (N = 34, Q5: 32), element-matrix-only plans", "runs": []}
     with torch.cuda.stream(stream):
         for p in degrees:
             n = n_by_degree.get(p, 10)
             v, c = inputs.hex_mesh(n, 0.15, 40 + p)
-            plan = api.Plan("hexahedron", v, c, p, precisions=precs, stream=stream)
+            plan = api.Plan("hexahedron", v, c, p, precisions=precs, stream=stream, elements_only=True)
             kap = torch.from_numpy(inputs.lognormal_kappa(plan.n_cells, plan.n_q, 50 + p)).cuda()
             nc, nq, nph = plan.n_cells, plan.n_q, plan.n_phi
             flops = 2.0 * (3 + 1) * nq * nph * nph * nc

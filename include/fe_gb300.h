@@ -75,8 +75,13 @@ typedef enum {
 typedef enum { FE_TRIANGLE = 2, FE_TETRAHEDRON = 3, FE_QUADRILATERAL = 4, FE_HEXAHEDRON = 5 } fe_cell_type;
 
 /* Forms (bitmask).  Sec. 3.1: mass a(w,v) = int z w v and Poisson
- * a(w,v) = int z grad w . grad v with coefficient z = kappa. */
-enum { FE_FORM_MASS = 1, FE_FORM_STIFFNESS = 2 };
+ * a(w,v) = int z grad w . grad v with coefficient z = kappa.
+ * FE_PLAN_ELEMENTS_ONLY, or-ed into fe_plan_create's form mask, builds a plan
+ * for element matrices only (the paper's kernel experiments, Sec. 5): no dof
+ * map, CSR pattern or assembly streams, so plan creation stays cheap on large
+ * high-degree meshes; calls that need them (assembly, actions, adjoints,
+ * fe_csr_pattern, fe_cell_dofs) return FE_ERR_INVALID_ARG. */
+enum { FE_FORM_MASS = 1, FE_FORM_STIFFNESS = 2, FE_PLAN_ELEMENTS_ONLY = 0x100 };
 
 /* Contraction precisions (List 1: the storage precision u_s of C and of the
  * tabulated operand; products and accumulation are FP32 on the tensor cores,

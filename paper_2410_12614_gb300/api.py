@@ -73,7 +73,8 @@ class Plan:
     """One mesh, degree and quadrature rule on the current CUDA device (fe_plan_*)."""
 
     def __init__(self, cell_type: str, vertices, cells, degree: int, points=None, weights=None,
-                 forms=("stiffness", "mass"), precisions=("bf16",), stream: torch.cuda.Stream | None = None):
+                 forms=("stiffness", "mass"), precisions=("bf16",), stream: torch.cuda.Stream | None = None,
+                 elements_only: bool = False):
         lib = load()
         t, self.d = _lib.CELL_TYPES[cell_type]
         self.cell_type = {_lib.FE_TRIANGLE: "triangle", _lib.FE_TETRAHEDRON: "tetrahedron",
@@ -91,6 +92,8 @@ class Plan:
         fmask = 0
         for f in forms:
             fmask |= FORMS[f]
+        if elements_only:
+            fmask |= 0x100   # FE_PLAN_ELEMENTS_ONLY
         pmask = 0
         for p in precisions:
             pmask |= 1 << PRECISIONS[p]

@@ -85,3 +85,24 @@ def test_boxed_rejects_simplex_only_calls():
     with pytest.raises(api._lib.FeError) as e:
         plan.action(kd, w, prec="bf16")
     assert e.value.status == -2
+
+
+def test_elements_only_plan():
+    # FE_PLAN_ELEMENTS_ONLY: the same element matrices without a dof map or
+    # pattern; calls that need them are rejected
+    v, c = inputs.hex_mesh(5, 0.15, 11)
+    full = api.Plan("hexahedron", v, c, 3, precisions=("bf16",))
+    lean = api.Plan("hexahedron", v, c, 3, precisions=("bf16",), elements_only=True)
+    assert lean.n_dofs == 0 and lean.nnz == 0
+    kd = cuda(inputs.lognormal_kappa(full.n_cells, full.n_q, 12))
+    import torch
+    for prec in ("bf16", "fp64"):
+        a = full.element_matrices(kd, prec=prec)
+        b = lean.element_matrices(kd, prec=prec)
+        full.sync()
+        lean.sync()
+        for f in a:
+            assert torch.equal(a[f], b[f])
+    with pytest.raises(api._lib.FeError) as e:
+        lean.assemble(kd, prec="bf16")
+    assert e.value.status == -1
