@@ -96,6 +96,7 @@ struct DevBuf {
 struct fe_plan {
     int d = 0, p = 0, n_phi = 0, n_q = 0, n_pairs = 0, n_sym = 0;
     bool boxed = false;                  // quadrilaterals / hexahedra: geometry per quadrature point
+    bool elements_only = false;          // FE_PLAN_ELEMENTS_ONLY: no dof map, pattern or assembly streams
     int nv = 0;                          // vertices per cell
     DevBuf dpsi_box;                     // boxed: Q1 derivatives at the rule's points [d][nv][n_q]
     DevBuf ws_geoq;                      // boxed FP64 path: G pairs and |det J| per point [n_cells][n_q][7]
@@ -174,6 +175,7 @@ static cudaError_t upload(DevBuf &b, const std::vector<T> &v, cudaStream_t s) {
 
 static fe_status pack_operand(fe_plan &P, int prec, int fi, int np_pass);
 static fe_status autotune_plan(fe_plan &P);
+static fe_status need_pattern(const fe_plan *plan);
 
 extern "C" {
 
@@ -278,6 +280,8 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
         return fail(FE_ERR_UNSUPPORTED, "degree %d not supported for this cell type", degree);
     if (mesh->n_vertices <= 0 || mesh->n_cells <= 0) return fail(FE_ERR_INVALID_ARG, "empty mesh");
     if (rule->n_q <= 0 || rule->n_q > 4096) return fail(FE_ERR_UNSUPPORTED, "n_q must lie in 1..4096");
+    const bool elements_only = (form_mask & FE_PLAN_ELEMENTS_ONLY) != 0;
+    form_mask &= ~(unsigned)FE_PLAN_ELEMENTS_ONLY;
     if (form_mask == 0 || (form_mask & ~3u)) return fail(FE_ERR_INVALID_ARG, "bad form mask");
     if (prec_mask == 0 || (prec_mask & ~63u)) return fail(FE_ERR_INVALID_ARG, "bad precision mask");
     for (int64_t i = 0; i < mesh->n_vertices * d; ++i)
@@ -313,8 +317,19 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
     host::Pattern pat;
     // slices of one wave of tiles for the fused assembly
     P.fuse_cells = (int64_t)std::max(1, P.sms) * TC_M;
-    std::string err = host::build_pattern(d, degree, mesh->n_vertices, mesh->n_cells, mesh->cells, pat, true, boxed);
-    if (!err.empty()) return fail(FE_ERR_INVALID_ARG, "%s", err.c_str());
+    P.elements_only = elements_only;
+    if (elements_only) {
+        // no dof map, pattern or assembly streams: check the connectivity only
+        for (int64_t i = 0; i < mesh->n_cells * P.nv; ++i)
+            if (mesh->cells[i] < 0 || mesh->cells[i] >= mesh->n_vertices)
+                return fail(FE_ERR_INVALID_ARG, "cell vertex index out of range");
+        pat.chunk_row.assign(1, 0);
+        pat.inc_ptr.assign(1, 0);
+    } else {
+        std::string err =
+            host::build_pattern(d, degree, mesh->n_vertices, mesh->n_cells, mesh->cells, pat, true, boxed);
+        if (!err.empty()) return fail(FE_ERR_INVALID_ARG, "%s", err.c_str());
+    }
     P.n_dofs = pat.n_dofs;
     P.nnz = pat.nnz;
     P.max_row = pat.max_row;
@@ -518,6 +533,7 @@ fe_status fe_plan_sizes(const fe_plan *plan, int64_t *n_cells, int64_t *n_vertic
 
 fe_status fe_csr_pattern(const fe_plan *plan, int64_t *row_ptr, int32_t *col_idx) {
     if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (need_pattern(plan)) return FE_ERR_INVALID_ARG;
     if (row_ptr)
         FE_CUDA(cudaMemcpyAsync(row_ptr, plan->row_ptr.p, sizeof(int64_t) * (plan->n_dofs + 1),
                                 cudaMemcpyDeviceToDevice, plan->stream), "copy row_ptr");
@@ -529,6 +545,7 @@ fe_status fe_csr_pattern(const fe_plan *plan, int64_t *row_ptr, int32_t *col_idx
 
 fe_status fe_cell_dofs(const fe_plan *plan, int32_t *cell_dofs) {
     if (!plan || !cell_dofs) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+    if (need_pattern(plan)) return FE_ERR_INVALID_ARG;
     FE_CUDA(cudaMemcpyAsync(cell_dofs, plan->cell_dofs.p, sizeof(int32_t) * plan->n_cells * plan->n_phi,
                             cudaMemcpyDeviceToDevice, plan->stream), "copy dofs");
     return FE_OK;
@@ -582,6 +599,12 @@ static void mark(fe_plan *P, int stage, bool begin) {
     if (!P->timing) return;
     cudaEventRecord(P->ev[2 * stage + (begin ? 0 : 1)], P->stream);
     if (!begin) P->stage_marks |= 1 << stage;
+}
+
+static fe_status need_pattern(const fe_plan *plan) {
+    if (plan && plan->elements_only)
+        return fail(FE_ERR_INVALID_ARG, "the plan was built with FE_PLAN_ELEMENTS_ONLY: no dof map or pattern");
+    return FE_OK;
 }
 
 static fe_status check_call(fe_plan *plan, unsigned forms, fe_precision prec) {
@@ -652,15 +675,28 @@ static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status, un
     a.np_max = 16;
     a.nq_max = 1;
     a.pitch_max = 0;
-    int64_t tiles = 0;
+    int64_t tiles = 0, jobs = 0, cost = 0;
     for (int i = 0; i < n; ++i) {
+        int tile_cost = 0, tile_jobs = 0;
         for (int f = 0; f < MAX_FORMS; ++f)
-            if ((segs[i].form_mask >> f) & 1) a.np_max = std::max(a.np_max, segs[i].op[f].NP);
+            if ((segs[i].form_mask >> f) & 1) {
+                const TcOperand &op = segs[i].op[f];
+                a.np_max = std::max(a.np_max, op.NP);
+                tile_cost += op.n_pass * (op.n_kchunks + TC_JOB_EPI_COST);
+                tile_jobs += op.n_pass;
+            }
         a.nq_max = std::max(a.nq_max, segs[i].n_q);
         segs[i].tile_begin = tiles;
-        tiles += (segs[i].n_cells + TC_M - 1) / TC_M;
+        segs[i].tiles = (segs[i].n_cells + TC_M - 1) / TC_M;
+        segs[i].cost_begin = cost;
+        segs[i].tile_cost = tile_cost;
+        tiles += segs[i].tiles;
+        jobs += segs[i].tiles * tile_jobs;
+        cost += segs[i].tiles * tile_cost;
     }
     a.n_tiles = tiles;
+    a.n_jobs = jobs;
+    a.total_cost = cost;
     for (int i = 0; i < n; ++i) {
         if (tc_can_stage(a, segs[i])) {
             segs[i].staged = 1;
@@ -672,6 +708,22 @@ static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status, un
     }
     a.status = status;
     a.timeout_ns = wait_limit_ns;  // per wait, counted from the wait's start
+    // operand rings beside the staging area: the shared-operand ring first
+    // (each stage is one more bulk copy in flight against the L2 latency), up
+    // to four stages, then a third built-operand stage (slack for the builders'
+    // window loads), then shared-operand stages up to the maximum
+    a.ring_a = a.ring_b = 2;
+    const auto grow = [&a](int &r, int to) {
+        while (r < to) {
+            ++r;
+            if (tc_smem_bytes(a) > 227 * 1024) {
+                --r;
+                return false;
+            }
+        }
+        return true;
+    };
+    if (grow(a.ring_b, 4) && grow(a.ring_a, 3)) grow(a.ring_b, TC_MAX_RING_B);
 }
 
 static AsmSeg make_asm_seg(fe_plan *P, unsigned forms, const void *const A[2], void *const csr[2]) {
@@ -1010,6 +1062,8 @@ fe_status fe_assemble(fe_plan *plan, unsigned forms, fe_precision prec, const do
     g_err.clear();
     fe_status st = check_call(plan, forms, prec);
     if (st) return st;
+    st = need_pattern(plan);
+    if (st) return st;
     if (!kappa) return fail(FE_ERR_INVALID_ARG, "NULL kappa");
     const bool fp64 = prec == FE_PREC_FP64;
     if (!fp64 && !A_stiffness && !A_mass && plan->fuse_ok && plan->fuse_mode == 1) {
@@ -1041,6 +1095,8 @@ fe_status fe_assemble_elements(fe_plan *plan, unsigned forms, fe_precision prec,
     g_err.clear();
     fe_status st = check_call(plan, forms, prec);
     if (st) return st;
+    st = need_pattern(plan);
+    if (st) return st;
     const void *A[2] = {A_stiffness, A_mass};
     for (int fi = 0; fi < 2; ++fi)
         if ((forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS)) && !A[fi])
@@ -1056,6 +1112,8 @@ fe_status fe_assemble_host(fe_plan *plan, unsigned forms, fe_precision prec, con
                            void *csr_stiffness_host, void *csr_mass_host) {
     g_err.clear();
     fe_status st = check_call(plan, forms, prec);
+    if (st) return st;
+    st = need_pattern(plan);
     if (st) return st;
     if (!kappa_host) return fail(FE_ERR_INVALID_ARG, "NULL kappa");
     const bool fp64 = prec == FE_PREC_FP64;
@@ -1085,6 +1143,8 @@ fe_status fe_assemble_host_many(fe_plan *plan, unsigned forms, fe_precision prec
                                 void *const *csr_mass_host) {
     g_err.clear();
     fe_status st = check_call(plan, forms, prec);
+    if (st) return st;
+    st = need_pattern(plan);
     if (st) return st;
     if (n <= 0 || !kappa_host) return fail(FE_ERR_INVALID_ARG, "empty sequence or NULL kappa array");
     for (int i = 0; i < n; ++i)
@@ -1152,6 +1212,7 @@ fe_status fe_adjoint(fe_plan *plan, const double *vertices, const double *kappa,
                      double *g_kappa, double *g_vertices, double *L_out) {
     g_err.clear();
     if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (need_pattern(plan)) return FE_ERR_INVALID_ARG;
     if (plan->boxed) return fail(FE_ERR_UNSUPPORTED, "fe_adjoint: simplices only");
     if (!(plan->form_mask & FE_FORM_STIFFNESS)) return fail(FE_ERR_INVALID_ARG, "plan does not serve stiffness");
     if (!kappa || !u || !v) return fail(FE_ERR_INVALID_ARG, "NULL argument");
@@ -1192,6 +1253,7 @@ fe_status fe_adjoint_values(fe_plan *plan, const double *vertices, const double 
                             double *g_kappa, double *g_vertices, double *L_out) {
     g_err.clear();
     if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (need_pattern(plan)) return FE_ERR_INVALID_ARG;
     if (plan->boxed) return fail(FE_ERR_UNSUPPORTED, "fe_adjoint_values: simplices only");
     if (!(plan->form_mask & FE_FORM_STIFFNESS)) return fail(FE_ERR_INVALID_ARG, "plan does not serve stiffness");
     if (!kappa || !grad_values) return fail(FE_ERR_INVALID_ARG, "NULL argument");
@@ -1293,6 +1355,7 @@ fe_status fe_action(fe_plan *plan, unsigned forms, fe_precision prec, const doub
                     const double *w, void *b_stiffness, void *b_mass, void *v_stiffness, void *v_mass) {
     g_err.clear();
     if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (need_pattern(plan)) return FE_ERR_INVALID_ARG;
     if (plan->boxed) return fail(FE_ERR_UNSUPPORTED, "fe_action: simplices only");
     if (forms == 0 || (forms & ~plan->form_mask)) return fail(FE_ERR_INVALID_ARG, "forms not served by the plan");
     if (prec != FE_PREC_FP64 && prec != FE_PREC_TF32 && prec != FE_PREC_BF16 && prec != FE_PREC_FP16)
@@ -1381,6 +1444,7 @@ fe_status fe_adjoint_noalloc(fe_plan *plan, const double *vertices, const double
                              const float *v, double *g_kappa, double *g_vertices, double *L_out) {
     g_err.clear();
     if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (need_pattern(plan)) return FE_ERR_INVALID_ARG;
     if (plan->boxed) return fail(FE_ERR_UNSUPPORTED, "fe_adjoint_noalloc: simplices only");
     if (!(plan->form_mask & FE_FORM_STIFFNESS)) return fail(FE_ERR_INVALID_ARG, "plan does not serve stiffness");
     if (!kappa || !u || !v) return fail(FE_ERR_INVALID_ARG, "NULL argument");
@@ -1521,6 +1585,7 @@ fe_status fe_batch_create(fe_batch **out, fe_plan *const *plans, int n_plans, un
         fe_status st = check_call(plans[i], forms, prec);
         if (st) return st;
         if (plans[i]->boxed) return fail(FE_ERR_UNSUPPORTED, "batches take simplex plans only (plan %d is boxed)", i);
+        if (want_csr && need_pattern(plans[i])) return FE_ERR_INVALID_ARG;
         if (!kappa[i]) return fail(FE_ERR_INVALID_ARG, "NULL kappa for plan %d", i);
         if (want_csr) {
             if ((forms & FE_FORM_STIFFNESS) && (!csr_stiffness || !csr_stiffness[i]))

@@ -17,6 +17,7 @@
 //    storage format (List 1, u_s) and laid out as 128-byte-swizzled K-major
 //    tiles for the tensor cores.
 #include "fe_host.h"
+#include "fe_internal.h"
 
 #include <algorithm>
 #include <climits>
@@ -763,6 +764,9 @@ std::vector<int> np_candidates(int n_phi_) {
         return out;
     }
     out.push_back(-row_block_rows(n_phi_));
+    // half as many rows per pass: a smaller staging area leaves room for a
+    // deeper operand ring
+    if (row_block_rows(n_phi_) >= 2) out.push_back(-(row_block_rows(n_phi_) / 2));
     const int passes = (n_sym + 255) / 256;
     out.push_back(256);
     // the narrowest multiple of 16 with the same number of passes
@@ -906,8 +910,15 @@ void build_operand(int prec, int form, int d, int n_phi_, int n_q, const std::ve
     img.p_inv_scale = std::ldexp(1.0, -eP);
     img.n_blk = (prec == FE_PREC_TF32X3) ? 3 : 1;
     img.n_pairs = n_pairs;
-    img.n_qw = (n_q + KCE - 1) / KCE;
-    img.n_kchunks = img.n_qw * n_pairs * img.n_blk;
+    // K blocks (quadrature window qw of KW points, pair j, split block blk),
+    // numbered h = (qw n_pairs + j) n_blk + blk; a 128-byte chunk holds
+    // KCE / KW consecutive blocks (two 64-point blocks for e4m3, so that a
+    // builder thread needs only a 64-point window, one block otherwise)
+    const int KW = tc_window_points(prec);
+    const int WPC = KCE / KW;
+    img.n_qw = (n_q + KW - 1) / KW;
+    const int n_blocks = img.n_qw * n_pairs * img.n_blk;
+    img.n_kchunks = (n_blocks + WPC - 1) / WPC;
     img.n_cols = n_sym;
     if (np_pass == 0 && row_block_default(n_phi_)) np_pass = -row_block_rows(n_phi_);
     if (np_pass < 0) {
@@ -957,17 +968,18 @@ void build_operand(int prec, int form, int d, int n_phi_, int n_q, const std::ve
     img.bytes.assign(block * img.n_kchunks * img.n_pass, 0);
     for (int n = 0; n < img.n_pass; ++n)
         for (int ch = 0; ch < img.n_kchunks; ++ch) {
-            const int qw = ch / (n_pairs * img.n_blk);
-            const int j = (ch / img.n_blk) % n_pairs;
-            const int blk = ch % img.n_blk;
             uint8_t *base = img.bytes.data() + ((size_t)n * img.n_kchunks + ch) * block;
             for (int r = 0; r < img.NP; ++r) {
                 const int col = n * img.NP + r;
                 const int pr = pair_at[col];
                 for (int e = 0; e < KCE; ++e) {
-                    const int q = qw * KCE + e;
+                    const int h = ch * WPC + e / KW;   // K block of this byte range
+                    const int qw = h / (n_pairs * img.n_blk);
+                    const int j = (h / img.n_blk) % n_pairs;
+                    const int blk = h % img.n_blk;
+                    const int q = qw * KW + e % KW;
                     double v = 0.0;
-                    if (pr >= 0 && q < n_q) {
+                    if (pr >= 0 && h < n_blocks && q < n_q) {
                         const std::vector<double> &src = (blk == 1) ? lo : hi;  // C_hi P_hi, C_hi P_lo, C_lo P_hi
                         v = src[(size_t)(q * n_pairs + j) * n_sym + pr];
                     }

@@ -24,12 +24,23 @@ constexpr int TC_STAGES = 2;
 constexpr int TC_CHUNK_BYTES = 128;      // one 128B-swizzled K-major row per chunk
 constexpr int TC_MAX_NP = 256;           // N of one MMA pass
 constexpr int MAX_FORMS = 2;             // 0 = stiffness, 1 = mass
+constexpr int TC_JOB_EPI_COST = 2;       // a job's epilogue, in K chunks, for the work split
+constexpr int TC_MAX_RING_A = 3;         // deepest ring of built (per-cell) operand chunks
+constexpr int TC_MAX_RING_B = 8;         // deepest ring of shared-operand chunks in flight
+
+// Quadrature points per window (K block) for a storage format: 64 for every
+// format of at most 16 bits, 32 for TF32.
+__host__ __device__ constexpr int tc_window_points(int prec) {
+    return prec == FE_PREC_TF32 || prec == FE_PREC_TF32X3 ? 32 : 64;
+}
 
 // Operand description of one form in one precision.
-// K is split into 128-byte chunks; chunk ch holds the quadrature window
-// qw (KCE = 128/elem_bytes consecutive points) of pair j and split block
-// blk, ch = (qw * n_pairs + j) * n_blk + blk.  Each chunk of the shared
-// operand is stored as an NP x 128 B swizzled K-major tile.
+// K is split into blocks h = (qw * n_pairs + j) * n_blk + blk: quadrature
+// window qw (KW = tc_window_points consecutive points) of pair j and split
+// block blk.  A 128-byte chunk holds KCE / KW consecutive blocks (KCE =
+// 128/elem_bytes elements): one for the 16- and 32-bit formats (KW = KCE),
+// two 64-point blocks for e4m3.  Each chunk of the shared operand is stored
+// as an NP x 128 B swizzled K-major tile.
 struct TcOperand {
     const uint8_t *img = nullptr;  // [n_pass][n_kchunks][NP][128 B] swizzled images
     int n_kchunks = 0;             // K chunks of 128 bytes
@@ -61,6 +72,12 @@ struct TcSeg {
     const int16_t *full2sym;   // [n_phi * n_phi] operand column of entry (k, l)
     int staged;                // 1: staged coalesced epilogue (single pass)
     int64_t tile_begin;        // first global tile of this segment
+    int64_t tiles;             // tiles of this segment
+    // Work split: a job is one (tile, form, N pass) and costs the form's K
+    // chunks plus TC_JOB_EPI_COST; every tile of a segment costs tile_cost,
+    // and the segment's first job starts at cost_begin of the launch's total.
+    int64_t cost_begin;
+    int tile_cost;
     // written by the factor kernel, read by the element kernel
     float *win;                // [n_cells][win_slots][ldw] coefficient windows in FP32 (zero past n_q)
     float *cellf;              // [n_cells][CELLF] per-cell factors (CELLF_* slots)
@@ -88,6 +105,8 @@ struct TcArgs {
     const TcSeg *segs;         // device array of n_segs segments (batched launch)
     int n_segs;
     int64_t n_tiles;           // total tiles over all segments
+    int64_t n_jobs;            // (tile, form, pass) jobs over all segments
+    int64_t total_cost;        // summed job costs; CTA i of G takes the jobs starting in [iT/G, (i+1)T/G)
     int prec;                  // fe_precision
     int elem_bytes;            // storage bytes per operand element
     uint32_t idesc;            // instruction descriptor without the N field
@@ -95,6 +114,8 @@ struct TcArgs {
     int np_max;                // largest N per pass over the segments
     int nq_max;                // largest n_q
     int pitch_max;             // staging pitch (floats) over staged segments, 0 if none
+    int ring_a;                // stages of the built-operand ring (2..TC_MAX_RING_A)
+    int ring_b;                // stages of the shared-operand ring (2..TC_MAX_RING_B)
     int *status;
     unsigned long long timeout_ns;
 };

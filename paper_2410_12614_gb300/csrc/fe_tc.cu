@@ -22,12 +22,14 @@
 // The cell batching of Sec. 3.1 is generalised to uneven meshes: the global
 // tile sequence is the concatenation of every segment's (plan's) tiles, each
 // tile carrying its segment's shapes (cell type, degree, quadrature size) and
-// buffers.  One CTA per SM walks its tiles; a job is one (tile, form, N pass).
+// buffers.  A job is one (tile, form, N pass); one CTA per SM takes a
+// contiguous run of jobs of equal cost (K chunks plus an epilogue share), so
+// the SMs stay evenly loaded when the tiles do not divide over them.
 // Roles:
 //   warps 0-3  builders, one thread per cell: its factors and its window
 //              (shared by every (s,t) pair and both forms) in registers, its
-//              128-byte swizzled K-major row of C written into a 2-stage ring
-//              (one a_full arrival per warp).
+//              128-byte swizzled K-major row of C written into a 2- or 3-stage
+//              ring (one a_full arrival per warp).
 //   warps 4-11 epilogue, two warps per TMEM lane group: drain a finished
 //              accumulator into a conflict-free staging area, release it, and
 //              write row-major element matrices with coalesced stores: whole
@@ -35,9 +37,13 @@
 //              k > l; the columns are ordered so that these gathers hit
 //              distinct banks), or, for the full-row layout of large
 //              elements, each pass's rows as one contiguous run.
-//   warp 12    bulk copies of the pre-swizzled P chunks into a 2-stage ring
-//              (one 1-D copy per chunk, no multicast) and tcgen05.mma into
-//              one of two 256-column FP32 TMEM accumulators (lane 0 issues).
+//   warp 12    tcgen05.mma into one of two 256-column FP32 TMEM accumulators
+//              (lane 0 issues); it only waits for operands, never for its own
+//              MMAs, so the tensor pipe always has the next chunk queued.
+//   warp 13    bulk copies of the pre-swizzled P chunks (one 1-D copy per
+//              chunk, no multicast) into a ring of 2-8 stages, as deep as shared
+//              memory allows beside the staging area: the copies in flight
+//              cover the L2 latency of the next chunks.
 // So the build of tile t+1, the MMAs and the stores of tile t overlap.  Every
 // wait is bounded (globaltimer): a wait that sees no progress for the launch's
 // limit (timeout_ns, counted from the start of that wait) sets the status word
@@ -50,17 +56,17 @@ namespace fe {
 
 namespace {
 
-constexpr int V_THREADS = 416;   // 13 warps
+constexpr int V_THREADS = 448;   // 14 warps
 constexpr int W_EPI0 = 4;        // warps 4-11: epilogue, two per TMEM lane group
 constexpr int N_EPI = 8;
 constexpr int W_MMA = 12;
-constexpr int RING = 2;          // A and B ring stages
+constexpr int W_PROD = 13;       // bulk copies of the shared operand
 constexpr int ACC_COLS = 256;    // columns per TMEM accumulator (2 of them)
 constexpr int MAX_F2S_IT = 16;   // n_phi^2 <= 512 for the staged epilogue
 
 struct Smem {
-    uint8_t *A;        // [RING][128][128 B]
-    uint8_t *B;        // [RING][np_max][128 B]
+    uint8_t *A;        // [ring_a][128][128 B]
+    uint8_t *B;        // [ring_b][np_max][128 B]
     float *stage;      // [4][32][pitch_max]
     float *meta;       // [2][128] unscale per cell for the two accumulators
     float *rowc;       // [128][8] per cell: G pairs * scale (stiffness), |det J| * scale (mass)
@@ -70,8 +76,8 @@ struct Smem {
 };
 
 __host__ __device__ inline size_t align1k(size_t x) { return (x + 1023) & ~size_t(1023); }
-__host__ __device__ inline size_t bytes_A() { return (size_t)RING * TC_M * TC_CHUNK_BYTES; }
-__host__ __device__ inline size_t bytes_B(const TcArgs &a) { return (size_t)RING * a.np_max * TC_CHUNK_BYTES; }
+__host__ __device__ inline size_t bytes_A(const TcArgs &a) { return (size_t)a.ring_a * TC_M * TC_CHUNK_BYTES; }
+__host__ __device__ inline size_t bytes_B(const TcArgs &a) { return (size_t)a.ring_b * a.np_max * TC_CHUNK_BYTES; }
 __host__ __device__ inline size_t bytes_stage(const TcArgs &a) {
     return a.pitch_max > 0 ? align1k((size_t)4 * 32 * a.pitch_max * sizeof(float)) : 0;
 }
@@ -80,7 +86,7 @@ __device__ inline Smem carve(uint8_t *raw, const TcArgs &a) {
     uintptr_t p = (reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023);
     Smem s;
     s.A = reinterpret_cast<uint8_t *>(p);
-    s.B = s.A + bytes_A();
+    s.B = s.A + bytes_A(a);
     s.stage = reinterpret_cast<float *>(s.B + bytes_B(a));
     uint8_t *q = reinterpret_cast<uint8_t *>(s.stage) + bytes_stage(a);
     s.meta = reinterpret_cast<float *>(q);
@@ -89,10 +95,10 @@ __device__ inline Smem carve(uint8_t *raw, const TcArgs &a) {
     q = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(q) + 7) & ~uintptr_t(7));
     uint64_t *b = reinterpret_cast<uint64_t *>(q);
     s.a_full = b;
-    s.a_empty = b + RING;
-    s.b_full = b + 2 * RING;
-    s.b_empty = b + 3 * RING;
-    s.acc_full = b + 4 * RING;
+    s.a_empty = b + TC_MAX_RING_A;
+    s.b_full = b + 2 * TC_MAX_RING_A;
+    s.b_empty = s.b_full + TC_MAX_RING_B;
+    s.acc_full = s.b_empty + TC_MAX_RING_B;
     s.acc_empty = s.acc_full + 2;
     s.meta_full = s.acc_empty + 2;
     s.meta_empty = s.meta_full + 2;
@@ -117,6 +123,67 @@ __device__ __forceinline__ const TcSeg &seg_of(const TcArgs &a, int64_t t) {
 
 __device__ __forceinline__ int first_form(const TcSeg &S) { return (S.form_mask & 1) ? 0 : 1; }
 
+// The launch's jobs, (tile, form, N pass), in order: tiles in global order,
+// then the tile's forms, then the passes.  A job costs its form's K chunks
+// plus TC_JOB_EPI_COST.  CTA i of G takes the contiguous jobs whose cost
+// offset lies in [i T / G, (i + 1) T / G) of the total T, so the CTAs get the
+// same work to within one job even when the tiles do not divide evenly over
+// the SMs (a few hundred tiles of a high-degree element).  A tile may be
+// split between two CTAs at a form or pass boundary.  Every role walks the
+// same sequence with its own cursor.
+template <bool BATCHED>
+struct Jobs {
+    const TcSeg *S;   // segment of tile t
+    int64_t t;        // global tile
+    int f, n;         // form, pass
+    int64_t c;        // cost offset of this job
+    int64_t hi;       // end of this CTA's cost range
+    int64_t n_tiles;
+
+    __device__ __forceinline__ bool live() const { return c < hi && t < n_tiles; }
+
+    __device__ __forceinline__ void advance() {
+        const TcOperand &op = S->op[f];
+        c += op.n_kchunks + TC_JOB_EPI_COST;
+        if (++n < op.n_pass) return;
+        n = 0;
+        int nf = f + 1;
+        while (nf < MAX_FORMS && !(S->form_mask & (1 << nf))) ++nf;
+        if (nf < MAX_FORMS) {
+            f = nf;
+            return;
+        }
+        if (++t >= n_tiles) return;
+        if (BATCHED)
+            while (t >= S->tile_begin + S->tiles) ++S;   // t < n_tiles: a later segment holds it
+        f = first_form(*S);
+    }
+
+    __device__ __forceinline__ void start(const TcArgs &a, int i, int G) {
+        n_tiles = a.n_tiles;
+        const int64_t T = a.total_cost;
+        const int64_t lo = T * i / G;
+        hi = T * (i + 1) / G;
+        if (BATCHED) {
+            int l = 0, h = a.n_segs - 1;   // the last segment starting at or before lo
+            while (l < h) {
+                const int mid = (l + h + 1) >> 1;
+                if (a.segs[mid].cost_begin <= lo) l = mid; else h = mid - 1;
+            }
+            S = a.segs + l;
+        } else {
+            S = &a.seg0;
+        }
+        int64_t tt = S->tile_cost > 0 ? (lo - S->cost_begin) / S->tile_cost : 0;
+        if (tt >= S->tiles) tt = S->tiles - 1;
+        t = S->tile_begin + tt;
+        c = S->cost_begin + tt * S->tile_cost;
+        f = first_form(*S);
+        n = 0;
+        while (c < lo && t < n_tiles) advance();   // at most one tile's jobs
+    }
+};
+
 template <int PREC, bool BATCHED>
 __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_constant__ TcArgs a) {
     constexpr int EB = (PREC == FE_PREC_E4M3) ? 1 : ((PREC == FE_PREC_TF32 || PREC == FE_PREC_TF32X3) ? 4 : 2);
@@ -138,10 +205,13 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
     const int64_t n_tiles = a.n_tiles;
     const int NPm = a.np_max;
 
+    const int RA = a.ring_a, RB = a.ring_b;
     if (tid == 0) {
-        for (int s = 0; s < RING; ++s) {
+        for (int s = 0; s < RA; ++s) {
             mbar_init(&sm.a_full[s], TC_M / 32);         // one arrival per builder warp
             mbar_init(&sm.a_empty[s], 1);
+        }
+        for (int s = 0; s < RB; ++s) {
             mbar_init(&sm.b_full[s], 1);
             mbar_init(&sm.b_empty[s], 1);
         }
@@ -171,48 +241,32 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
     if (warp < 4) {
         // ======================= builders =======================
         // The factor kernel has left, per cell, the FP32 coefficient window
-        // w_q kappa_cq and the scaled geometry factors.  For the 16- and 32-bit
-        // formats the operand C is built with one thread per cell: the thread
-        // keeps its cell's window (one 128-byte chunk's worth of points) in
-        // registers and writes its own 128-byte K-major row as eight swizzled
-        // 16-byte stores.  For e4m3 (128 points per chunk) the window is held
-        // one lane per 4 points over the warp's 32 cells, with coalesced loads
-        // and one 32-bit word per lane and row.
-        constexpr bool CELL_ROWS = (PREC != FE_PREC_E4M3);
-        constexpr int QL = KCE / 32;            // e4m3: points per lane
+        // w_q kappa_cq and the scaled geometry factors.  The operand C is built
+        // with one thread per cell: the thread keeps its cell's current window
+        // (KW consecutive points of one slot) in registers and writes its own
+        // 128-byte K-major row of each chunk as eight swizzled 16-byte stores:
+        // one K block of KW points per chunk for the 16- and 32-bit formats, two
+        // 64-point blocks for e4m3 (128 points per chunk).
+        constexpr int KW = tc_window_points(PREC);   // points per window (K block)
+        constexpr int WPC = KCE / KW;                // K blocks per chunk
+        constexpr int GE = 16 / EB;                  // elements per 16-byte granule
+        constexpr int GPB = KW / GE;                 // granules per K block
+        static_assert(WPC * GPB == 8, "a chunk row is eight granules");
         const int cl = tid;
-        const int wrow0 = warp * 32;
         int ac = 0, jb = 0;
-        float win[CELL_ROWS ? KCE : 1];
-        // win[i] = the window row wrow's entry q = qw * KCE + i (wrow = this
+        float win[KW];
+        // win[i] = the window row wrow's entry q = qw * KW + i (wrow = this
         // thread's cell, times the slots per cell, plus the slot)
         auto load_own = [&](const float *__restrict__ W, int ldw, int64_t wrow, bool valid, int qw) {
-            const float *row = W + wrow * ldw + qw * KCE;
+            const float *row = W + wrow * ldw + qw * KW;
 #pragma unroll
-            for (int i = 0; i < KCE; i += 4) {
-                const float4 v = (valid && qw * KCE + i < ldw) ? __ldg(reinterpret_cast<const float4 *>(row + i))
-                                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = 0; i < KW; i += 4) {
+                const float4 v = (valid && qw * KW + i < ldw) ? __ldg(reinterpret_cast<const float4 *>(row + i))
+                                                             : make_float4(0.f, 0.f, 0.f, 0.f);
                 win[i] = v.x;
                 win[i + 1] = v.y;
                 win[i + 2] = v.z;
                 win[i + 3] = v.w;
-            }
-        };
-        // dst[r * QL + i] = entry q = qw * KCE + lane * QL + i of slot `slot` of
-        // cell r's window (e4m3)
-        auto load_rows = [&](const float *__restrict__ W, int ldw, int slots, int slot, int64_t n_cells,
-                             int64_t tile_cell0, int qw, float *dst) {
-            const int q = qw * KCE + lane * QL;
-#pragma unroll
-            for (int r = 0; r < 32; ++r) {
-                const int64_t cell_r = tile_cell0 + wrow0 + r;
-                const float4 v = (cell_r < n_cells && q < ldw)
-                                     ? __ldg(reinterpret_cast<const float4 *>(W + (cell_r * slots + slot) * ldw + q))
-                                     : make_float4(0.f, 0.f, 0.f, 0.f);
-                dst[r * QL] = v.x;
-                dst[r * QL + 1] = v.y;
-                dst[r * QL + 2] = v.z;
-                dst[r * QL + 3] = v.w;
             }
         };
         // the window and factor blocks of a tile are contiguous: pull the next
@@ -225,10 +279,15 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             prefetch_l2(S.win + c0 * S.ldw * S.win_slots, (uint32_t)(nc * S.ldw * S.win_slots * sizeof(float)));
             prefetch_l2(S.cellf + c0 * CELLF, (uint32_t)(nc * CELLF * sizeof(float)));
         };
-        prefetch_tile(blockIdx.x);
-        for (int64_t t = blockIdx.x; t < n_tiles && !*abort_flag; t += gridDim.x) {
-            prefetch_tile(t + gridDim.x);
-            const TcSeg &S = seg_of<BATCHED>(a, t);
+        Jobs<BATCHED> J;
+        J.start(a, blockIdx.x, gridDim.x);
+        if (J.live()) prefetch_tile(J.t);
+        int64_t cur_t = -1;
+        float unscale_f[MAX_FORMS] = {1.f, 1.f};
+        int qw_loaded = -1;
+        for (; J.live() && !*abort_flag; J.advance()) {
+            const int64_t t = J.t;
+            const TcSeg &S = *J.S;
             const float *__restrict__ s_win = S.win;
             const int s_ldw = S.ldw;
             const int64_t s_ncells = S.n_cells;
@@ -236,215 +295,208 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             const int64_t tile_cell0 = (t - S.tile_begin) * TC_M;
             const int64_t cell = tile_cell0 + cl;
             const bool valid = cell < s_ncells;
-            // this cell's factors: scaled geometry to the shared row table, unscales
-            float unscale_f[MAX_FORMS] = {1.f, 1.f};
-            {
-                float rec[12];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const float4 v = valid ? __ldg(reinterpret_cast<const float4 *>(S.cellf + cell * CELLF) + i)
-                                           : make_float4(0.f, 0.f, 0.f, 0.f);
-                    rec[4 * i] = v.x;
-                    rec[4 * i + 1] = v.y;
-                    rec[4 * i + 2] = v.z;
-                    rec[4 * i + 3] = v.w;
-                }
-#pragma unroll
-                for (int j = 0; j < 7; ++j) sm.rowc[cl * 8 + j] = rec[CELLF_G + j];
-                if (valid) {
-                    unscale_f[0] = rec[CELLF_UNSCALE];
-                    unscale_f[1] = rec[CELLF_UNSCALE + 1];
-                }
-            }
-            // a tile whose points fit one window (shared by every pair) loads it
-            // once, here; loaded = qw * 16 + slot of the registers' window
             const int s_slots = S.win_slots;
-            int qw_loaded = -1;
-            if (CELL_ROWS && s_nq <= KCE && s_slots == 1) {
-                load_own(s_win, s_ldw, cell, valid, 0);
-                qw_loaded = 0;
-            }
-            __syncwarp();
-            for (int f = 0; f < MAX_FORMS; ++f) {
-                if (!(S.form_mask & (1 << f))) continue;
-                const TcOperand op = S.op[f];
-                const int per_qw = op.n_pairs * op.n_blk;
-                for (int n = 0; n < op.n_pass; ++n) {
-                    const int b = jb & 1, ub = jb >> 1;
-                    if (jb >= 2 && !mbar_wait_warp(&sm.meta_empty[b], (ub - 1) & 1, deadline)) {
-                        sm.flags[0] = 1;
-                        break;
+            if (t != cur_t) {
+                // a new tile: this cell's factors (scaled geometry to the shared row
+                // table, unscales) and, where its points fit one window, the window
+                cur_t = t;
+                prefetch_tile(t + 1);
+                unscale_f[0] = unscale_f[1] = 1.f;
+                {
+                    float rec[12];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const float4 v = valid ? __ldg(reinterpret_cast<const float4 *>(S.cellf + cell * CELLF) + i)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                        rec[4 * i] = v.x;
+                        rec[4 * i + 1] = v.y;
+                        rec[4 * i + 2] = v.z;
+                        rec[4 * i + 3] = v.w;
                     }
-                    sm.meta[b * TC_M + cl] = unscale_f[f];
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sm.meta_full[b]);
-                    for (int ch = 0; ch < op.n_kchunks; ++ch) {
-                        const int s = ac % RING, ua = ac / RING;
-                        if (ac >= RING && !mbar_wait_warp(&sm.a_empty[s], (ua - 1) & 1, deadline)) {
-                            sm.flags[0] = 1;
-                            break;
-                        }
-                        const int qw = ch / per_qw;
-                        const int j = (ch / op.n_blk) % op.n_pairs;
-                        const int blk = ch % op.n_blk;
-                        const int cidx = (f == 0) ? j : 6;
-                        // window slot: simplices share one; boxed cells have one per pair and one for the mass form
-                        const int slot = (s_slots == 1) ? 0 : ((f == 0) ? j : s_slots - 1);
-                        uint8_t *stA = sm.A + s * (TC_M * TC_CHUNK_BYTES);
-                        if constexpr (CELL_ROWS) {
-                            if (qw * 16 + slot != qw_loaded) {
-                                qw_loaded = qw * 16 + slot;
-                                load_own(s_win, s_ldw, cell * s_slots + slot, valid, qw);
-                            }
-                            const float gj = sm.rowc[cl * 8 + cidx];
-                            uint8_t *rowp = stA + (cl >> 3) * 1024 + (cl & 7) * 128;
-                            constexpr int GE = 16 / EB;   // elements per 16-byte granule
 #pragma unroll
-                            for (int k = 0; k < 8; ++k) {
-                                const float *w = win + k * GE;
-                                uint4 v;
-                                if constexpr (PREC == FE_PREC_BF16) {
-                                    v.x = pack_bf16x2(w[0] * gj, w[1] * gj);
-                                    v.y = pack_bf16x2(w[2] * gj, w[3] * gj);
-                                    v.z = pack_bf16x2(w[4] * gj, w[5] * gj);
-                                    v.w = pack_bf16x2(w[6] * gj, w[7] * gj);
-                                } else if constexpr (PREC == FE_PREC_FP16) {
-                                    v.x = pack_f16x2(w[0] * gj, w[1] * gj);
-                                    v.y = pack_f16x2(w[2] * gj, w[3] * gj);
-                                    v.z = pack_f16x2(w[4] * gj, w[5] * gj);
-                                    v.w = pack_f16x2(w[6] * gj, w[7] * gj);
-                                } else {
-                                    uint32_t u[4];
-#pragma unroll
-                                    for (int e = 0; e < 4; ++e) {
-                                        const float x = w[e] * gj;
-                                        u[e] = round_tf32(x);
-                                        if (PREC == FE_PREC_TF32X3 && blk == 2) u[e] = round_tf32(x - __uint_as_float(u[e]));
-                                    }
-                                    v = make_uint4(u[0], u[1], u[2], u[3]);
-                                }
-                                *reinterpret_cast<uint4 *>(rowp + ((k ^ (cl & 7)) << 4)) = v;
-                            }
-                        } else {
-                            float w[32 * QL];
-                            load_rows(s_win, s_ldw, s_slots, slot, s_ncells, tile_cell0, qw, w);
-                            const int byte = lane * 4;   // this lane's word inside a 128-byte row
-#pragma unroll
-                            for (int r = 0; r < 32; ++r) {
-                                const int R = wrow0 + r;
-                                const float gj = sm.rowc[R * 8 + cidx];
-                                const uint32_t word = pack_e4m3x2(w[r * QL] * gj, w[r * QL + 1] * gj) |
-                                                      (pack_e4m3x2(w[r * QL + 2] * gj, w[r * QL + 3] * gj) << 16);
-                                *reinterpret_cast<uint32_t *>(stA + (R >> 3) * 1024 + (R & 7) * 128 +
-                                                              ((((byte >> 4) ^ (R & 7)) & 7) << 4) + (byte & 15)) = word;
-                            }
-                        }
-                        fence_proxy_async();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&sm.a_full[s]);
-                        ++ac;
+                    for (int j = 0; j < 7; ++j) sm.rowc[cl * 8 + j] = rec[CELLF_G + j];
+                    if (valid) {
+                        unscale_f[0] = rec[CELLF_UNSCALE];
+                        unscale_f[1] = rec[CELLF_UNSCALE + 1];
                     }
-                    ++jb;
-                    if (*abort_flag) break;
                 }
-                if (*abort_flag) break;
-            }
-        }
-    } else if (warp == W_MMA) {
-        // ======================= bulk copies + MMA =======================
-        // B cursor: (tile, form, pass, chunk) of the next shared-operand copy;
-        // bc counts the copies issued (the same in every lane).
-        int64_t bt = blockIdx.x, bc = 0;
-        int bf = 0, bn = 0, bch = 0;
-        if (bt < n_tiles) bf = first_form(seg_of<BATCHED>(a, bt));
-        auto issue_b = [&](int64_t upto) -> bool {
-            while (bc < upto && bt < n_tiles) {
-                const TcSeg &S = seg_of<BATCHED>(a, bt);
-                const TcOperand &op = S.op[bf];
-                const uint32_t bytes = (uint32_t)op.NP * TC_CHUNK_BYTES;
-                const int s = (int)(bc % RING);
-                const int64_t ub = bc / RING;
-                if (bc >= RING && !mbar_wait_warp(&sm.b_empty[s], (uint32_t)((ub - 1) & 1), deadline)) return false;
-                if (lane == 0) {
-                    mbar_arrive_expect_tx(&sm.b_full[s], bytes);
-                    bulk_g2s(sm.B + (size_t)s * NPm * TC_CHUNK_BYTES, op.img + ((size_t)bn * op.n_kchunks + bch) * bytes,
-                             bytes, &sm.b_full[s]);
+                // a tile whose points fit one window (shared by every pair) loads it
+                // once, here; loaded = qw * 16 + slot of the registers' window
+                qw_loaded = -1;
+                if (s_nq <= KW && s_slots == 1) {
+                    load_own(s_win, s_ldw, cell, valid, 0);
+                    qw_loaded = 0;
                 }
                 __syncwarp();
-                ++bc;
-                if (++bch == op.n_kchunks) {
-                    bch = 0;
-                    if (++bn == op.n_pass) {
-                        bn = 0;
-                        int nf = bf + 1;
-                        while (nf < MAX_FORMS && !(S.form_mask & (1 << nf))) ++nf;
-                        if (nf < MAX_FORMS) {
-                            bf = nf;
+            }
+            const int f = J.f;
+            const TcOperand op = S.op[f];
+            const int per_qw = op.n_pairs * op.n_blk;
+            const int n_blocks = op.n_qw * per_qw;
+            const int b = jb & 1, ub = jb >> 1;
+            if (jb >= 2 && !mbar_wait_warp(&sm.meta_empty[b], (ub - 1) & 1, deadline)) {
+                sm.flags[0] = 1;
+                break;
+            }
+            sm.meta[b * TC_M + cl] = unscale_f[f];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.meta_full[b]);
+            for (int ch = 0; ch < op.n_kchunks; ++ch) {
+                const int s = ac % RA, ua = ac / RA;
+                if (ac >= RA && !mbar_wait_warp(&sm.a_empty[s], (ua - 1) & 1, deadline)) {
+                    sm.flags[0] = 1;
+                    break;
+                }
+                uint8_t *stA = sm.A + s * (TC_M * TC_CHUNK_BYTES);
+                uint8_t *rowp = stA + (cl >> 3) * 1024 + (cl & 7) * 128;
+#pragma unroll
+                for (int sub = 0; sub < WPC; ++sub) {
+                    const int h = ch * WPC + sub;      // K block: window qw, pair j, split block blk
+                    const int qw = h / per_qw;
+                    const int j = (h / op.n_blk) % op.n_pairs;
+                    const int blk = h % op.n_blk;
+                    const bool live = h < n_blocks;    // (e4m3: the last chunk may end with a zero block)
+                    const int cidx = (f == 0) ? j : 6;
+                    // window slot: simplices share one; boxed cells have one per pair and one for the mass form
+                    const int slot = (s_slots == 1) ? 0 : ((f == 0) ? j : s_slots - 1);
+                    if (live && qw * 16 + slot != qw_loaded) {
+                        qw_loaded = qw * 16 + slot;
+                        load_own(s_win, s_ldw, cell * s_slots + slot, valid, qw);
+                    }
+                    const float gj = sm.rowc[cl * 8 + cidx];
+#pragma unroll
+                    for (int kk = 0; kk < GPB; ++kk) {
+                        const int k = sub * GPB + kk;   // granule of the 128-byte row
+                        const float *w = win + kk * GE;
+                        uint4 v;
+                        if constexpr (PREC == FE_PREC_BF16) {
+                            v.x = pack_bf16x2(w[0] * gj, w[1] * gj);
+                            v.y = pack_bf16x2(w[2] * gj, w[3] * gj);
+                            v.z = pack_bf16x2(w[4] * gj, w[5] * gj);
+                            v.w = pack_bf16x2(w[6] * gj, w[7] * gj);
+                        } else if constexpr (PREC == FE_PREC_FP16) {
+                            v.x = pack_f16x2(w[0] * gj, w[1] * gj);
+                            v.y = pack_f16x2(w[2] * gj, w[3] * gj);
+                            v.z = pack_f16x2(w[4] * gj, w[5] * gj);
+                            v.w = pack_f16x2(w[6] * gj, w[7] * gj);
+                        } else if constexpr (PREC == FE_PREC_E4M3) {
+                            uint32_t u[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                u[e] = pack_e4m3x2(w[4 * e] * gj, w[4 * e + 1] * gj) |
+                                       (pack_e4m3x2(w[4 * e + 2] * gj, w[4 * e + 3] * gj) << 16);
+                            v = make_uint4(u[0], u[1], u[2], u[3]);
                         } else {
-                            bt += gridDim.x;
-                            if (bt < n_tiles) bf = first_form(seg_of<BATCHED>(a, bt));
+                            uint32_t u[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float x = w[e] * gj;
+                                u[e] = round_tf32(x);
+                                if (PREC == FE_PREC_TF32X3 && blk == 2) u[e] = round_tf32(x - __uint_as_float(u[e]));
+                            }
+                            v = make_uint4(u[0], u[1], u[2], u[3]);
                         }
+                        if (!live) v = make_uint4(0u, 0u, 0u, 0u);
+                        *reinterpret_cast<uint4 *>(rowp + ((k ^ (cl & 7)) << 4)) = v;
                     }
                 }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.a_full[s]);
+                ++ac;
             }
-            return true;
-        };
+            ++jb;
+        }
+    } else if (warp == W_MMA) {
+        // ======================= MMA =======================
+        // Consumes chunk mc from the two rings (stage mc % RA of the built
+        // operand, mc % RB of the shared one) and queues its MMAs at once: the
+        // completions free the stages asynchronously, so the tensor pipe always
+        // holds the next chunk's MMAs while the producers refill.
         int64_t mc = 0;
         int jb = 0;
-        bool fail = !issue_b(RING);
-        for (int64_t t = blockIdx.x; t < n_tiles && !fail; t += gridDim.x) {
-            const TcSeg &S = seg_of<BATCHED>(a, t);
-            for (int f = 0; f < MAX_FORMS && !fail; ++f) {
-                if (!(S.form_mask & (1 << f))) continue;
-                const TcOperand op = S.op[f];
-                const uint32_t idesc = a.idesc | ((uint32_t)(op.NP >> 3) << 17);
-                for (int n = 0; n < op.n_pass && !fail; ++n) {
-                    const int b = jb & 1, ub = jb >> 1;
-                    if (jb >= 2 && !mbar_wait_warp(&sm.acc_empty[b], (ub - 1) & 1, deadline)) {
-                        fail = true;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t dacc = tmem + (uint32_t)(b * ACC_COLS);
-                    for (int ch = 0; ch < op.n_kchunks; ++ch) {
-                        const int sa = (int)(mc % RING);
-                        const uint32_t par = (uint32_t)((mc / RING) & 1);
-                        if (!mbar_wait_warp(&sm.a_full[sa], par, deadline) || !mbar_wait_warp(&sm.b_full[sa], par, deadline)) {
-                            fail = true;
-                            break;
-                        }
-                        tc_fence_after();
-                        if (lane == 0) {
-                            const uint32_t a0 = smem_u32(sm.A + sa * (TC_M * TC_CHUNK_BYTES));
-                            const uint32_t b0 = smem_u32(sm.B + (size_t)sa * NPm * TC_CHUNK_BYTES);
-#pragma unroll
-                            for (int ks = 0; ks < TC_CHUNK_BYTES / 32; ++ks)
-                                umma<KIND>(dacc, sdesc_sw128(a0 + 32 * ks), sdesc_sw128(b0 + 32 * ks), idesc,
-                                           (ch | ks) != 0 ? 1u : 0u);
-                            umma_commit(&sm.a_empty[sa]);
-                            umma_commit(&sm.b_empty[sa]);
-                            if (ch == op.n_kchunks - 1) umma_commit(&sm.acc_full[b]);
-                        }
-                        __syncwarp();
-                        ++mc;
-                        // refill the stage of chunk mc-1 once its MMAs are done
-                        if (!issue_b(mc + RING)) {
-                            fail = true;
-                            break;
-                        }
-                    }
-                    ++jb;
-                    if (*abort_flag) fail = true;
+        bool fail = false;
+        Jobs<BATCHED> J;
+        J.start(a, blockIdx.x, gridDim.x);
+        for (; J.live() && !fail; J.advance()) {
+            const TcOperand op = J.S->op[J.f];
+            const uint32_t idesc = a.idesc | ((uint32_t)(op.NP >> 3) << 17);
+            const int b = jb & 1, ub = jb >> 1;
+            if (jb >= 2 && !mbar_wait_warp(&sm.acc_empty[b], (ub - 1) & 1, deadline)) {
+                fail = true;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t dacc = tmem + (uint32_t)(b * ACC_COLS);
+            for (int ch = 0; ch < op.n_kchunks; ++ch) {
+                const int sa = (int)(mc % RA), sb = (int)(mc % RB);
+                if (!mbar_wait_warp(&sm.a_full[sa], (uint32_t)((mc / RA) & 1), deadline) ||
+                    !mbar_wait_warp(&sm.b_full[sb], (uint32_t)((mc / RB) & 1), deadline)) {
+                    fail = true;
+                    break;
                 }
+                tc_fence_after();
+                if (lane == 0) {
+                    const uint32_t a0 = smem_u32(sm.A + sa * (TC_M * TC_CHUNK_BYTES));
+                    const uint32_t b0 = smem_u32(sm.B + (size_t)sb * NPm * TC_CHUNK_BYTES);
+#pragma unroll
+                    for (int ks = 0; ks < TC_CHUNK_BYTES / 32; ++ks)
+                        umma<KIND>(dacc, sdesc_sw128(a0 + 32 * ks), sdesc_sw128(b0 + 32 * ks), idesc,
+                                   (ch | ks) != 0 ? 1u : 0u);
+                    umma_commit(&sm.a_empty[sa]);
+                    umma_commit(&sm.b_empty[sb]);
+                    if (ch == op.n_kchunks - 1) umma_commit(&sm.acc_full[b]);
+                }
+                __syncwarp();
+                ++mc;
+            }
+            ++jb;
+            if (*abort_flag) fail = true;
+        }
+        if (fail) sm.flags[0] = 1;
+        // drain: every issued MMA finished (a CTA that issued none has nothing
+        // to wait for)
+        if (mc > 0) {
+            if (lane == 0) umma_commit(sm.drain);
+            __syncwarp();
+            mbar_wait(sm.drain, 0, 200000000ull);   // 0.2 s
+        }
+    } else if (warp == W_PROD) {
+        // ======================= shared-operand producer =======================
+        // One 1-D bulk copy per chunk (NP rows of 128 bytes, pre-swizzled) into
+        // stage bc % RB, once the MMAs of the chunk that last used the stage are
+        // done: up to RB copies in flight hide the L2 latency.
+        Jobs<BATCHED> BJ;
+        BJ.start(a, blockIdx.x, gridDim.x);
+        int64_t bc = 0;
+        int bch = 0;
+        bool fail = false;
+        while (BJ.live() && !*abort_flag) {
+            const TcOperand &op = BJ.S->op[BJ.f];
+            const uint32_t bytes = (uint32_t)op.NP * TC_CHUNK_BYTES;
+            const int s = (int)(bc % RB);
+            if (bc >= RB && !mbar_wait_warp(&sm.b_empty[s], (uint32_t)(((bc / RB) - 1) & 1), deadline)) {
+                fail = true;
+                break;
+            }
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&sm.b_full[s], bytes);
+                bulk_g2s(sm.B + (size_t)s * NPm * TC_CHUNK_BYTES, op.img + ((size_t)BJ.n * op.n_kchunks + bch) * bytes,
+                         bytes, &sm.b_full[s]);
+            }
+            __syncwarp();
+            ++bc;
+            if (++bch == op.n_kchunks) {
+                bch = 0;
+                BJ.advance();
             }
         }
         if (fail) sm.flags[0] = 1;
-        // drain: every issued MMA finished, every issued bulk copy landed
-        if (lane == 0) umma_commit(sm.drain);
-        __syncwarp();
-        const unsigned long long drain_deadline = 200000000ull;   // 0.2 s per wait
-        mbar_wait(sm.drain, 0, drain_deadline);
-        for (int64_t c = mc; c < bc; ++c) mbar_wait(&sm.b_full[c % RING], (uint32_t)((c / RING) & 1), drain_deadline);
+        // every issued copy has landed before the CTA leaves (the last copy of
+        // each stage is the one its current phase waits for)
+        const int64_t first = bc > RB ? bc - RB : 0;
+        for (int64_t c = first; c < bc; ++c)
+            mbar_wait(&sm.b_full[c % RB], (uint32_t)((c / RB) & 1), 200000000ull);
     } else if (warp >= W_EPI0 && warp < W_EPI0 + N_EPI) {
         // ======================= epilogue =======================
         // warps 4-7 and 8-11: lane group g = warp % 4 (TMEM lanes 32g..32g+31),
@@ -461,8 +513,11 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         // Every decision to stop is taken per pass, after the pass's waits, and
         // (for staged segments) jointly by the two warps of the lane group.
         bool stop = false;
-        for (int64_t t = blockIdx.x; t < n_tiles && !stop; t += gridDim.x) {
-            const TcSeg &S = seg_of<BATCHED>(a, t);
+        Jobs<BATCHED> J;
+        J.start(a, blockIdx.x, gridDim.x);
+        for (; J.live() && !stop; J.advance()) {
+            const int64_t t = J.t;
+            const TcSeg &S = *J.S;
             const int nph = S.n_phi, nph2 = nph * nph;
             const int n_it = (nph2 + 31) / 32;
             // 16-byte stores when every matrix starts on a 16-byte boundary
@@ -477,147 +532,142 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 }
                 cur = &S;
             }
-            for (int f = 0; f < MAX_FORMS; ++f) {
-                if (!(S.form_mask & (1 << f))) continue;
-                const TcOperand op = S.op[f];
-                float *__restrict__ out = S.out[f];
-                const int64_t s_ncells = S.n_cells;
-                const int s_staged = S.staged;
-                const int32_t *__restrict__ s_symkl = S.sym_kl;
-                for (int n = 0; n < op.n_pass; ++n) {
-                    const int b = jb & 1, ub = jb >> 1;
-                    bool ok = !*abort_flag && mbar_wait_warp(&sm.acc_full[b], ub & 1, deadline) &&
-                              mbar_wait_warp(&sm.meta_full[b], ub & 1, deadline);
-                    if (s_staged) {
-                        // the two warps of this lane group meet at named barriers below:
-                        // they take one common outcome here, so that a wait that gave up
-                        // in one of them cannot leave the other alone at a barrier
-                        if (lane == 0) pair_ok[g * 2 + h] = ok ? 1 : 0;
-                        named_bar_sync(1 + g, 64);
-                        ok = pair_ok[g * 2] && pair_ok[g * 2 + 1];
-                    }
-                    if (!ok) {
-                        sm.flags[0] = 1;
-                        stop = true;
-                        break;
-                    }
-                    tc_fence_after();
-                    const float us = sm.meta[b * TC_M + g * 32 + lane];
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sm.meta_empty[b]);
-                    const uint32_t tbase = tmem + (uint32_t)(b * ACC_COLS) + ((uint32_t)(g * 32) << 16);
-                    const int64_t cell0 = (t - S.tile_begin) * TC_M + g * 32;
-                    if (s_staged) {
-                        float *mine = stg + lane * pitch;
-                        for (int c0 = 32 * h; c0 < op.NP; c0 += 64) {
-                            uint32_t r[32];
-                            tmem_ld32(tbase + (uint32_t)c0, r);
-#pragma unroll
-                            for (int i = 0; i < 32; ++i)
-                                if (c0 + i < op.NP) mine[c0 + i] = __uint_as_float(r[i]) * us;
-                        }
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&sm.acc_empty[b]);
-                        named_bar_sync(1 + g, 64);
-                        // whole row-major matrices of 16 consecutive cells (loads first, then stores)
-                        if (out && op.rows_per_pass > 0) {
-                            // full-row pass: rows [k0, k0 + R) of each cell are one contiguous run
-                            const int k0 = n * op.rows_per_pass;
-                            const int len = (nph - k0 < op.rows_per_pass ? nph - k0 : op.rows_per_pass) * nph;
-                            for (int cc = 16 * h; cc < 16 * h + 16; ++cc) {
-                                if (cell0 + cc >= s_ncells) break;
-                                float *__restrict__ dst = out + (cell0 + cc) * (int64_t)nph2 + (int64_t)k0 * nph;
-                                const float *__restrict__ src = stg + cc * pitch;
-                                for (int i0 = 0; i0 < len; i0 += 128) {
-                                    float x[4];
-#pragma unroll
-                                    for (int u = 0; u < 4; ++u) {
-                                        const int i = i0 + u * 32 + lane;
-                                        x[u] = i < len ? src[i] : 0.f;
-                                    }
-#pragma unroll
-                                    for (int u = 0; u < 4; ++u) {
-                                        const int i = i0 + u * 32 + lane;
-                                        if (i < len) __stcs(dst + i, x[u]);
-                                    }
-                                }
-                            }
-                        } else if (out && v4) {
-                            // two cells per step, 16-byte coalesced stores
-                            for (int cc = 16 * h; cc < 16 * h + 16; cc += 2) {
-                                float4 vals[2][MAX_F2S_IT / 4];
-#pragma unroll
-                                for (int u = 0; u < 2; ++u) {
-                                    const float *__restrict__ src = stg + (cc + u) * pitch;
-#pragma unroll
-                                    for (int it = 0; it < MAX_F2S_IT / 4; ++it)
-                                        vals[u][it] = make_float4(src[f2s_reg[4 * it]], src[f2s_reg[4 * it + 1]],
-                                                                  src[f2s_reg[4 * it + 2]], src[f2s_reg[4 * it + 3]]);
-                                }
-#pragma unroll
-                                for (int u = 0; u < 2; ++u) {
-                                    if (cell0 + cc + u >= s_ncells) break;
-                                    float *__restrict__ dst = out + (cell0 + cc + u) * (int64_t)nph2;
-#pragma unroll
-                                    for (int it = 0; it < MAX_F2S_IT / 4; ++it) {
-                                        const int pos = 128 * it + 4 * lane;
-                                        if (pos < nph2) __stcs(reinterpret_cast<float4 *>(dst + pos), vals[u][it]);
-                                    }
-                                }
-                            }
-                        } else if (out) {
-                            for (int cc = 16 * h; cc < 16 * h + 16; ++cc) {
-                                if (cell0 + cc >= s_ncells) break;
-                                float *__restrict__ dst = out + (cell0 + cc) * (int64_t)nph2;
-                                const float *__restrict__ src = stg + cc * pitch;
-                                float vals[MAX_F2S_IT];
-#pragma unroll
-                                for (int it = 0; it < MAX_F2S_IT; ++it) vals[it] = (it < n_it) ? src[f2s_reg[it]] : 0.f;
-#pragma unroll
-                                for (int it = 0; it < MAX_F2S_IT; ++it) {
-                                    const int pos = lane + 32 * it;
-                                    if (it < n_it && pos < nph2) __stcs(dst + pos, vals[it]);
-                                }
-                            }
-                        }
-                        named_bar_sync(1 + g, 64);
-                    } else {
-                        const int64_t mycell = cell0 + lane;
-                        for (int c0 = 32 * h; c0 < op.NP; c0 += 64) {
-                            uint32_t r[32];
-                            tmem_ld32(tbase + (uint32_t)c0, r);
-                            if (mycell < s_ncells && out) {
-                                float *dst = out + mycell * (int64_t)nph2;
-#pragma unroll
-                                for (int i = 0; i < 32; ++i) {
-                                    const int col = n * op.NP + c0 + i;
-                                    if (op.rows_per_pass > 0) {
-                                        // full-row layout: column c of pass n is entry (nR + c / n_phi, c % n_phi)
-                                        const int cc = c0 + i;
-                                        const int k = n * op.rows_per_pass + cc / nph;
-                                        if (cc < op.NP && cc < op.rows_per_pass * nph && k < nph)
-                                            __stcs(dst + k * nph + cc % nph, __uint_as_float(r[i]) * us);
-                                        continue;
-                                    }
-                                    const int32_t kl = (c0 + i < op.NP && col < op.n_cols) ? __ldg(s_symkl + col) : -1;
-                                    if (kl >= 0) {   // (padding columns carry no pair)
-                                        const int k = kl & 0xFFFF, l = kl >> 16;
-                                        const float v = __uint_as_float(r[i]) * us;
-                                        __stcs(dst + k * nph + l, v);
-                                        __stcs(dst + l * nph + k, v);
-                                    }
-                                }
-                            }
-                        }
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&sm.acc_empty[b]);
-                    }
-                    ++jb;
-                }
-                if (stop) break;
+            const int f = J.f, n = J.n;
+            const TcOperand op = S.op[f];
+            float *__restrict__ out = S.out[f];
+            const int64_t s_ncells = S.n_cells;
+            const int s_staged = S.staged;
+            const int32_t *__restrict__ s_symkl = S.sym_kl;
+            const int b = jb & 1, ub = jb >> 1;
+            bool ok = !*abort_flag && mbar_wait_warp(&sm.acc_full[b], ub & 1, deadline) &&
+                      mbar_wait_warp(&sm.meta_full[b], ub & 1, deadline);
+            if (s_staged) {
+                // the two warps of this lane group meet at named barriers below:
+                // they take one common outcome here, so that a wait that gave up
+                // in one of them cannot leave the other alone at a barrier
+                if (lane == 0) pair_ok[g * 2 + h] = ok ? 1 : 0;
+                named_bar_sync(1 + g, 64);
+                ok = pair_ok[g * 2] && pair_ok[g * 2 + 1];
             }
+            if (!ok) {
+                sm.flags[0] = 1;
+                stop = true;
+                break;
+            }
+            tc_fence_after();
+            const float us = sm.meta[b * TC_M + g * 32 + lane];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.meta_empty[b]);
+            const uint32_t tbase = tmem + (uint32_t)(b * ACC_COLS) + ((uint32_t)(g * 32) << 16);
+            const int64_t cell0 = (t - S.tile_begin) * TC_M + g * 32;
+            if (s_staged) {
+                float *mine = stg + lane * pitch;
+                for (int c0 = 32 * h; c0 < op.NP; c0 += 64) {
+                    uint32_t r[32];
+                    tmem_ld32(tbase + (uint32_t)c0, r);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (c0 + i < op.NP) mine[c0 + i] = __uint_as_float(r[i]) * us;
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.acc_empty[b]);
+                named_bar_sync(1 + g, 64);
+                // whole row-major matrices of 16 consecutive cells (loads first, then stores)
+                if (out && op.rows_per_pass > 0) {
+                    // full-row pass: rows [k0, k0 + R) of each cell are one contiguous run
+                    const int k0 = n * op.rows_per_pass;
+                    const int len = (nph - k0 < op.rows_per_pass ? nph - k0 : op.rows_per_pass) * nph;
+                    for (int cc = 16 * h; cc < 16 * h + 16; ++cc) {
+                        if (cell0 + cc >= s_ncells) break;
+                        float *__restrict__ dst = out + (cell0 + cc) * (int64_t)nph2 + (int64_t)k0 * nph;
+                        const float *__restrict__ src = stg + cc * pitch;
+                        for (int i0 = 0; i0 < len; i0 += 128) {
+                            float x[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int i = i0 + u * 32 + lane;
+                                x[u] = i < len ? src[i] : 0.f;
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int i = i0 + u * 32 + lane;
+                                if (i < len) __stcs(dst + i, x[u]);
+                            }
+                        }
+                    }
+                } else if (out && v4) {
+                    // two cells per step, 16-byte coalesced stores
+                    for (int cc = 16 * h; cc < 16 * h + 16; cc += 2) {
+                        float4 vals[2][MAX_F2S_IT / 4];
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            const float *__restrict__ src = stg + (cc + u) * pitch;
+#pragma unroll
+                            for (int it = 0; it < MAX_F2S_IT / 4; ++it)
+                                vals[u][it] = make_float4(src[f2s_reg[4 * it]], src[f2s_reg[4 * it + 1]],
+                                                          src[f2s_reg[4 * it + 2]], src[f2s_reg[4 * it + 3]]);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            if (cell0 + cc + u >= s_ncells) break;
+                            float *__restrict__ dst = out + (cell0 + cc + u) * (int64_t)nph2;
+#pragma unroll
+                            for (int it = 0; it < MAX_F2S_IT / 4; ++it) {
+                                const int pos = 128 * it + 4 * lane;
+                                if (pos < nph2) __stcs(reinterpret_cast<float4 *>(dst + pos), vals[u][it]);
+                            }
+                        }
+                    }
+                } else if (out) {
+                    for (int cc = 16 * h; cc < 16 * h + 16; ++cc) {
+                        if (cell0 + cc >= s_ncells) break;
+                        float *__restrict__ dst = out + (cell0 + cc) * (int64_t)nph2;
+                        const float *__restrict__ src = stg + cc * pitch;
+                        float vals[MAX_F2S_IT];
+#pragma unroll
+                        for (int it = 0; it < MAX_F2S_IT; ++it) vals[it] = (it < n_it) ? src[f2s_reg[it]] : 0.f;
+#pragma unroll
+                        for (int it = 0; it < MAX_F2S_IT; ++it) {
+                            const int pos = lane + 32 * it;
+                            if (it < n_it && pos < nph2) __stcs(dst + pos, vals[it]);
+                        }
+                    }
+                }
+                named_bar_sync(1 + g, 64);
+            } else {
+                const int64_t mycell = cell0 + lane;
+                for (int c0 = 32 * h; c0 < op.NP; c0 += 64) {
+                    uint32_t r[32];
+                    tmem_ld32(tbase + (uint32_t)c0, r);
+                    if (mycell < s_ncells && out) {
+                        float *dst = out + mycell * (int64_t)nph2;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) {
+                            const int col = n * op.NP + c0 + i;
+                            if (op.rows_per_pass > 0) {
+                                // full-row layout: column c of pass n is entry (nR + c / n_phi, c % n_phi)
+                                const int cc = c0 + i;
+                                const int k = n * op.rows_per_pass + cc / nph;
+                                if (cc < op.NP && cc < op.rows_per_pass * nph && k < nph)
+                                    __stcs(dst + k * nph + cc % nph, __uint_as_float(r[i]) * us);
+                                continue;
+                            }
+                            const int32_t kl = (c0 + i < op.NP && col < op.n_cols) ? __ldg(s_symkl + col) : -1;
+                            if (kl >= 0) {   // (padding columns carry no pair)
+                                const int k = kl & 0xFFFF, l = kl >> 16;
+                                const float v = __uint_as_float(r[i]) * us;
+                                __stcs(dst + k * nph + l, v);
+                                __stcs(dst + l * nph + k, v);
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.acc_empty[b]);
+            }
+            ++jb;
         }
     }
     if (sm.flags[0] && tid == 0) atomicOr(&sm.flags[1], ST_TIMEOUT);
@@ -632,10 +682,10 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
 
 size_t tc_smem_bytes(const TcArgs &a) {
     size_t b = 1024;  // alignment slack
-    b += bytes_A() + bytes_B(a) + bytes_stage(a);
+    b += bytes_A(a) + bytes_B(a) + bytes_stage(a);
     b += 2 * TC_M * sizeof(float) + 8 * TC_M * sizeof(float);
     b += 8;
-    b += (4 * RING + 9) * sizeof(uint64_t) + 8 + 16;
+    b += (2 * TC_MAX_RING_A + 2 * TC_MAX_RING_B + 9) * sizeof(uint64_t) + 8 + 16;
     return b;
 }
 
@@ -654,6 +704,7 @@ bool tc_can_stage(const TcArgs &a, const TcSeg &seg) {
     if (pairs && seg.n_phi * seg.n_phi > 32 * MAX_F2S_IT) return false;
     TcArgs t = a;
     t.pitch_max = (np + 1) > a.pitch_max ? (np + 1) : a.pitch_max;
+    t.ring_a = t.ring_b = 2;   // staging is decided at the shallowest rings; deeper rings take what is left
     return tc_smem_bytes(t) <= 227 * 1024;
 }
 
@@ -680,7 +731,7 @@ int launch_tc_elements(const TcArgs &a, size_t smem, cudaStream_t s, int grid) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         grid = sms;
     }
-    if (grid > a.n_tiles) grid = (int)a.n_tiles;
+    if (grid > a.n_jobs) grid = (int)a.n_jobs;
     switch (a.prec) {
         case FE_PREC_BF16: return launch_prec<FE_PREC_BF16>(a, smem, s, grid);
         case FE_PREC_FP16: return launch_prec<FE_PREC_FP16>(a, smem, s, grid);
