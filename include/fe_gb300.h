@@ -205,6 +205,24 @@ fe_status fe_plan_set_fusion(fe_plan *plan, int mode, int *active);
  * workload, where rows are short).  Both sum every CSR value's entries in
  * increasing cell order from zero: bitwise the same values. */
 fe_status fe_plan_set_assembly(fe_plan *plan, int algo);
+/* Window prefetch of the tensor-core element kernel, where a job reads more
+ * than one coefficient window (more quadrature points than one 128-byte K
+ * chunk holds, or boxed cells, whose geometry gives each pair its own window):
+ * the builder threads copy their next window asynchronously into shared
+ * memory while the current one is used, at the price of a shared-memory slot
+ * per thread that would otherwise hold an operand stage.  mode -1 (default):
+ * as the plan's autotuner measured fastest per precision and form; 0 off;
+ * 1 on wherever it fits.  The element matrices are bitwise the same in every
+ * mode. */
+fe_status fe_plan_set_window_prefetch(fe_plan *plan, int mode);
+/* Launch shape the tensor-core element kernel takes for these forms and this
+ * (reduced) precision on this plan, as fe_element_matrices would launch it
+ * now: stages of the built-operand ring (ring_a) and of the shared-operand
+ * ring (ring_b), whether the builders prefetch windows (win_buf, 0/1), and
+ * whether the epilogue stages through shared memory (staged, 0/1).  Any
+ * output pointer may be NULL.  No device work. */
+fe_status fe_plan_tc_config(fe_plan *plan, unsigned forms, fe_precision prec, int32_t *ring_a, int32_t *ring_b,
+                            int32_t *win_buf, int32_t *staged);
 /* Device memory the plan holds, in bytes: plan_bytes for what plan creation
  * allocated (mesh, tabulations, operand images, dof map, pattern, assembly
  * streams, action tables built so far), workspace_bytes for the workspaces

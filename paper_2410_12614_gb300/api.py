@@ -321,6 +321,19 @@ class Plan:
         one warp per CSR row; the CSR values are bitwise the same."""
         check(load().fe_plan_set_assembly(self._h, int(algo)), "fe_plan_set_assembly")
 
+    def set_window_prefetch(self, mode: int = -1):
+        """fe_plan_set_window_prefetch: -1 as autotuned (default), 0 off, 1 on; the
+        element matrices are bitwise the same."""
+        check(load().fe_plan_set_window_prefetch(self._h, int(mode)), "fe_plan_set_window_prefetch")
+
+    def tc_config(self, forms=("stiffness", "mass"), prec="bf16"):
+        """fe_plan_tc_config: the tensor-core launch shape for these forms and
+        precision, as a dict (ring_a, ring_b, win_buf, staged)."""
+        v = [ctypes.c_int32() for _ in range(4)]
+        check(load().fe_plan_tc_config(self._h, self._forms_mask(forms), PRECISIONS[prec],
+                                       *[ctypes.byref(x) for x in v]), "fe_plan_tc_config")
+        return dict(zip(("ring_a", "ring_b", "win_buf", "staged"), (x.value for x in v)))
+
     def memory(self):
         """(plan_bytes, workspace_bytes) of device memory the plan holds (fe_plan_memory)."""
         pb, wb = ctypes.c_int64(), ctypes.c_int64()

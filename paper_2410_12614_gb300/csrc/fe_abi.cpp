@@ -109,6 +109,7 @@ struct fe_plan {
     std::vector<int64_t> fuse_row_off;
     DevBuf inc_slot;                     // [n_inc][n_phi] column slots (row-wise assembly)
     int asm_algo = 0;                    // fe_plan_set_assembly: 0 chunked segments (default), 1 one warp per row
+    int wpref_mode = -1;                 // fe_plan_set_window_prefetch: -1 tuned, 0 off, 1 on
     int fuse_mode = 0;                   // fe_plan_set_fusion: 1 on where eligible, 0 off (default)
     unsigned form_mask = 0, prec_mask = 0;
     int64_t n_cells = 0, n_vertices = 0, n_dofs = 0, nnz = 0;
@@ -176,6 +177,10 @@ static cudaError_t upload(DevBuf &b, const std::vector<T> &v, cudaStream_t s) {
 static fe_status pack_operand(fe_plan &P, int prec, int fi, int np_pass);
 static fe_status autotune_plan(fe_plan &P);
 static fe_status need_pattern(const fe_plan *plan);
+static fe_status check_call(fe_plan *plan, unsigned forms, fe_precision prec);
+static TcSeg make_tc_seg(fe_plan *P, unsigned forms, int prec, const double *vertices, const double *kappa,
+                         void *const A[2], float *win, float *cellf);
+static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status, unsigned long long wait_limit_ns);
 
 extern "C" {
 
@@ -505,6 +510,32 @@ fe_status fe_plan_set_assembly(fe_plan *plan, int algo) {
     return FE_OK;
 }
 
+fe_status fe_plan_set_window_prefetch(fe_plan *plan, int mode) {
+    if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
+    if (mode < -1 || mode > 1) return fail(FE_ERR_INVALID_ARG, "mode must be -1 (tuned), 0 (off) or 1 (on)");
+    plan->wpref_mode = mode;
+    return FE_OK;
+}
+
+fe_status fe_plan_tc_config(fe_plan *plan, unsigned forms, fe_precision prec, int32_t *ring_a, int32_t *ring_b,
+                            int32_t *win_buf, int32_t *staged) {
+    g_err.clear();
+    fe_status st = check_call(plan, forms, prec);
+    if (st) return st;
+    if (prec == FE_PREC_FP64) return fail(FE_ERR_INVALID_ARG, "the FP64 path does not use the tensor-core kernel");
+    TcArgs a{};
+    void *A[2] = {nullptr, nullptr};
+    a.seg0 = make_tc_seg(plan, forms, prec, nullptr, nullptr, A, nullptr, nullptr);
+    a.segs = nullptr;
+    a.n_segs = 1;
+    tc_finalize(a, &a.seg0, 1, prec, nullptr, plan->wait_limit_ns);
+    if (ring_a) *ring_a = a.ring_a;
+    if (ring_b) *ring_b = a.ring_b;
+    if (win_buf) *win_buf = a.win_buf;
+    if (staged) *staged = a.seg0.staged;
+    return FE_OK;
+}
+
 fe_status fe_plan_set_fusion(fe_plan *plan, int mode, int *active) {
     if (!plan) return fail(FE_ERR_INVALID_ARG, "NULL plan");
     if (mode != 0 && mode != 1) return fail(FE_ERR_INVALID_ARG, "mode must be 1 (on) or 0 (off)");
@@ -653,6 +684,7 @@ static TcSeg make_tc_seg(fe_plan *P, unsigned forms, int prec, const double *ver
         const int fi = form_index(form);
         g.form_mask |= 1 << fi;
         g.op[fi] = P->op[prec][fi];
+        if (P->wpref_mode >= 0) g.op[fi].win_pref = P->wpref_mode;
         g.out[fi] = static_cast<float *>(A[fi]);
     }
     g.sym_kl = P->sym_kl.as<int32_t>();
@@ -668,6 +700,7 @@ static TcSeg make_tc_seg(fe_plan *P, unsigned forms, int prec, const double *ver
 // Global launch shape over the segments: operand maxima, then the staged
 // epilogue for every segment that fits (greedy, in segment order).
 static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status, unsigned long long wait_limit_ns) {
+    a.win_buf = 0;   // (the staging decisions below are taken without it)
     a.prec = prec;
     a.elem_bytes = host::format_of(prec).elem_bytes;
     a.idesc = idesc_for(prec);
@@ -708,6 +741,15 @@ static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status, un
     }
     a.status = status;
     a.timeout_ns = wait_limit_ns;  // per wait, counted from the wait's start
+    // a next-window slot per builder thread where a job reads more than one
+    // window (more points than one window holds, or one window per pair) and
+    // the autotuner measured the prefetch faster for one of the forms
+    for (int i = 0; i < n; ++i)
+        if (segs[i].n_q > tc_window_points(prec) || segs[i].win_slots > 1)
+            for (int f = 0; f < MAX_FORMS; ++f)
+                if (((segs[i].form_mask >> f) & 1) && segs[i].op[f].win_pref) a.win_buf = 1;
+    a.ring_a = a.ring_b = 2;
+    if (a.win_buf && tc_smem_bytes(a) > 227 * 1024) a.win_buf = 0;
     // operand rings beside the staging area: the shared-operand ring first
     // (each stage is one more bulk copy in flight against the L2 latency), up
     // to four stages, then a third built-operand stage (slack for the builders'
@@ -932,7 +974,7 @@ static fe_status pack_operand(fe_plan &P, int prec, int fi, int np_pass) {
 
 namespace {
 std::mutex g_tune_mutex;
-std::map<std::string, int> g_tune_cache;  // "(d,p,n_q,prec,form)" -> N-pass width
+std::map<std::string, std::pair<int, int>> g_tune_cache;  // "(d,p,n_q,prec,form,boxed)" -> (N-pass width, window prefetch)
 }  // namespace
 
 // Autotuner for the tile shape of every (cell type, degree, quadrature size,
@@ -956,16 +998,24 @@ static fe_status autotune_plan(fe_plan &P) {
             const unsigned form = fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS;
             if (!(P.form_mask & form)) continue;
             std::vector<int> cand = host::np_candidates(P.n_phi);
-            if (cand.size() < 2) continue;
+            // the builders' next-window prefetch is a choice wherever a job reads
+            // more than one window: it costs a shared-memory slot per builder
+            // thread, which may otherwise hold an operand stage
+            const bool multi_win = P.n_q > tc_window_points(prec) || win_slots(&P) > 1;
+            const int n_wp = multi_win ? 2 : 1;
+            if (cand.size() * n_wp < 2) continue;
             char key[96];
-            snprintf(key, sizeof(key), "%d,%d,%d,%d,%d", P.d, P.p, P.n_q, prec, fi);
-            int best = -1;
+            snprintf(key, sizeof(key), "%d,%d,%d,%d,%d,%d", P.d, P.p, P.n_q, prec, fi, (int)P.boxed);
+            int best = INT_MIN, best_wp = 0;
             {
                 std::lock_guard<std::mutex> lock(g_tune_mutex);
                 auto it = g_tune_cache.find(key);
-                if (it != g_tune_cache.end()) best = it->second;
+                if (it != g_tune_cache.end()) {
+                    best = it->second.first;
+                    best_wp = it->second.second;
+                }
             }
-            if (best < 0) {
+            if (best == INT_MIN) {
                 // sample: at most one tile per SM and at most 256 MB of element output
                 // two full waves of tiles (every SM busy, as in a production launch;
                 // a partial wave would time one tile's latency instead), at most 2 GB
@@ -988,9 +1038,13 @@ static fe_status autotune_plan(fe_plan &P) {
                 FE_CUDA(cudaMemcpyAsync(kap.p, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice,
                                         P.stream), "autotune upload");
                 float best_ms = 1e30f;
-                for (int np : cand) {
-                    fe_status st = pack_operand(P, prec, fi, np);
-                    if (st) return st;
+                for (size_t ci = 0; ci < cand.size() * n_wp; ++ci) {
+                    const int np = cand[ci / n_wp], wp = (int)(ci % n_wp);
+                    if (wp == 0) {
+                        fe_status st = pack_operand(P, prec, fi, np);
+                        if (st) return st;
+                    }
+                    P.op[prec][fi].win_pref = wp;
                     void *A[2] = {nullptr, nullptr};
                     A[fi] = out.p;
                     TcArgs a{};
@@ -1019,6 +1073,7 @@ static fe_status autotune_plan(fe_plan &P) {
                     if (ms_min < best_ms) {
                         best_ms = ms_min;
                         best = np;
+                        best_wp = wp;
                     }
                 }
                 int stw = 0;
@@ -1028,12 +1083,13 @@ static fe_status autotune_plan(fe_plan &P) {
                     return fail(FE_ERR_CUDA, "autotune run reported status %d", stw);
                 }
                 std::lock_guard<std::mutex> lock(g_tune_mutex);
-                g_tune_cache[key] = best;
+                g_tune_cache[key] = {best, best_wp};
             }
             if (P.tuned_np[prec][fi] != best) {
                 fe_status st = pack_operand(P, prec, fi, best);
                 if (st) return st;
             }
+            P.op[prec][fi].win_pref = best_wp;
         }
     }
     FE_CUDA(cudaStreamSynchronize(P.stream), "autotune");

@@ -52,6 +52,7 @@ struct TcOperand {
     int n_blk = 1;                 // 1, or 3 for split TF32 (head, head, tail)
     int rows_per_pass = 0;         // 0: columns are symmetric pairs; R: pass n holds rows nR..nR+R-1 (all l)
     float p_inv_scale = 1.f;       // 2^-e_P
+    int win_pref = 0;              // 1: the builders prefetch the next window (autotuned where a job reads several)
 };
 
 // One plan's share of a (possibly batched) tensor-core element launch.
@@ -116,6 +117,7 @@ struct TcArgs {
     int pitch_max;             // staging pitch (floats) over staged segments, 0 if none
     int ring_a;                // stages of the built-operand ring (2..TC_MAX_RING_A)
     int ring_b;                // stages of the shared-operand ring (2..TC_MAX_RING_B)
+    int win_buf;               // 1: a per-builder-thread shared-memory slot for the next window
     int *status;
     unsigned long long timeout_ns;
 };

@@ -69,7 +69,7 @@ struct Smem {
     uint8_t *B;        // [ring_b][np_max][128 B]
     float *stage;      // [4][32][pitch_max]
     float *meta;       // [2][128] unscale per cell for the two accumulators
-    float *rowc;       // [128][8] per cell: G pairs * scale (stiffness), |det J| * scale (mass)
+    float *wnext;      // [128][KW + 4] each builder thread's next window (win_buf)
     uint64_t *a_full, *a_empty, *b_full, *b_empty, *acc_full, *acc_empty, *meta_full, *meta_empty, *drain;
     uint32_t *tmem_holder;
     int *flags;        // [0] abort, [1] status bits
@@ -81,6 +81,12 @@ __host__ __device__ inline size_t bytes_B(const TcArgs &a) { return (size_t)a.ri
 __host__ __device__ inline size_t bytes_stage(const TcArgs &a) {
     return a.pitch_max > 0 ? align1k((size_t)4 * 32 * a.pitch_max * sizeof(float)) : 0;
 }
+// the next-window slots: a pitch of KW + 4 floats keeps each quarter warp's
+// 16-byte accesses on distinct banks
+__host__ __device__ inline int wnext_pitch(const TcArgs &a) { return tc_window_points(a.prec) + 4; }
+__host__ __device__ inline size_t bytes_wnext(const TcArgs &a) {
+    return a.win_buf ? (size_t)TC_M * wnext_pitch(a) * sizeof(float) : 0;
+}
 
 __device__ inline Smem carve(uint8_t *raw, const TcArgs &a) {
     uintptr_t p = (reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023);
@@ -89,9 +95,10 @@ __device__ inline Smem carve(uint8_t *raw, const TcArgs &a) {
     s.B = s.A + bytes_A(a);
     s.stage = reinterpret_cast<float *>(s.B + bytes_B(a));
     uint8_t *q = reinterpret_cast<uint8_t *>(s.stage) + bytes_stage(a);
+    s.wnext = reinterpret_cast<float *>(q);
+    q += bytes_wnext(a);
     s.meta = reinterpret_cast<float *>(q);
-    s.rowc = s.meta + 2 * TC_M;
-    q = reinterpret_cast<uint8_t *>(s.rowc + 8 * TC_M);
+    q = reinterpret_cast<uint8_t *>(s.meta + 2 * TC_M);
     q = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(q) + 7) & ~uintptr_t(7));
     uint64_t *b = reinterpret_cast<uint64_t *>(q);
     s.a_full = b;
@@ -124,7 +131,9 @@ __device__ __forceinline__ const TcSeg &seg_of(const TcArgs &a, int64_t t) {
 __device__ __forceinline__ int first_form(const TcSeg &S) { return (S.form_mask & 1) ? 0 : 1; }
 
 // The launch's jobs, (tile, form, N pass), in order: tiles in global order,
-// then the tile's forms, then the passes.  A job costs its form's K chunks
+// then the passes, and in each pass the forms (so the short mass passes, whose
+// stores outlast their MMAs, alternate with the long stiffness passes).  A job
+// costs its form's K chunks
 // plus TC_JOB_EPI_COST.  CTA i of G takes the contiguous jobs whose cost
 // offset lies in [i T / G, (i + 1) T / G) of the total T, so the CTAs get the
 // same work to within one job even when the tiles do not divide evenly over
@@ -142,17 +151,22 @@ struct Jobs {
 
     __device__ __forceinline__ bool live() const { return c < hi && t < n_tiles; }
 
+    // the first form after g whose layout has pass `pass` (-1: none)
+    __device__ __forceinline__ int form_after(int g, int pass) const {
+        for (++g; g < MAX_FORMS; ++g)
+            if ((S->form_mask & (1 << g)) && pass < S->op[g].n_pass) return g;
+        return -1;
+    }
+
     __device__ __forceinline__ void advance() {
-        const TcOperand &op = S->op[f];
-        c += op.n_kchunks + TC_JOB_EPI_COST;
-        if (++n < op.n_pass) return;
-        n = 0;
-        int nf = f + 1;
-        while (nf < MAX_FORMS && !(S->form_mask & (1 << nf))) ++nf;
-        if (nf < MAX_FORMS) {
+        c += S->op[f].n_kchunks + TC_JOB_EPI_COST;
+        int nf = form_after(f, n);
+        if (nf < 0) nf = form_after(-1, ++n);
+        if (nf >= 0) {
             f = nf;
             return;
         }
+        n = 0;
         if (++t >= n_tiles) return;
         if (BATCHED)
             while (t >= S->tile_begin + S->tiles) ++S;   // t < n_tiles: a later segment holds it
@@ -284,7 +298,25 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         if (J.live()) prefetch_tile(J.t);
         int64_t cur_t = -1;
         float unscale_f[MAX_FORMS] = {1.f, 1.f};
+        float gf[7];          // this cell's scaled G pairs and |det J|
         int qw_loaded = -1;
+        // window prefetch (win_buf): the next distinct window this thread will
+        // need is copied asynchronously into its own shared-memory slot while
+        // the current one is used; key = qw * 16 + slot, -1 for none
+        float *const myslot = sm.wnext + cl * wnext_pitch(a);
+        int pf_key = -1, want_pf = -1;
+        auto issue_pf = [&](const float *__restrict__ W, int ldw, int slots, int64_t c, bool valid, int key) {
+            const int pq = key >> 4, ps = key & 15;
+            const float *row = W + (c * slots + ps) * ldw + pq * KW;
+#pragma unroll
+            for (int i = 0; i < KW; i += 4) {
+                const bool in = valid && pq * KW + i < ldw;
+                cp_async16_zfill(myslot + i, in ? row + i : W, in ? 16u : 0u);
+            }
+            cp_async_commit();
+        };
+        int as = 0;           // built-operand stage of chunk ac, and its use parity
+        uint32_t aph = 0;
         for (; J.live() && !*abort_flag; J.advance()) {
             const int64_t t = J.t;
             const TcSeg &S = *J.S;
@@ -297,9 +329,11 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             const bool valid = cell < s_ncells;
             const int s_slots = S.win_slots;
             if (t != cur_t) {
-                // a new tile: this cell's factors (scaled geometry to the shared row
-                // table, unscales) and, where its points fit one window, the window
+                // a new tile: this cell's factors (scaled geometry, unscales) and,
+                // where its points fit one window, the window
                 cur_t = t;
+                if (pf_key >= 0) cp_async_wait_all();   // (the slot is reused below)
+                pf_key = -1;
                 prefetch_tile(t + 1);
                 unscale_f[0] = unscale_f[1] = 1.f;
                 {
@@ -314,7 +348,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         rec[4 * i + 3] = v.w;
                     }
 #pragma unroll
-                    for (int j = 0; j < 7; ++j) sm.rowc[cl * 8 + j] = rec[CELLF_G + j];
+                    for (int j = 0; j < 7; ++j) gf[j] = rec[CELLF_G + j];
                     if (valid) {
                         unscale_f[0] = rec[CELLF_UNSCALE];
                         unscale_f[1] = rec[CELLF_UNSCALE + 1];
@@ -331,8 +365,6 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             }
             const int f = J.f;
             const TcOperand op = S.op[f];
-            const int per_qw = op.n_pairs * op.n_blk;
-            const int n_blocks = op.n_qw * per_qw;
             const int b = jb & 1, ub = jb >> 1;
             if (jb >= 2 && !mbar_wait_warp(&sm.meta_empty[b], (ub - 1) & 1, deadline)) {
                 sm.flags[0] = 1;
@@ -341,9 +373,11 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             sm.meta[b * TC_M + cl] = unscale_f[f];
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.meta_full[b]);
+            // running K block (window qw, pair j, split block blk) of the chunk row
+            int qw = 0, j = 0, blk = 0;
             for (int ch = 0; ch < op.n_kchunks; ++ch) {
-                const int s = ac % RA, ua = ac / RA;
-                if (ac >= RA && !mbar_wait_warp(&sm.a_empty[s], (ua - 1) & 1, deadline)) {
+                const int s = as;
+                if (ac >= RA && !mbar_wait_warp(&sm.a_empty[s], aph ^ 1u, deadline)) {
                     sm.flags[0] = 1;
                     break;
                 }
@@ -351,19 +385,51 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 uint8_t *rowp = stA + (cl >> 3) * 1024 + (cl & 7) * 128;
 #pragma unroll
                 for (int sub = 0; sub < WPC; ++sub) {
-                    const int h = ch * WPC + sub;      // K block: window qw, pair j, split block blk
-                    const int qw = h / per_qw;
-                    const int j = (h / op.n_blk) % op.n_pairs;
-                    const int blk = h % op.n_blk;
-                    const bool live = h < n_blocks;    // (e4m3: the last chunk may end with a zero block)
-                    const int cidx = (f == 0) ? j : 6;
+                    const bool live = qw < op.n_qw;    // (e4m3: the last chunk may end with a zero block)
                     // window slot: simplices share one; boxed cells have one per pair and one for the mass form
                     const int slot = (s_slots == 1) ? 0 : ((f == 0) ? j : s_slots - 1);
-                    if (live && qw * 16 + slot != qw_loaded) {
-                        qw_loaded = qw * 16 + slot;
-                        load_own(s_win, s_ldw, cell * s_slots + slot, valid, qw);
+                    const int key = qw * 16 + slot;
+                    if (live && key != qw_loaded) {
+                        if (key == pf_key) {
+                            cp_async_wait_all();
+#pragma unroll
+                            for (int i = 0; i < KW; i += 4) {
+                                const float4 v = *reinterpret_cast<const float4 *>(myslot + i);
+                                win[i] = v.x;
+                                win[i + 1] = v.y;
+                                win[i + 2] = v.z;
+                                win[i + 3] = v.w;
+                            }
+                        } else {
+                            if (pf_key >= 0) cp_async_wait_all();   // a stale copy lands before the slot is reused
+                            load_own(s_win, s_ldw, cell * s_slots + slot, valid, qw);
+                        }
+                        pf_key = -1;
+                        qw_loaded = key;
+                        if (a.win_buf) {
+                            // the next window of this job that differs from this one ...
+                            int nk = -1;
+                            if (s_slots > 1 && f == 0) {
+                                if (j + 1 < op.n_pairs) nk = qw * 16 + j + 1;
+                                else if (qw + 1 < op.n_qw) nk = (qw + 1) * 16;
+                            } else if (qw + 1 < op.n_qw) {
+                                nk = (qw + 1) * 16 + slot;
+                            }
+                            // ... or the first window of the next job, when it is this tile's
+                            if (nk < 0) {
+                                Jobs<BATCHED> Jn = J;
+                                Jn.advance();
+                                if (Jn.live() && Jn.t == t) nk = (s_slots == 1 || Jn.f == 0) ? 0 : s_slots - 1;
+                            }
+                            want_pf = (nk == key) ? -1 : nk;
+                        }
                     }
-                    const float gj = sm.rowc[cl * 8 + cidx];
+                    float gj = gf[6];
+                    if (f == 0) {
+                        gj = gf[0];
+#pragma unroll
+                        for (int i = 1; i < 6; ++i) gj = (j == i) ? gf[i] : gj;
+                    }
 #pragma unroll
                     for (int kk = 0; kk < GPB; ++kk) {
                         const int k = sub * GPB + kk;   // granule of the 128-byte row
@@ -399,14 +465,31 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         if (!live) v = make_uint4(0u, 0u, 0u, 0u);
                         *reinterpret_cast<uint4 *>(rowp + ((k ^ (cl & 7)) << 4)) = v;
                     }
+                    if (want_pf >= 0) {   // issued once this block's window registers are consumed
+                        issue_pf(s_win, s_ldw, s_slots, cell, valid, want_pf);
+                        pf_key = want_pf;
+                        want_pf = -1;
+                    }
+                    if (++blk == op.n_blk) {
+                        blk = 0;
+                        if (++j == op.n_pairs) {
+                            j = 0;
+                            ++qw;
+                        }
+                    }
                 }
                 fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.a_full[s]);
                 ++ac;
+                if (++as == RA) {
+                    as = 0;
+                    aph ^= 1u;
+                }
             }
             ++jb;
         }
+        cp_async_wait_all();   // no prefetch may still be landing when the CTA leaves
     } else if (warp == W_MMA) {
         // ======================= MMA =======================
         // Consumes chunk mc from the two rings (stage mc % RA of the built
@@ -414,6 +497,8 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         // completions free the stages asynchronously, so the tensor pipe always
         // holds the next chunk's MMAs while the producers refill.
         int64_t mc = 0;
+        int sa = 0, sb = 0;          // stages of chunk mc in the two rings
+        uint32_t pa = 0, pb = 0;     // their use parities
         int jb = 0;
         bool fail = false;
         Jobs<BATCHED> J;
@@ -429,9 +514,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             tc_fence_after();
             const uint32_t dacc = tmem + (uint32_t)(b * ACC_COLS);
             for (int ch = 0; ch < op.n_kchunks; ++ch) {
-                const int sa = (int)(mc % RA), sb = (int)(mc % RB);
-                if (!mbar_wait_warp(&sm.a_full[sa], (uint32_t)((mc / RA) & 1), deadline) ||
-                    !mbar_wait_warp(&sm.b_full[sb], (uint32_t)((mc / RB) & 1), deadline)) {
+                if (!mbar_wait_warp(&sm.a_full[sa], pa, deadline) || !mbar_wait_warp(&sm.b_full[sb], pb, deadline)) {
                     fail = true;
                     break;
                 }
@@ -449,6 +532,14 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 }
                 __syncwarp();
                 ++mc;
+                if (++sa == RA) {
+                    sa = 0;
+                    pa ^= 1u;
+                }
+                if (++sb == RB) {
+                    sb = 0;
+                    pb ^= 1u;
+                }
             }
             ++jb;
             if (*abort_flag) fail = true;
@@ -470,12 +561,13 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         BJ.start(a, blockIdx.x, gridDim.x);
         int64_t bc = 0;
         int bch = 0;
+        int s = 0;             // stage of copy bc, and its use parity
+        uint32_t ph = 0;
         bool fail = false;
         while (BJ.live() && !*abort_flag) {
             const TcOperand &op = BJ.S->op[BJ.f];
             const uint32_t bytes = (uint32_t)op.NP * TC_CHUNK_BYTES;
-            const int s = (int)(bc % RB);
-            if (bc >= RB && !mbar_wait_warp(&sm.b_empty[s], (uint32_t)(((bc / RB) - 1) & 1), deadline)) {
+            if (bc >= RB && !mbar_wait_warp(&sm.b_empty[s], ph ^ 1u, deadline)) {
                 fail = true;
                 break;
             }
@@ -486,6 +578,10 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             }
             __syncwarp();
             ++bc;
+            if (++s == RB) {
+                s = 0;
+                ph ^= 1u;
+            }
             if (++bch == op.n_kchunks) {
                 bch = 0;
                 BJ.advance();
@@ -521,7 +617,8 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             const int nph = S.n_phi, nph2 = nph * nph;
             const int n_it = (nph2 + 31) / 32;
             // 16-byte stores when every matrix starts on a 16-byte boundary
-            const bool v4 = (nph2 & 3) == 0;
+            const bool v4 = (nph2 & 3) == 0 &&
+                            ((reinterpret_cast<uintptr_t>(S.out[0]) | reinterpret_cast<uintptr_t>(S.out[1])) & 15) == 0;
             if (&S != cur) {
                 // sym index of each output position this lane writes: v4 -> positions
                 // 128 it + 4 lane + e in register 4 it + e; otherwise lane + 32 it
@@ -682,8 +779,8 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
 
 size_t tc_smem_bytes(const TcArgs &a) {
     size_t b = 1024;  // alignment slack
-    b += bytes_A(a) + bytes_B(a) + bytes_stage(a);
-    b += 2 * TC_M * sizeof(float) + 8 * TC_M * sizeof(float);
+    b += bytes_A(a) + bytes_B(a) + bytes_stage(a) + bytes_wnext(a);
+    b += 2 * TC_M * sizeof(float);
     b += 8;
     b += (2 * TC_MAX_RING_A + 2 * TC_MAX_RING_B + 9) * sizeof(uint64_t) + 8 + 16;
     return b;

@@ -123,3 +123,32 @@ def test_distorted_cells_all_formats(shape):
             x = K * 2 * 2.0 ** -23
             tol = x / (1 - x) * M + 2.0 ** -24 * np.abs(E) + slack
             assert np.all(np.abs(got - E) <= tol), (shape, form, prec, float((np.abs(got - E) / tol).max()))
+
+
+@pytest.mark.parametrize("p", [3, 5])
+def test_misaligned_buffers_same_bits(p):
+    """Element matrices written into views that start 4 bytes past a 16-byte
+    boundary, from a kappa view 8 bytes past one, are bitwise those of aligned
+    buffers: the vector loads and stores are taken only on aligned addresses
+    (P3: the staged pair layout; P5: full-row passes)."""
+    import torch
+    v, c = inputs.cube_mesh(4, 0.15, 3)
+    pts, w = api.quadrature_rule("tetrahedron", p + 1)
+    plan = api.Plan("tetrahedron", v, c, p, pts, w, precisions=("bf16",), elements_only=True)
+    kap = inputs.lognormal_kappa(plan.n_cells, plan.n_q, 5)
+    k_al = cuda(kap)
+    k_buf = torch.empty(kap.size + 1, dtype=torch.float64, device="cuda")
+    k_off = k_buf[1:].view(plan.n_cells, plan.n_q)
+    k_off.copy_(k_al)
+    assert k_off.data_ptr() % 16 == 8
+    ref = plan.element_matrices(k_al, prec="bf16")
+    n = plan.n_cells * plan.n_phi * plan.n_phi
+    outs = {}
+    for f in ("stiffness", "mass"):
+        buf = torch.full((n + 1,), float("nan"), dtype=torch.float32, device="cuda")
+        outs[f] = buf[1:].view(plan.n_cells, plan.n_phi, plan.n_phi)
+        assert outs[f].data_ptr() % 16 == 4
+    got = plan.element_matrices(k_off, prec="bf16", out=outs)
+    plan.sync()
+    for f in ("stiffness", "mass"):
+        assert torch.equal(got[f], ref[f]), f
