@@ -215,14 +215,22 @@ fe_status fe_plan_set_assembly(fe_plan *plan, int algo);
  * 1 on wherever it fits.  The element matrices are bitwise the same in every
  * mode. */
 fe_status fe_plan_set_window_prefetch(fe_plan *plan, int mode);
+/* N layout of the tensor-core contraction for these forms in this (reduced)
+ * precision: whole-row passes of `rows` rows of every element matrix each
+ * (rows * n_phi columns, at most 512; above 256 a pass is wide: both halves of
+ * the tensor memory form one accumulator and each coefficient chunk feeds two
+ * MMAs), replacing the layout the plan's autotuner chose.  The element
+ * matrices agree with every other layout to FP32 accumulation order. */
+fe_status fe_plan_set_rows_per_pass(fe_plan *plan, fe_precision prec, unsigned forms, int rows);
 /* Launch shape the tensor-core element kernel takes for these forms and this
  * (reduced) precision on this plan, as fe_element_matrices would launch it
  * now: stages of the built-operand ring (ring_a) and of the shared-operand
- * ring (ring_b), whether the builders prefetch windows (win_buf, 0/1), and
- * whether the epilogue stages through shared memory (staged, 0/1).  Any
- * output pointer may be NULL.  No device work. */
+ * ring (ring_b), whether the builders prefetch windows (win_buf, 0/1),
+ * whether the epilogue stages through shared memory (staged, 0/1), and the
+ * number of tensor-memory accumulators (n_acc: 2 of 256 columns, or 1 of 512
+ * when a pass is wide).  Any output pointer may be NULL.  No device work. */
 fe_status fe_plan_tc_config(fe_plan *plan, unsigned forms, fe_precision prec, int32_t *ring_a, int32_t *ring_b,
-                            int32_t *win_buf, int32_t *staged);
+                            int32_t *win_buf, int32_t *staged, int32_t *n_acc);
 /* Device memory the plan holds, in bytes: plan_bytes for what plan creation
  * allocated (mesh, tabulations, operand images, dof map, pattern, assembly
  * streams, action tables built so far), workspace_bytes for the workspaces

@@ -61,7 +61,8 @@ SIGNATURES = {
     "fe_plan_set_fusion": [_vp, ctypes.c_int, _pi32],
     "fe_plan_set_assembly": [_vp, ctypes.c_int],
     "fe_plan_set_window_prefetch": [_vp, ctypes.c_int],
-    "fe_plan_tc_config": [_vp, ctypes.c_uint, ctypes.c_int, _pi32, _pi32, _pi32, _pi32],
+    "fe_plan_set_rows_per_pass": [_vp, ctypes.c_int, ctypes.c_uint, ctypes.c_int],
+    "fe_plan_tc_config": [_vp, ctypes.c_uint, ctypes.c_int, _pi32, _pi32, _pi32, _pi32, _pi32],
     "fe_plan_memory": [_vp, _pi64, _pi64],
     "fe_plan_sizes": [_vp, _pi64, _pi64, _pi64, _pi64, _pi32, _pi32],
     "fe_csr_pattern": [_vp, _vp, _vp],

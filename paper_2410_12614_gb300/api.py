@@ -326,13 +326,19 @@ class Plan:
         element matrices are bitwise the same."""
         check(load().fe_plan_set_window_prefetch(self._h, int(mode)), "fe_plan_set_window_prefetch")
 
+    def set_rows_per_pass(self, rows: int, forms=("stiffness", "mass"), prec="bf16"):
+        """fe_plan_set_rows_per_pass: whole-row passes of `rows` rows (wide above
+        256 columns) for these forms in this precision, instead of the tuned layout."""
+        check(load().fe_plan_set_rows_per_pass(self._h, PRECISIONS[prec], self._forms_mask(forms), int(rows)),
+              "fe_plan_set_rows_per_pass")
+
     def tc_config(self, forms=("stiffness", "mass"), prec="bf16"):
         """fe_plan_tc_config: the tensor-core launch shape for these forms and
-        precision, as a dict (ring_a, ring_b, win_buf, staged)."""
-        v = [ctypes.c_int32() for _ in range(4)]
+        precision, as a dict (ring_a, ring_b, win_buf, staged, n_acc)."""
+        v = [ctypes.c_int32() for _ in range(5)]
         check(load().fe_plan_tc_config(self._h, self._forms_mask(forms), PRECISIONS[prec],
                                        *[ctypes.byref(x) for x in v]), "fe_plan_tc_config")
-        return dict(zip(("ring_a", "ring_b", "win_buf", "staged"), (x.value for x in v)))
+        return dict(zip(("ring_a", "ring_b", "win_buf", "staged", "n_acc"), (x.value for x in v)))
 
     def memory(self):
         """(plan_bytes, workspace_bytes) of device memory the plan holds (fe_plan_memory)."""

@@ -517,8 +517,26 @@ fe_status fe_plan_set_window_prefetch(fe_plan *plan, int mode) {
     return FE_OK;
 }
 
+fe_status fe_plan_set_rows_per_pass(fe_plan *plan, fe_precision prec, unsigned forms, int rows) {
+    g_err.clear();
+    fe_status st = check_call(plan, forms, prec);
+    if (st) return st;
+    if (prec == FE_PREC_FP64) return fail(FE_ERR_INVALID_ARG, "the FP64 path has no N layout");
+    if (rows < 1 || rows > plan->n_phi || rows * plan->n_phi > 2 * TC_MAX_NP)
+        return fail(FE_ERR_INVALID_ARG, "rows must lie in 1..min(n_phi, 512 / n_phi)");
+    for (int fi = 0; fi < 2; ++fi)
+        if (forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS)) {
+            const int wp = plan->op[prec][fi].win_pref;
+            st = pack_operand(*plan, prec, fi, -rows);
+            if (st) return st;
+            plan->op[prec][fi].win_pref = wp;
+        }
+    FE_CUDA(cudaStreamSynchronize(plan->stream), "operand upload");
+    return FE_OK;
+}
+
 fe_status fe_plan_tc_config(fe_plan *plan, unsigned forms, fe_precision prec, int32_t *ring_a, int32_t *ring_b,
-                            int32_t *win_buf, int32_t *staged) {
+                            int32_t *win_buf, int32_t *staged, int32_t *n_acc) {
     g_err.clear();
     fe_status st = check_call(plan, forms, prec);
     if (st) return st;
@@ -533,6 +551,7 @@ fe_status fe_plan_tc_config(fe_plan *plan, unsigned forms, fe_precision prec, in
     if (ring_b) *ring_b = a.ring_b;
     if (win_buf) *win_buf = a.win_buf;
     if (staged) *staged = a.seg0.staged;
+    if (n_acc) *n_acc = a.n_acc;
     return FE_OK;
 }
 
@@ -701,6 +720,10 @@ static TcSeg make_tc_seg(fe_plan *P, unsigned forms, int prec, const double *ver
 // epilogue for every segment that fits (greedy, in segment order).
 static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status, unsigned long long wait_limit_ns) {
     a.win_buf = 0;   // (the staging decisions below are taken without it)
+    a.n_acc = 2;     // two 256-column accumulators unless a pass is wide
+    for (int i = 0; i < n; ++i)
+        for (int f = 0; f < MAX_FORMS; ++f)
+            if (((segs[i].form_mask >> f) & 1) && segs[i].op[f].NP > TC_MAX_NP) a.n_acc = 1;
     a.prec = prec;
     a.elem_bytes = host::format_of(prec).elem_bytes;
     a.idesc = idesc_for(prec);

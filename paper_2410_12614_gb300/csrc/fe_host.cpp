@@ -764,6 +764,10 @@ std::vector<int> np_candidates(int n_phi_) {
         return out;
     }
     out.push_back(-row_block_rows(n_phi_));
+    // wide passes: as many rows as fill both 256-column TMEM halves (one
+    // accumulator, each coefficient chunk feeding two MMAs)
+    const int wide_rows = 512 / n_phi_;
+    if (wide_rows > row_block_rows(n_phi_) && wide_rows * n_phi_ > 256) out.push_back(-wide_rows);
     // half as many rows per pass: a smaller staging area leaves room for a
     // deeper operand ring
     if (row_block_rows(n_phi_) >= 2) out.push_back(-(row_block_rows(n_phi_) / 2));

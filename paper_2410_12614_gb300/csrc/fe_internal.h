@@ -47,7 +47,7 @@ struct TcOperand {
     int n_qw = 0;                  // quadrature windows
     int n_pairs = 1;               // symmetric (s,t) pairs (stiffness) or 1 (mass)
     int n_pass = 0;                // N passes
-    int NP = 0;                    // N per pass (multiple of 16, <= 256)
+    int NP = 0;                    // N per pass (multiple of 16; <= 256, or <= 512 for a wide full-row pass)
     int n_cols = 0;                // operand columns that may carry a pair (sym_kl entries)
     int n_blk = 1;                 // 1, or 3 for split TF32 (head, head, tail)
     int rows_per_pass = 0;         // 0: columns are symmetric pairs; R: pass n holds rows nR..nR+R-1 (all l)
@@ -118,6 +118,7 @@ struct TcArgs {
     int ring_a;                // stages of the built-operand ring (2..TC_MAX_RING_A)
     int ring_b;                // stages of the shared-operand ring (2..TC_MAX_RING_B)
     int win_buf;               // 1: a per-builder-thread shared-memory slot for the next window
+    int n_acc;                 // TMEM accumulators: 2 of 256 columns, or 1 of 512 when a pass is wide
     int *status;
     unsigned long long timeout_ns;
 };

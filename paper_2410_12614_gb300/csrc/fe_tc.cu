@@ -220,6 +220,9 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
     const int NPm = a.np_max;
 
     const int RA = a.ring_a, RB = a.ring_b;
+    // accumulators: two 256-column buffers (pass j in buffer j % 2), or, when a
+    // pass is wide, one of 512 columns (pass j a new use of buffer 0)
+    const int NACC = a.n_acc, acc_mask = NACC - 1, acc_shift = NACC - 1;
     if (tid == 0) {
         for (int s = 0; s < RA; ++s) {
             mbar_init(&sm.a_full[s], TC_M / 32);         // one arrival per builder warp
@@ -365,7 +368,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             }
             const int f = J.f;
             const TcOperand op = S.op[f];
-            const int b = jb & 1, ub = jb >> 1;
+            const int b = jb & 1, ub = jb >> 1;   // (the unscales are double-buffered whatever the accumulators)
             if (jb >= 2 && !mbar_wait_warp(&sm.meta_empty[b], (ub - 1) & 1, deadline)) {
                 sm.flags[0] = 1;
                 break;
@@ -505,9 +508,13 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
         J.start(a, blockIdx.x, gridDim.x);
         for (; J.live() && !fail; J.advance()) {
             const TcOperand op = J.S->op[J.f];
-            const uint32_t idesc = a.idesc | ((uint32_t)(op.NP >> 3) << 17);
-            const int b = jb & 1, ub = jb >> 1;
-            if (jb >= 2 && !mbar_wait_warp(&sm.acc_empty[b], (ub - 1) & 1, deadline)) {
+            // a wide pass (N > 256, both TMEM halves as one accumulator) takes two
+            // MMAs per K step: columns [0, 256) and [256, NP), B rows likewise
+            const bool wide = op.NP > ACC_COLS;
+            const uint32_t idesc = a.idesc | ((uint32_t)((wide ? ACC_COLS : op.NP) >> 3) << 17);
+            const uint32_t idesc2 = a.idesc | ((uint32_t)((wide ? op.NP - ACC_COLS : 16) >> 3) << 17);
+            const int b = jb & acc_mask, ub = jb >> acc_shift;
+            if (jb >= NACC && !mbar_wait_warp(&sm.acc_empty[b], (ub - 1) & 1, deadline)) {
                 fail = true;
                 break;
             }
@@ -523,9 +530,13 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                     const uint32_t a0 = smem_u32(sm.A + sa * (TC_M * TC_CHUNK_BYTES));
                     const uint32_t b0 = smem_u32(sm.B + (size_t)sb * NPm * TC_CHUNK_BYTES);
 #pragma unroll
-                    for (int ks = 0; ks < TC_CHUNK_BYTES / 32; ++ks)
-                        umma<KIND>(dacc, sdesc_sw128(a0 + 32 * ks), sdesc_sw128(b0 + 32 * ks), idesc,
-                                   (ch | ks) != 0 ? 1u : 0u);
+                    for (int ks = 0; ks < TC_CHUNK_BYTES / 32; ++ks) {
+                        const uint64_t ad = sdesc_sw128(a0 + 32 * ks);
+                        umma<KIND>(dacc, ad, sdesc_sw128(b0 + 32 * ks), idesc, (ch | ks) != 0 ? 1u : 0u);
+                        if (wide)
+                            umma<KIND>(dacc + ACC_COLS, ad, sdesc_sw128(b0 + ACC_COLS * TC_CHUNK_BYTES + 32 * ks), idesc2,
+                                       (ch | ks) != 0 ? 1u : 0u);
+                    }
                     umma_commit(&sm.a_empty[sa]);
                     umma_commit(&sm.b_empty[sb]);
                     if (ch == op.n_kchunks - 1) umma_commit(&sm.acc_full[b]);
@@ -635,9 +646,10 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
             const int64_t s_ncells = S.n_cells;
             const int s_staged = S.staged;
             const int32_t *__restrict__ s_symkl = S.sym_kl;
-            const int b = jb & 1, ub = jb >> 1;
+            const int b = jb & acc_mask, ub = jb >> acc_shift;   // accumulator
+            const int mb = jb & 1, mub = jb >> 1;                  // unscale buffer
             bool ok = !*abort_flag && mbar_wait_warp(&sm.acc_full[b], ub & 1, deadline) &&
-                      mbar_wait_warp(&sm.meta_full[b], ub & 1, deadline);
+                      mbar_wait_warp(&sm.meta_full[mb], mub & 1, deadline);
             if (s_staged) {
                 // the two warps of this lane group meet at named barriers below:
                 // they take one common outcome here, so that a wait that gave up
@@ -652,9 +664,9 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 break;
             }
             tc_fence_after();
-            const float us = sm.meta[b * TC_M + g * 32 + lane];
+            const float us = sm.meta[mb * TC_M + g * 32 + lane];
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.meta_empty[b]);
+            if (lane == 0) mbar_arrive(&sm.meta_empty[mb]);
             const uint32_t tbase = tmem + (uint32_t)(b * ACC_COLS) + ((uint32_t)(g * 32) << 16);
             const int64_t cell0 = (t - S.tile_begin) * TC_M + g * 32;
             if (s_staged) {
@@ -732,6 +744,35 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                     }
                 }
                 named_bar_sync(1 + g, 64);
+            } else if (op.rows_per_pass > 0) {
+                // full-row pass not staged (or wide): this cell's rows [k0, k0 + R) are one
+                // contiguous run of len values, column c of the pass at offset c; each lane
+                // writes its own cell's 32 columns per block, as 16-byte stores where the
+                // run starts on a 16-byte boundary
+                const int64_t mycell = cell0 + lane;
+                const int k0 = n * op.rows_per_pass;
+                const int len = (nph - k0 < op.rows_per_pass ? nph - k0 : op.rows_per_pass) * nph;
+                float *__restrict__ run = (out && mycell < s_ncells) ? out + mycell * (int64_t)nph2 + (int64_t)k0 * nph : nullptr;
+                const bool v4r = (nph & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+                for (int c0 = 32 * h; c0 < op.NP; c0 += 64) {
+                    uint32_t r[32];
+                    tmem_ld32(tbase + (uint32_t)c0, r);
+                    if (!run) continue;
+                    if (v4r && c0 + 32 <= len) {
+#pragma unroll
+                        for (int i = 0; i < 32; i += 4)
+                            __stcs(reinterpret_cast<float4 *>(run + c0 + i),
+                                   make_float4(__uint_as_float(r[i]) * us, __uint_as_float(r[i + 1]) * us,
+                                               __uint_as_float(r[i + 2]) * us, __uint_as_float(r[i + 3]) * us));
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (c0 + i < len) __stcs(run + c0 + i, __uint_as_float(r[i]) * us);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.acc_empty[b]);
             } else {
                 const int64_t mycell = cell0 + lane;
                 for (int c0 = 32 * h; c0 < op.NP; c0 += 64) {
@@ -742,14 +783,6 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
 #pragma unroll
                         for (int i = 0; i < 32; ++i) {
                             const int col = n * op.NP + c0 + i;
-                            if (op.rows_per_pass > 0) {
-                                // full-row layout: column c of pass n is entry (nR + c / n_phi, c % n_phi)
-                                const int cc = c0 + i;
-                                const int k = n * op.rows_per_pass + cc / nph;
-                                if (cc < op.NP && cc < op.rows_per_pass * nph && k < nph)
-                                    __stcs(dst + k * nph + cc % nph, __uint_as_float(r[i]) * us);
-                                continue;
-                            }
                             const int32_t kl = (c0 + i < op.NP && col < op.n_cols) ? __ldg(s_symkl + col) : -1;
                             if (kl >= 0) {   // (padding columns carry no pair)
                                 const int k = kl & 0xFFFF, l = kl >> 16;
@@ -796,6 +829,7 @@ bool tc_can_stage(const TcArgs &a, const TcSeg &seg) {
                 if (seg.op[f].n_pass != 1) return false;
                 pairs = true;
             }
+            if (seg.op[f].NP > ACC_COLS) return false;   // a wide pass leaves from registers
             np = seg.op[f].NP > np ? seg.op[f].NP : np;
         }
     if (pairs && seg.n_phi * seg.n_phi > 32 * MAX_F2S_IT) return false;
