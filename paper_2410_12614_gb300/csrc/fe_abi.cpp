@@ -997,117 +997,127 @@ static fe_status pack_operand(fe_plan &P, int prec, int fi, int np_pass) {
 
 namespace {
 std::mutex g_tune_mutex;
-std::map<std::string, std::pair<int, int>> g_tune_cache;  // "(d,p,n_q,prec,form,boxed)" -> (N-pass width, window prefetch)
+std::map<std::string, std::pair<int, int>> g_tune_cache;  // "(d,p,n_q,prec,forms,boxed)" -> (N layout, window prefetch)
 }  // namespace
 
 // Autotuner for the tile shape of every (cell type, degree, quadrature size,
-// precision, form): the N layout of the contraction when the symmetric pairs
-// need more than one 256-column accumulator (whole rows per pass, or pairs in
-// passes of a given width).  Candidates come from host::np_candidates; each is
-// timed with CUDA events on a sample of this plan's own cells (unit
-// coefficient) -- two full waves of tiles, so that every SM runs as in a
-// production launch, with the L2 flushed before each run -- and the fastest is
-// kept.  Results are cached per key for the life of the process.
-// FE_GB300_AUTOTUNE=0 keeps the default shapes.
+// precision, set of forms): the N layout of the contraction when the symmetric
+// pairs need more than one 256-column accumulator (whole rows per pass, wide
+// passes of up to 512 columns, or pairs in passes of a given width), and, where
+// a job reads several coefficient windows, the builders' window prefetch.
+// Candidates come from host::np_candidates; each is applied to all the plan's
+// forms and timed with CUDA events as one launch of them, as production runs
+// it, on a sample of this plan's own cells (unit coefficient) -- two full waves
+// of tiles, so that every SM runs as in a production launch, with the L2
+// flushed before each run -- and the fastest is kept.  Results are cached per
+// key for the life of the process.  FE_GB300_AUTOTUNE=0 keeps the default
+// shapes.
 static fe_status autotune_plan(fe_plan &P) {
     const char *env = getenv("FE_GB300_AUTOTUNE");
     if (env && env[0] == '0') return FE_OK;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned forms = P.form_mask & (FE_FORM_STIFFNESS | FE_FORM_MASS);
+    const int n_forms = n_forms_of(forms);
     for (int prec = 1; prec <= 5; ++prec) {
         if (!(P.prec_mask & FE_PREC_MASK(prec))) continue;
-        for (int fi = 0; fi < 2; ++fi) {
-            const unsigned form = fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS;
-            if (!(P.form_mask & form)) continue;
-            std::vector<int> cand = host::np_candidates(P.n_phi);
-            // the builders' next-window prefetch is a choice wherever a job reads
-            // more than one window: it costs a shared-memory slot per builder
-            // thread, which may otherwise hold an operand stage
-            const bool multi_win = P.n_q > tc_window_points(prec) || win_slots(&P) > 1;
-            const int n_wp = multi_win ? 2 : 1;
-            if (cand.size() * n_wp < 2) continue;
-            char key[96];
-            snprintf(key, sizeof(key), "%d,%d,%d,%d,%d,%d", P.d, P.p, P.n_q, prec, fi, (int)P.boxed);
-            int best = INT_MIN, best_wp = 0;
-            {
-                std::lock_guard<std::mutex> lock(g_tune_mutex);
-                auto it = g_tune_cache.find(key);
-                if (it != g_tune_cache.end()) {
-                    best = it->second.first;
-                    best_wp = it->second.second;
-                }
+        std::vector<int> cand = host::np_candidates(P.n_phi);
+        // the builders' next-window prefetch is a choice wherever a job reads
+        // more than one window: it costs a shared-memory slot per builder
+        // thread, which may otherwise hold an operand stage
+        const bool multi_win = P.n_q > tc_window_points(prec) || win_slots(&P) > 1;
+        const int n_wp = multi_win ? 2 : 1;
+        if (cand.size() * n_wp < 2) continue;
+        char key[96];
+        snprintf(key, sizeof(key), "%d,%d,%d,%d,%u,%d", P.d, P.p, P.n_q, prec, forms, (int)P.boxed);
+        int best = INT_MIN, best_wp = 0;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mutex);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                best = it->second.first;
+                best_wp = it->second.second;
             }
-            if (best == INT_MIN) {
-                // sample: at most one tile per SM and at most 256 MB of element output
-                // two full waves of tiles (every SM busy, as in a production launch;
-                // a partial wave would time one tile's latency instead), at most 2 GB
-                // of sample output
-                int64_t n = std::min<int64_t>(P.n_cells, 2ll * sms * TC_M);
-                n = std::min<int64_t>(n, std::max<int64_t>(TC_M, (2048ll << 20) / (4ll * P.n_phi * P.n_phi)));
-                DevBuf kap, out, win, cellf, flush;
-                FE_CUDA(kap.alloc(sizeof(double) * n * P.n_q), "autotune buffer");
-                // written before every timed run so that each candidate starts with
-                // the sample's output out of L2, as a production launch does: the
-                // layouts differ in how many partially written sectors they leave
-                const size_t flush_bytes = (size_t)256 << 20;
-                FE_CUDA(flush.alloc(flush_bytes), "autotune buffer");
-                // the factor kernel's windows: one per cell (simplices) or one per
-                // pair and one for the mass form (boxed cells), as win_bytes
-                FE_CUDA(win.alloc(sizeof(float) * n * win_ld(P.n_q) * win_slots(&P)), "autotune buffer");
-                FE_CUDA(cellf.alloc(sizeof(float) * n * CELLF), "autotune buffer");
-                FE_CUDA(out.alloc(sizeof(float) * n * P.n_phi * P.n_phi), "autotune buffer");
-                std::vector<double> ones((size_t)n * P.n_q, 1.0);
-                FE_CUDA(cudaMemcpyAsync(kap.p, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice,
-                                        P.stream), "autotune upload");
-                float best_ms = 1e30f;
-                for (size_t ci = 0; ci < cand.size() * n_wp; ++ci) {
-                    const int np = cand[ci / n_wp], wp = (int)(ci % n_wp);
+        }
+        if (best == INT_MIN) {
+            // Every candidate is timed as production runs it: one launch of all the
+            // plan's forms with the same layout (a wide pass in one form makes the
+            // launch single-accumulator for both), on two full waves of tiles
+            // (every SM busy; a partial wave would time one tile's latency
+            // instead), at most 4 GB of sample output, unit coefficient.
+            int64_t n = std::min<int64_t>(P.n_cells, 2ll * sms * TC_M);
+            n = std::min<int64_t>(n, std::max<int64_t>(TC_M, (4096ll << 20) / (4ll * n_forms * P.n_phi * P.n_phi)));
+            DevBuf kap, out[2], win, cellf, flush;
+            FE_CUDA(kap.alloc(sizeof(double) * n * P.n_q), "autotune buffer");
+            // written before every timed run so that each candidate starts with
+            // the sample's output out of L2, as a production launch does: the
+            // layouts differ in how many partially written sectors they leave
+            const size_t flush_bytes = (size_t)256 << 20;
+            FE_CUDA(flush.alloc(flush_bytes), "autotune buffer");
+            // the factor kernel's windows: one per cell (simplices) or one per
+            // pair and one for the mass form (boxed cells), as win_bytes
+            FE_CUDA(win.alloc(sizeof(float) * n * win_ld(P.n_q) * win_slots(&P)), "autotune buffer");
+            FE_CUDA(cellf.alloc(sizeof(float) * n * CELLF), "autotune buffer");
+            void *A[2] = {nullptr, nullptr};
+            for (int fi = 0; fi < 2; ++fi)
+                if (forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS)) {
+                    FE_CUDA(out[fi].alloc(sizeof(float) * n * P.n_phi * P.n_phi), "autotune buffer");
+                    A[fi] = out[fi].p;
+                }
+            std::vector<double> ones((size_t)n * P.n_q, 1.0);
+            FE_CUDA(cudaMemcpyAsync(kap.p, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice,
+                                    P.stream), "autotune upload");
+            float best_ms = 1e30f;
+            for (size_t ci = 0; ci < cand.size() * n_wp; ++ci) {
+                const int np = cand[ci / n_wp], wp = (int)(ci % n_wp);
+                for (int fi = 0; fi < 2; ++fi) {
+                    if (!(forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS))) continue;
                     if (wp == 0) {
                         fe_status st = pack_operand(P, prec, fi, np);
                         if (st) return st;
                     }
                     P.op[prec][fi].win_pref = wp;
-                    void *A[2] = {nullptr, nullptr};
-                    A[fi] = out.p;
-                    TcArgs a{};
-                    a.seg0 = make_tc_seg(&P, form, prec, nullptr, kap.as<double>(), A, win.as<float>(),
-                                         cellf.as<float>());
-                    a.seg0.n_cells = n;
-                    a.n_segs = 1;
-                    tc_finalize(a, &a.seg0, 1, prec, P.status.as<int>(), kDefaultWaitLimitNs);
-                    const size_t smem = tc_smem_bytes(a);
-                    {
-                        const int r = launch_factor(a, P.stream);
-                        if (r < 0) return cuda_fail((cudaError_t)(-r), "autotune factor launch");
-                    }
-                    float ms_min = 1e30f;
-                    for (int rep = 0; rep < 3; ++rep) {
-                        FE_CUDA(cudaMemsetAsync(flush.p, rep, flush_bytes, P.stream), "autotune flush");
-                        FE_CUDA(cudaEventRecord(P.ev[4], P.stream), "autotune event");
-                        int r = launch_tc_elements(a, smem, P.stream);
-                        if (r < 0) return cuda_fail((cudaError_t)(-r), "autotune launch");
-                        FE_CUDA(cudaEventRecord(P.ev[5], P.stream), "autotune event");
-                        FE_CUDA(cudaEventSynchronize(P.ev[5]), "autotune sync");
-                        float ms = 0.f;
-                        cudaEventElapsedTime(&ms, P.ev[4], P.ev[5]);
-                        if (rep > 0) ms_min = std::min(ms_min, ms);
-                    }
-                    if (ms_min < best_ms) {
-                        best_ms = ms_min;
-                        best = np;
-                        best_wp = wp;
-                    }
                 }
-                int stw = 0;
-                cudaMemcpy(&stw, P.status.p, sizeof(int), cudaMemcpyDeviceToHost);
-                if (stw) {
-                    cudaMemset(P.status.p, 0, sizeof(int));
-                    return fail(FE_ERR_CUDA, "autotune run reported status %d", stw);
+                TcArgs a{};
+                a.seg0 = make_tc_seg(&P, forms, prec, nullptr, kap.as<double>(), A, win.as<float>(), cellf.as<float>());
+                a.seg0.n_cells = n;
+                a.n_segs = 1;
+                tc_finalize(a, &a.seg0, 1, prec, P.status.as<int>(), kDefaultWaitLimitNs);
+                const size_t smem = tc_smem_bytes(a);
+                {
+                    const int r = launch_factor(a, P.stream);
+                    if (r < 0) return cuda_fail((cudaError_t)(-r), "autotune factor launch");
                 }
-                std::lock_guard<std::mutex> lock(g_tune_mutex);
-                g_tune_cache[key] = {best, best_wp};
+                float ms_min = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    FE_CUDA(cudaMemsetAsync(flush.p, rep, flush_bytes, P.stream), "autotune flush");
+                    FE_CUDA(cudaEventRecord(P.ev[4], P.stream), "autotune event");
+                    int r = launch_tc_elements(a, smem, P.stream);
+                    if (r < 0) return cuda_fail((cudaError_t)(-r), "autotune launch");
+                    FE_CUDA(cudaEventRecord(P.ev[5], P.stream), "autotune event");
+                    FE_CUDA(cudaEventSynchronize(P.ev[5]), "autotune sync");
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, P.ev[4], P.ev[5]);
+                    if (rep > 0) ms_min = std::min(ms_min, ms);
+                }
+                if (ms_min < best_ms) {
+                    best_ms = ms_min;
+                    best = np;
+                    best_wp = wp;
+                }
             }
+            int stw = 0;
+            cudaMemcpy(&stw, P.status.p, sizeof(int), cudaMemcpyDeviceToHost);
+            if (stw) {
+                cudaMemset(P.status.p, 0, sizeof(int));
+                return fail(FE_ERR_CUDA, "autotune run reported status %d", stw);
+            }
+            std::lock_guard<std::mutex> lock(g_tune_mutex);
+            g_tune_cache[key] = {best, best_wp};
+        }
+        for (int fi = 0; fi < 2; ++fi) {
+            if (!(forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS))) continue;
             if (P.tuned_np[prec][fi] != best) {
                 fe_status st = pack_operand(P, prec, fi, best);
                 if (st) return st;
