@@ -718,6 +718,10 @@ static TcSeg make_tc_seg(fe_plan *P, unsigned forms, int prec, const double *ver
 
 // Global launch shape over the segments: operand maxima, then the staged
 // epilogue for every segment that fits (greedy, in segment order).
+// Shared-operand size above which one plan's launch takes the pass-major job
+// order: a quarter of GB300's 126 MB L2.
+constexpr size_t kJobRrOperandBytes = (size_t)32 << 20;
+
 static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status, unsigned long long wait_limit_ns) {
     a.win_buf = 0;   // (the staging decisions below are taken without it)
     a.n_acc = 2;     // two 256-column accumulators unless a pass is wide
@@ -764,6 +768,24 @@ static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status, un
     }
     a.status = status;
     a.timeout_ns = wait_limit_ns;  // per wait, counted from the wait's start
+    // job order: contiguous cost ranges per CTA, or, for one plan whose shared
+    // operand (every pass and form) exceeds a quarter of the L2 cache and whose
+    // forms have the same number of passes, pass-major round robin so that the
+    // CTAs share each operand chunk through L2
+    a.job_rr = 0;
+    if (n == 1) {
+        size_t op_bytes = 0;
+        int passes = -1;
+        bool same = true;
+        for (int f = 0; f < MAX_FORMS; ++f)
+            if ((segs[0].form_mask >> f) & 1) {
+                const TcOperand &op = segs[0].op[f];
+                op_bytes += (size_t)op.n_pass * op.n_kchunks * op.NP * TC_CHUNK_BYTES;
+                if (passes >= 0 && passes != op.n_pass) same = false;
+                passes = op.n_pass;
+            }
+        if (same && op_bytes > kJobRrOperandBytes) a.job_rr = 1;
+    }
     // a next-window slot per builder thread where a job reads more than one
     // window (more points than one window holds, or one window per pair) and
     // the autotuner measured the prefetch faster for one of the forms

@@ -119,6 +119,7 @@ struct TcArgs {
     int ring_b;                // stages of the shared-operand ring (2..TC_MAX_RING_B)
     int win_buf;               // 1: a per-builder-thread shared-memory slot for the next window
     int n_acc;                 // TMEM accumulators: 2 of 256 columns, or 1 of 512 when a pass is wide
+    int job_rr;                // 1: jobs in pass-major order dealt round-robin (single plan, large operand)
     int *status;
     unsigned long long timeout_ns;
 };

@@ -141,6 +141,13 @@ __device__ __forceinline__ int first_form(const TcSeg &S) { return (S.form_mask 
 // split between two CTAs at a form or pass boundary.  Every role walks the
 // same sequence with its own cursor.
 template <bool BATCHED>
+//
+// Pass-major order (job_rr, one plan whose forms have the same number of
+// passes): the jobs ordered (pass, form, tile) and dealt round-robin, CTA i
+// taking jobs i, i + G, i + 2G, ...  All CTAs then work on the same pass at
+// the same time, so each chunk of the shared operand is read from DRAM once
+// and served to the others from L2 -- the order for an operand larger than
+// the L2 share it can keep (high degrees).  The load stays balanced to one job.
 struct Jobs {
     const TcSeg *S;   // segment of tile t
     int64_t t;        // global tile
@@ -148,8 +155,11 @@ struct Jobs {
     int64_t c;        // cost offset of this job
     int64_t hi;       // end of this CTA's cost range
     int64_t n_tiles;
+    // pass-major round robin
+    bool rr;
+    int stride, fidx, nf_rr, form_rr0, form_rr1, n_pass_rr;   // (the forms as scalars: no local array)
 
-    __device__ __forceinline__ bool live() const { return c < hi && t < n_tiles; }
+    __device__ __forceinline__ bool live() const { return rr ? n < n_pass_rr : (c < hi && t < n_tiles); }
 
     // the first form after g whose layout has pass `pass` (-1: none)
     __device__ __forceinline__ int form_after(int g, int pass) const {
@@ -159,6 +169,18 @@ struct Jobs {
     }
 
     __device__ __forceinline__ void advance() {
+        if (rr) {
+            t += stride;
+            while (t >= n_tiles && n < n_pass_rr) {
+                t -= n_tiles;
+                if (++fidx == nf_rr) {
+                    fidx = 0;
+                    ++n;
+                }
+            }
+            f = fidx ? form_rr1 : form_rr0;
+            return;
+        }
         c += S->op[f].n_kchunks + TC_JOB_EPI_COST;
         int nf = form_after(f, n);
         if (nf < 0) nf = form_after(-1, ++n);
@@ -175,6 +197,23 @@ struct Jobs {
 
     __device__ __forceinline__ void start(const TcArgs &a, int i, int G) {
         n_tiles = a.n_tiles;
+        rr = !BATCHED && a.job_rr;
+        if (rr) {
+            S = &a.seg0;
+            stride = G;
+            form_rr0 = first_form(*S);
+            form_rr1 = 1;
+            nf_rr = (S->form_mask & 3) == 3 ? 2 : 1;
+            n_pass_rr = S->op[form_rr0].n_pass;
+            // job i: (pass, form, tile) = i in mixed radix (n_pass, forms, tiles)
+            t = i % n_tiles;
+            const int64_t q = i / n_tiles;
+            fidx = (int)(q % nf_rr);
+            n = (int)(q / nf_rr);
+            f = fidx ? form_rr1 : form_rr0;
+            c = hi = 0;
+            return;
+        }
         const int64_t T = a.total_cost;
         const int64_t lo = T * i / G;
         hi = T * (i + 1) / G;
