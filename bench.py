@@ -151,15 +151,6 @@ def algorithmic_bytes(plan, prec):
     return factor, elem, asm
 
 
-def fused_element_bytes(plan, prec):
-    """Element kernel that forms the window and factors itself (one plan of
-    simplices whose points fit one window: no factor kernel): kappa (FP64),
-    connectivity and vertices in, element matrices of both forms out."""
-    eb = 8 if prec == "fp64" else 4
-    nc, nph, nq, d = plan.n_cells, plan.n_phi, plan.n_q, plan.d
-    return nc * nq * 8 + nc * (d + 1) * 4 + plan.n_vertices * d * 8 + 2 * nc * nph * nph * eb
-
-
 def action_cost(plan):
     """Algorithmic HBM bytes and FP32 flops of one action step (both forms in
     one pass): kappa (FP64), connectivity, vertices and the cells' dof lists in
@@ -395,15 +386,9 @@ def run_ours(args, rank, world):
     hbm, how = _peaks()
     fb, eb, ab = algorithmic_bytes(plan, "bf16")
     fa_avg, el_avg, as_avg = statistics.mean(fa_ms), statistics.mean(el_ms), statistics.mean(as_ms)
-    if fa_avg < 0.005:
-        # no factor launch: the element kernel's builders formed the windows and factors
-        kernels = {"tc_element_kernel": ("element matrices (tcgen05 BF16, factors formed by its builders)", el_avg,
-                                         fused_element_bytes(plan, "bf16")),
-                   "assemble_kernel": ("assembly (chunked segmented reduction)", as_avg, ab)}
-    else:
-        kernels = {"factor_kernel": ("factor (geometry + coefficient window)", fa_avg, fb),
-                   "tc_element_kernel": ("element matrices (tcgen05 BF16)", el_avg, eb),
-                   "assemble_kernel": ("assembly (chunked segmented reduction)", as_avg, ab)}
+    kernels = {"factor_kernel": ("factor (geometry + coefficient window)", fa_avg, fb),
+               "tc_element_kernel": ("element matrices (tcgen05 BF16)", el_avg, eb),
+               "assemble_kernel": ("assembly (chunked segmented reduction)", as_avg, ab)}
     dom_key = max(kernels, key=lambda k: kernels[k][1])
     dom, dom_ms, dom_bytes = kernels[dom_key]
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9

@@ -768,11 +768,6 @@ static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status, un
     }
     a.status = status;
     a.timeout_ns = wait_limit_ns;  // per wait, counted from the wait's start
-    // one plan of simplices whose quadrature points fit one window: the
-    // builders form the window and the scaled factors of their cell at the start
-    // of each tile (the factor kernel's arithmetic, in its order), so the factor
-    // launch and its workspace round trip go away
-    a.fuse_factor = (n == 1 && segs[0].win_slots == 1 && segs[0].n_q <= tc_window_points(prec)) ? 1 : 0;
     // job order: contiguous cost ranges per CTA, or, for one plan whose shared
     // operand (every pass and form) exceeds a quarter of the L2 cache and whose
     // forms have the same number of passes, pass-major round robin so that the
@@ -1117,7 +1112,7 @@ static fe_status autotune_plan(fe_plan &P) {
                     if (r < 0) return cuda_fail((cudaError_t)(-r), "autotune factor launch");
                 }
                 float ms_min = 1e30f;
-                for (int rep = 0; rep < 5; ++rep) {   // the first run warms up; the best of the other four counts
+                for (int rep = 0; rep < 3; ++rep) {
                     FE_CUDA(cudaMemsetAsync(flush.p, rep, flush_bytes, P.stream), "autotune flush");
                     FE_CUDA(cudaEventRecord(P.ev[4], P.stream), "autotune event");
                     int r = launch_tc_elements(a, smem, P.stream);

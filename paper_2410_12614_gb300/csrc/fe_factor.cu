@@ -27,11 +27,7 @@
 // Each CTA owns half a tile (64 cells): its four warps stream that part of
 // the kappa block (a contiguous range) with coalesced loads, so the factor
 // work runs at full occupancy instead of on the element kernel's four
-// builder warps.  For one plan of simplices whose quadrature points fit one
-// window (TcArgs::fuse_factor) the element kernel's builders do this work at
-// the start of each tile instead, with the same arithmetic, and no factor
-// kernel is launched: there the element kernel is bound by its stores and its
-// builders are idle most of the time.
+// builder warps.
 #include "fe_device.cuh"
 
 namespace fe {
@@ -289,7 +285,7 @@ __global__ void __launch_bounds__(F_THREADS) factor_box_kernel(const __grid_cons
 }  // namespace
 
 int launch_factor(const TcArgs &a, cudaStream_t s) {
-    if (a.n_tiles <= 0 || a.fuse_factor) return 0;   // (fused: the element kernel's builders do this work)
+    if (a.n_tiles <= 0) return 0;
     const bool g64 = a.prec == FE_PREC_TF32X3;
     const unsigned grid = (unsigned)(a.n_tiles * (TC_M / F_CELLS));
     if (!a.segs && a.seg0.win_slots > 1) {

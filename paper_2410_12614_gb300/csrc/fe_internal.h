@@ -120,7 +120,6 @@ struct TcArgs {
     int win_buf;               // 1: a per-builder-thread shared-memory slot for the next window
     int n_acc;                 // TMEM accumulators: 2 of 256 columns, or 1 of 512 when a pass is wide
     int job_rr;                // 1: jobs in pass-major order dealt round-robin (single plan, large operand)
-    int fuse_factor;           // 1: the builders form the window and factors themselves (no factor kernel)
     int *status;
     unsigned long long timeout_ns;
 };

@@ -297,9 +297,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
     if (warp < 4) {
         // ======================= builders =======================
         // The factor kernel has left, per cell, the FP32 coefficient window
-        // w_q kappa_cq and the scaled geometry factors (or, with fuse_factor,
-        // each builder thread forms them for its cell at the start of a tile,
-        // with the factor kernel's arithmetic).  The operand C is built
+        // w_q kappa_cq and the scaled geometry factors.  The operand C is built
         // with one thread per cell: the thread keeps its cell's current window
         // (KW consecutive points of one slot) in registers and writes its own
         // 128-byte K-major row of each chunk as eight swizzled 16-byte stores:
@@ -380,67 +378,7 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                 pf_key = -1;
                 prefetch_tile(t + 1);
                 unscale_f[0] = unscale_f[1] = 1.f;
-                if (!BATCHED && a.fuse_factor) {
-                    // the factor kernel's work for this cell, here (one plan of
-                    // simplices whose points fit one window): the same roundings
-                    // in the same order, so the operand is bitwise the same
-                    float g6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, adet = 0.f;
-                    int st = 0, nonfinite = 0;
-                    if (valid) {
-                        if (PREC == FE_PREC_TF32X3) {
-                            CellGeom geo;
-                            st = cell_geometry(S.vertices, S.cells, cell, S.d, geo);
-                            if (!st) {
-#pragma unroll
-                                for (int j = 0; j < 6; ++j) g6[j] = (float)geo.G[j];
-                                adet = (float)geo.absdet;
-                            }
-                        } else {
-                            st = cell_g32(S.vertices, S.cells, cell, S.d, g6, adet);
-                        }
-                        if (st) {
-#pragma unroll
-                            for (int j = 0; j < 6; ++j) g6[j] = 0.f;
-                            adet = 0.f;
-                        }
-                    }
-                    // w_q kappa_cq: kappa rounded once to FP32, times the FP32 weight
-                    float wmax = 0.f;
-                    const double *__restrict__ krow = S.kappa + cell * s_nq;
-#pragma unroll
-                    for (int i = 0; i < KW; ++i) {
-                        win[i] = (valid && i < s_nq) ? f64_to_f32_rne(__ldg(krow + i), nonfinite) * (float)__ldg(S.weights + i)
-                                                     : 0.f;
-                        wmax = fmaxf(wmax, fabsf(win[i]));
-                    }
-                    qw_loaded = 0;
-                    const int flagbits = st | (nonfinite ? ST_NONFINITE : 0);
-                    if (flagbits) atomicOr(&sm.flags[1], flagbits);
-                    const bool need_max = a.target_exp > 1;
-#pragma unroll
-                    for (int ff = 0; ff < MAX_FORMS; ++ff) {
-                        const float gmax = (ff == 0) ? fmaxf(fmaxf(fmaxf(fabsf(g6[0]), fabsf(g6[1])), fmaxf(fabsf(g6[2]), fabsf(g6[3]))),
-                                                             fmaxf(fabsf(g6[4]), fabsf(g6[5])))
-                                                     : adet;
-                        int e_c = 0;
-                        if (need_max && !st) {
-                            const float cmax = wmax * gmax;
-                            if (cmax > 0.f && isfinite(cmax)) {
-                                int e;
-                                frexpf(cmax, &e);
-                                e_c = a.target_exp - e;
-                            }
-                        }
-                        const float scale = ldexpf(1.f, e_c);
-                        if (valid && (S.form_mask & (1 << ff))) unscale_f[ff] = ldexpf(S.op[ff].p_inv_scale, -e_c);
-                        if (ff == 0) {
-#pragma unroll
-                            for (int j = 0; j < 6; ++j) gf[j] = g6[j] * scale;
-                        } else {
-                            gf[6] = adet * scale;
-                        }
-                    }
-                } else {
+                {
                     float rec[12];
 #pragma unroll
                     for (int i = 0; i < 3; ++i) {
@@ -457,13 +395,13 @@ __global__ void __launch_bounds__(V_THREADS, 1) tc_element_kernel(const __grid_c
                         unscale_f[0] = rec[CELLF_UNSCALE];
                         unscale_f[1] = rec[CELLF_UNSCALE + 1];
                     }
-                    // a tile whose points fit one window (shared by every pair) loads it
-                    // once, here; loaded = qw * 16 + slot of the registers' window
-                    qw_loaded = -1;
-                    if (s_nq <= KW && s_slots == 1) {
-                        load_own(s_win, s_ldw, cell, valid, 0);
-                        qw_loaded = 0;
-                    }
+                }
+                // a tile whose points fit one window (shared by every pair) loads it
+                // once, here; loaded = qw * 16 + slot of the registers' window
+                qw_loaded = -1;
+                if (s_nq <= KW && s_slots == 1) {
+                    load_own(s_win, s_ldw, cell, valid, 0);
+                    qw_loaded = 0;
                 }
                 __syncwarp();
             }
