@@ -1112,7 +1112,7 @@ static fe_status autotune_plan(fe_plan &P) {
                     if (r < 0) return cuda_fail((cudaError_t)(-r), "autotune factor launch");
                 }
                 float ms_min = 1e30f;
-                for (int rep = 0; rep < 3; ++rep) {
+                for (int rep = 0; rep < 5; ++rep) {   // the first run warms up; the best of the other four counts
                     FE_CUDA(cudaMemsetAsync(flush.p, rep, flush_bytes, P.stream), "autotune flush");
                     FE_CUDA(cudaEventRecord(P.ev[4], P.stream), "autotune event");
                     int r = launch_tc_elements(a, smem, P.stream);
