@@ -24,22 +24,31 @@
 // tile carrying its segment's shapes (cell type, degree, quadrature size) and
 // buffers.  A job is one (tile, form, N pass); one CTA per SM takes a
 // contiguous run of jobs of equal cost (K chunks plus an epilogue share), so
-// the SMs stay evenly loaded when the tiles do not divide over them.
+// the SMs stay evenly loaded when the tiles do not divide over them, or, for
+// one plan whose shared operand exceeds a quarter of L2, every G-th job in
+// pass-major order, so that all CTAs stream the same operand chunks at once.
 // Roles:
 //   warps 0-3  builders, one thread per cell: its factors and its window
 //              (shared by every (s,t) pair and both forms) in registers, its
 //              128-byte swizzled K-major row of C written into a 2- or 3-stage
-//              ring (one a_full arrival per warp).
+//              ring (one a_full arrival per warp); where a job reads several
+//              windows, optionally the next one copied asynchronously into a
+//              per-thread shared-memory slot while the current one is used.
 //   warps 4-11 epilogue, two warps per TMEM lane group: drain a finished
 //              accumulator into a conflict-free staging area, release it, and
 //              write row-major element matrices with coalesced stores: whole
 //              matrices gathered from the pair columns (mirroring k <= l to
 //              k > l; the columns are ordered so that these gathers hit
 //              distinct banks), or, for the full-row layout of large
-//              elements, each pass's rows as one contiguous run.
-//   warp 12    tcgen05.mma into one of two 256-column FP32 TMEM accumulators
-//              (lane 0 issues); it only waits for operands, never for its own
-//              MMAs, so the tensor pipe always has the next chunk queued.
+//              elements, each pass's rows as one contiguous run.  Full-row
+//              passes that do not fit the staging area, and wide passes,
+//              leave from registers: each lane writes its own cell's run in
+//              16-byte stores where it is aligned.
+//   warp 12    tcgen05.mma into one of two 256-column FP32 TMEM accumulators,
+//              or, for a wide full-row pass (up to 512 columns), into both
+//              halves as one accumulator with two MMAs per K step (lane 0
+//              issues); it only waits for operands, never for its own MMAs,
+//              so the tensor pipe always has the next chunk queued.
 //   warp 13    bulk copies of the pre-swizzled P chunks (one 1-D copy per
 //              chunk, no multicast) into a ring of 2-8 stages, as deep as shared
 //              memory allows beside the staging area: the copies in flight
