@@ -110,6 +110,13 @@ struct fe_plan {
     DevBuf inc_slot;                     // [n_inc][n_phi] column slots (row-wise assembly)
     int asm_algo = 0;                    // fe_plan_set_assembly: 0 chunked segments (default), 1 one warp per row
     int wpref_mode = -1;                 // fe_plan_set_window_prefetch: -1 tuned, 0 off, 1 on
+    // fe_assemble_host: the assembly in kHostPieces ranges of chunks (consecutive
+    // rows), whose CSR values leave for the host while the next range is summed
+    std::vector<int64_t> piece_chunk;    // [pieces + 1] first chunk of each range
+    std::vector<int64_t> piece_val;      // [pieces + 1] first CSR value of each range
+    DevBuf chunk_iota;                   // [n_chunks] 0, 1, 2, ... (chunk lists of the ranges)
+    cudaEvent_t piece_done[8] = {};
+    bool pieces_ready = false;
     int fuse_mode = 0;                   // fe_plan_set_fusion: 1 on where eligible, 0 off (default)
     unsigned form_mask = 0, prec_mask = 0;
     int64_t n_cells = 0, n_vertices = 0, n_dofs = 0, nnz = 0;
@@ -150,6 +157,8 @@ struct fe_plan {
         for (int i = 0; i < 2; ++i)
             for (cudaEvent_t e : {pipe_in[i], pipe_used[i], pipe_out[i]})
                 if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : piece_done)
+            if (e) cudaEventDestroy(e);
         if (pipe_h2d) cudaStreamDestroy(pipe_h2d);
         if (pipe_d2h) cudaStreamDestroy(pipe_d2h);
     }
@@ -175,6 +184,8 @@ static cudaError_t upload(DevBuf &b, const std::vector<T> &v, cudaStream_t s) {
 }
 
 static fe_status pack_operand(fe_plan &P, int prec, int fi, int np_pass);
+// ranges of the assembly in fe_assemble_host, each downloaded as soon as it is summed
+constexpr int kHostPieces = 4;
 static fe_status autotune_plan(fe_plan &P);
 static fe_status need_pattern(const fe_plan *plan);
 static fe_status check_call(fe_plan *plan, unsigned forms, fe_precision prec);
@@ -339,6 +350,14 @@ fe_status fe_plan_create(fe_plan **out, const fe_mesh *mesh, int degree, const f
     P.nnz = pat.nnz;
     P.max_row = pat.max_row;
     P.n_chunks = (int64_t)pat.chunk_row.size() - 1;
+    if (!elements_only) {
+        const int pieces = (int)std::min<int64_t>(kHostPieces, std::max<int64_t>(1, P.n_chunks));
+        for (int k = 0; k <= pieces; ++k) {
+            const int64_t c = P.n_chunks * k / pieces;
+            P.piece_chunk.push_back(c);
+            P.piece_val.push_back(pat.row_ptr[c < P.n_chunks ? pat.chunk_row[c] : pat.n_dofs]);
+        }
+    }
 
     std::vector<double> phi, dphi, psi_box, dpsi_box;
     if (boxed) {
@@ -1240,12 +1259,80 @@ fe_status fe_assemble_host(fe_plan *plan, unsigned forms, fe_precision prec, con
         csr[fi] = plan->ws_csr[fi].p;
     }
     FE_CUDA(cudaMemcpyAsync(plan->ws_kappa.p, kappa_host, kbytes, cudaMemcpyHostToDevice, plan->stream), "copy kappa");
-    st = fe_assemble(plan, forms, prec, nullptr, plan->ws_kappa.as<double>(), nullptr, nullptr, csr[0], csr[1]);
-    if (st) return st;
     void *hout[2] = {csr_stiffness_host, csr_mass_host};
+    const int pieces = (int)plan->piece_chunk.size() - 1;
+    if (pieces < 2 || plan->asm_algo != 0 || (plan->fuse_ok && plan->fuse_mode == 1)) {
+        st = fe_assemble(plan, forms, prec, nullptr, plan->ws_kappa.as<double>(), nullptr, nullptr, csr[0], csr[1]);
+        if (st) return st;
+        for (int fi = 0; fi < 2; ++fi)
+            if (csr[fi] && hout[fi])
+                FE_CUDA(cudaMemcpyAsync(hout[fi], csr[fi], vbytes, cudaMemcpyDeviceToHost, plan->stream), "copy CSR");
+        return fe_sync_status(plan);
+    }
+    // the element matrices, then the assembly in ranges of consecutive rows (the
+    // last first, as the whole-range launch walks them); each range's CSR values
+    // are downloaded on the copy stream while the next range is summed
+    fe_plan &P = *plan;
+    if (!P.pieces_ready) {
+        std::vector<int32_t> iota((size_t)P.n_chunks);
+        for (int64_t c = 0; c < P.n_chunks; ++c) iota[(size_t)c] = (int32_t)c;
+        FE_CUDA(upload(P.chunk_iota, iota, P.stream), "upload chunk list");
+        if (!P.pipe_ready) {
+            FE_CUDA(cudaStreamCreateWithFlags(&P.pipe_h2d, cudaStreamNonBlocking), "pipeline stream");
+            FE_CUDA(cudaStreamCreateWithFlags(&P.pipe_d2h, cudaStreamNonBlocking), "pipeline stream");
+            for (int slot = 0; slot < 2; ++slot) {
+                FE_CUDA(cudaEventCreateWithFlags(&P.pipe_in[slot], cudaEventDisableTiming), "pipeline event");
+                FE_CUDA(cudaEventCreateWithFlags(&P.pipe_used[slot], cudaEventDisableTiming), "pipeline event");
+                FE_CUDA(cudaEventCreateWithFlags(&P.pipe_out[slot], cudaEventDisableTiming), "pipeline event");
+            }
+            P.pipe_ready = true;
+        }
+        for (int k = 0; k < pieces; ++k)
+            FE_CUDA(cudaEventCreateWithFlags(&P.piece_done[k], cudaEventDisableTiming), "piece event");
+        P.pieces_ready = true;
+    }
+    const size_t ebytes = (fp64 ? 8 : 4) * (size_t)P.n_cells * P.n_phi * P.n_phi;
+    void *A[2] = {nullptr, nullptr};
     for (int fi = 0; fi < 2; ++fi)
-        if (csr[fi] && hout[fi])
-            FE_CUDA(cudaMemcpyAsync(hout[fi], csr[fi], vbytes, cudaMemcpyDeviceToHost, plan->stream), "copy CSR");
+        if (forms & (fi == 0 ? FE_FORM_STIFFNESS : FE_FORM_MASS)) {
+            st = ensure_ws(P.ws_elem[fi], ebytes, "element workspace");
+            if (st) return st;
+            A[fi] = P.ws_elem[fi].p;
+        }
+    int launches = 0;
+    st = run_elements(plan, forms, prec, nullptr, P.ws_kappa.as<double>(), A, launches);
+    if (st) return st;
+    const void *Ac[2] = {A[0], A[1]};
+    const size_t vsize = fp64 ? 8 : 4;
+    mark(plan, 1, true);
+    for (int k = pieces - 1; k >= 0; --k) {
+        AsmArgs a{};
+        a.seg0 = make_asm_seg(plan, forms, Ac, csr);
+        a.segs = nullptr;
+        a.n_segs = 1;
+        a.n_rows = P.n_dofs;
+        a.n_chunks = P.n_chunks;
+        a.n_forms = n_forms_of(forms);
+        a.algo = 0;
+        a.chunk_list = P.chunk_iota.as<int32_t>() + P.piece_chunk[k];
+        a.list_count = P.piece_chunk[k + 1] - P.piece_chunk[k];
+        if (a.list_count > 0) {
+            const int r = launch_assemble(a, fp64, P.stream);
+            if (r < 0) return cuda_fail((cudaError_t)(-r), "assembly kernel launch");
+            launches += r;
+        }
+        FE_CUDA(cudaEventRecord(P.piece_done[k], P.stream), "piece event");
+        FE_CUDA(cudaStreamWaitEvent(P.pipe_d2h, P.piece_done[k], 0), "piece wait");
+        const int64_t v0 = P.piece_val[k], nv = P.piece_val[k + 1] - v0;
+        for (int fi = 0; fi < 2; ++fi)
+            if (csr[fi] && hout[fi] && nv > 0)
+                FE_CUDA(cudaMemcpyAsync(static_cast<char *>(hout[fi]) + v0 * vsize,
+                                        static_cast<const char *>(csr[fi]) + v0 * vsize, (size_t)nv * vsize,
+                                        cudaMemcpyDeviceToHost, P.pipe_d2h), "copy CSR");
+    }
+    mark(plan, 1, false);
+    P.last_launches = launches;
+    FE_CUDA(cudaStreamSynchronize(P.pipe_d2h), "copy CSR");
     return fe_sync_status(plan);
 }
 

@@ -29,3 +29,24 @@ def test_pipelined_host_assembly_matches_single_calls(prec):
     plan.assemble_host_many(kaps[:2], only, forms=("stiffness",), prec=prec)
     for i in range(2):
         assert torch.equal(only[i]["stiffness"], plan.assemble_host(kaps[i], forms=("stiffness",), prec=prec)["stiffness"])
+
+
+@pytest.mark.parametrize("cell,n,p,prec,forms", [
+    ("tetrahedron", 10, 3, "bf16", ("stiffness", "mass")),
+    ("tetrahedron", 8, 2, "fp64", ("stiffness",)),
+    ("triangle", 40, 4, "fp16", ("mass",)),
+])
+def test_single_call_ranges_bitwise(cell, n, p, prec, forms):
+    """fe_assemble_host sums the CSR rows in ranges and downloads each range
+    while the next is summed: the host values are bitwise those of the device
+    call, for both forms or one, in FP64 and the reduced formats."""
+    import torch
+    v, c = inputs.structured_mesh(cell, n, 0.15, 31)
+    pts, w = api.quadrature_rule(cell, p + 1)
+    plan = api.Plan(cell, v, c, p, pts, w, precisions=("bf16",) if prec == "fp64" else (prec,))
+    kap = inputs.lognormal_kappa(plan.n_cells, plan.n_q, 32)
+    dev = plan.assemble(torch.from_numpy(kap).cuda(), forms=forms, prec=prec)
+    host = plan.assemble_host(torch.from_numpy(kap).pin_memory(), forms=forms, prec=prec)
+    plan.sync()
+    for f in forms:
+        assert torch.equal(dev[f].cpu(), host[f]), f
