@@ -814,10 +814,10 @@ static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status, un
                 if (((segs[i].form_mask >> f) & 1) && segs[i].op[f].win_pref) a.win_buf = 1;
     a.ring_a = a.ring_b = 2;
     if (a.win_buf && tc_smem_bytes(a) > 227 * 1024) a.win_buf = 0;
-    // operand rings beside the staging area: the shared-operand ring first
-    // (each stage is one more bulk copy in flight against the L2 latency), up
-    // to four stages, then a third built-operand stage (slack for the builders'
-    // window loads), then shared-operand stages up to the maximum
+    // operand rings beside the staging area: the built-operand ring first, up to
+    // four stages (16 KB each: the builders then run further ahead of the MMAs,
+    // which hides the handshake latency of each chunk), then shared-operand stages
+    // up to the maximum (each one more bulk copy in flight against the L2 latency)
     a.ring_a = a.ring_b = 2;
     const auto grow = [&a](int &r, int to) {
         while (r < to) {
@@ -829,7 +829,8 @@ static void tc_finalize(TcArgs &a, TcSeg *segs, int n, int prec, int *status, un
         }
         return true;
     };
-    if (grow(a.ring_b, 4) && grow(a.ring_a, 3)) grow(a.ring_b, TC_MAX_RING_B);
+    grow(a.ring_a, TC_MAX_RING_A);
+    grow(a.ring_b, TC_MAX_RING_B);
 }
 
 static AsmSeg make_asm_seg(fe_plan *P, unsigned forms, const void *const A[2], void *const csr[2]) {

@@ -25,7 +25,7 @@ constexpr int TC_CHUNK_BYTES = 128;      // one 128B-swizzled K-major row per ch
 constexpr int TC_MAX_NP = 256;           // N of one MMA pass
 constexpr int MAX_FORMS = 2;             // 0 = stiffness, 1 = mass
 constexpr int TC_JOB_EPI_COST = 2;       // a job's epilogue, in K chunks, for the work split
-constexpr int TC_MAX_RING_A = 3;         // deepest ring of built (per-cell) operand chunks
+constexpr int TC_MAX_RING_A = 4;         // deepest ring of built (per-cell) operand chunks
 constexpr int TC_MAX_RING_B = 8;         // deepest ring of shared-operand chunks in flight
 
 // Quadrature points per window (K block) for a storage format: 64 for every

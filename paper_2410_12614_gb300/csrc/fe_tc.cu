@@ -30,7 +30,7 @@
 // Roles:
 //   warps 0-3  builders, one thread per cell: its factors and its window
 //              (shared by every (s,t) pair and both forms) in registers, its
-//              128-byte swizzled K-major row of C written into a 2- or 3-stage
+//              128-byte swizzled K-major row of C written into a 2- to 4-stage
 //              ring (one a_full arrival per warp); where a job reads several
 //              windows, optionally the next one copied asynchronously into a
 //              per-thread shared-memory slot while the current one is used.
